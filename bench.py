@@ -1,0 +1,307 @@
+"""Benchmark: block-based OI basis tracking + projection + reconstruction.
+
+Default workload (one step = the whole hot path over one mesh): closed torus
+from a 1024 x 1024 parametric grid (1,048,576 vertices, radial Perlin-style
+noise), 1,024 blocks of 32 x 32 vertices in one warm-start chain (raster
+order), c = 64, 2 OI steps per block, Rayleigh-Ritz, then E = U^T X and
+X~ = U E for the xyz coordinates.  Metric: Mvertices/s.
+
+Timing: W warm-up steps, then K steps, each bracketed by CUDA events on the
+launching stream; between steps a 512 MB buffer is written to flush L2 (the
+per-step inputs are smaller than L2).  Under torchrun every rank runs its own
+replica (the chain has no data-parallel split); value = all ranks' vertices /
+the slowest rank's time.  `--impl reference` times the CPU oracle on this
+host's cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1810_02719_gb300 import synth  # noqa: E402
+
+METRIC = "Mvertices/s of OI basis tracking+projection vs per-block eig, same GPU; % HBM roof"
+
+
+def workload(args):
+    N, T = args.grid, args.tile
+    xyz, faces = synth.torus(N, seed=0)
+    ptr, verts = synth.tile_partition(N, T)
+    parent = synth.raster_chain(len(ptr) - 1)
+    starts = synth.gaussian_starts(ptr, parent, args.c, seed=0)
+    return xyz, faces, ptr, verts, parent, starts
+
+
+def config_dict(args):
+    return {"workload": f"torus {args.grid}x{args.grid} ({args.grid ** 2} v), "
+                        f"{(args.grid // args.tile) ** 2} blocks of {args.tile}x{args.tile}, "
+                        f"raster warm-start chain, c={args.c}, {args.t} OI steps, RR, "
+                        f"project+reconstruct xyz",
+            "precision": args.precision, "delta": 1e-2, "z": 1, "cg_rtol": 1e-6,
+            "l2": "flushed between timed steps (512 MB write)"}
+
+
+class Clocks:
+    """nvidia-smi sampler for the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p["hbm_gbs"], "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def run_ours(args, rank, world, device):
+    import torch
+    from paper_1810_02719_gb300 import bsp
+
+    xyz, faces, ptr, verts, parent, starts = workload(args)
+    n = xyz.shape[0]
+    k = len(ptr) - 1
+    prec = {"mixed": bsp.BSP_PREC_MIXED, "f32": bsp.BSP_PREC_F32}[args.precision]
+    opts = bsp.make_opts(precision=prec, cols_per_cta=args.cs)
+    h = bsp.bsp_mesh_create(xyz, faces, ptr, verts, parent, opts)
+    stream = torch.cuda.current_stream(device)
+    V0 = torch.tensor(starts, dtype=torch.float32, device=device)
+    X = torch.tensor(xyz, dtype=torch.float32, device=device)
+    E = torch.empty(k * args.c, 3, dtype=torch.float32, device=device)
+    Xo = torch.empty_like(X)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
+
+    def step():
+        bsp.bsp_oi_track(h, args.c, args.t, V0, stream)
+        launches = bsp.bsp_get_stats(h)["gpu_launches"]
+        bsp.bsp_project(h, X, bsp.BSP_DT_F32, 3, E, stream)
+        bsp.bsp_reconstruct(h, E, 3, Xo, stream)
+        return launches + 2
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    times = []
+    launches = 0
+    with Clocks(device.index) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            launches += step()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+    torch.cuda.synchronize()
+    total = sum(times)
+    if world > 1:
+        t = torch.tensor([total], device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total = float(t.item())
+        torch.distributed.barrier()
+    value = world * n * args.steps / total / 1e6
+    st = bsp.bsp_get_stats(h)
+
+    # end to end through the C ABI with host buffers: H2D of V0 and X, D2H of E and X~
+    V0h = starts.astype(np.float32)
+    Xh = xyz.astype(np.float32)
+    Eh = np.empty((k * args.c, 3), np.float32)
+    Xoh = np.empty_like(Xh)
+    e2e_t = []
+    for i in range(max(2, args.steps // 2) + 1):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bsp.bsp_oi_track(h, args.c, args.t, V0h, stream)
+        bsp.bsp_project(h, Xh, bsp.BSP_DT_F32, 3, Eh, stream)
+        bsp.bsp_reconstruct(h, Eh, 3, Xoh, stream)
+        torch.cuda.synchronize()
+        if i > 0:
+            e2e_t.append(time.perf_counter() - t0)
+    e2e_value = world * n / statistics.mean(e2e_t) / 1e6
+
+    # roofline of the operator kernel: (L + delta I) P over all blocks, c columns
+    P = torch.randn(n, args.c, device=device)
+    Y = torch.empty_like(P)
+    for _ in range(3):
+        bsp.bsp_spmm(h, P, Y, args.c, stream)
+    reps = 20
+    sp = []
+    for _ in range(reps):
+        flush.fill_(1.0)
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        bsp.bsp_spmm(h, P, Y, args.c, stream)
+        a1.record(stream)
+        a1.synchronize()
+        sp.append(a0.elapsed_time(a1) / 1e3)
+    t_spmm = statistics.mean(sp)
+    nnz = st["nnz"]
+    alg_bytes = n * args.c * 4 * 2 + nnz * 2 + (n + 1) * 4 + n * 4 + n * 4
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / t_spmm / 1e9
+    bsp.bsp_mesh_destroy(h)
+    return {
+        "value": value, "ms_per_step": 1e3 * total / args.steps, "launches": launches // args.steps,
+        "clocks": clk.summary(),
+        "e2e": {"value": e2e_value, "unit": "Mvertices/s",
+                "h2d_bytes_per_step": int(V0h.nbytes + Xh.nbytes),
+                "d2h_bytes_per_step": int(Eh.nbytes + Xoh.nbytes)},
+        "roofline": {"kernel": "k_spmm_vec (Y = (L + delta I) P, all 1,024 blocks, c=64)",
+                     "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "algorithmic_bytes": alg_bytes, "avg_launch_s": t_spmm},
+        "stats": {"cg_steps_total": st["cg_steps_total"], "cg_steps_max": st["cg_steps_max"]},
+    }
+
+
+def oracle_sample(args, budget_s):
+    """Time the oracle's Algorithm 1 chain on the first blocks of the workload."""
+    from oracle import bsp_oracle as O
+    xyz, faces, ptr, verts, parent, starts = workload(args)
+    nb = args.tile * args.tile
+    om = O.build_mesh(xyz.shape[0], ptr, verts, parent, faces=faces)
+    t0 = time.perf_counter()
+    U = None
+    done = 0
+    for b in range(len(ptr) - 1):
+        L = O.laplacian(om.blocks[b])
+        V0 = starts[:nb, :args.c] if b == 0 else U
+        U, _ = O.oi_block(L, V0, 1e-2, 1, args.t, rr=True)
+        Xb = xyz[om.blocks[b].verts]
+        _ = U @ (U.T @ Xb)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return done * nb / dt / 1e6, done, dt, cores
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--grid", type=int, default=1024)
+    ap.add_argument("--tile", type=int, default=32)
+    ap.add_argument("--c", type=int, default=64)
+    ap.add_argument("--t", type=int, default=2)
+    ap.add_argument("--cs", type=int, default=0, help="CG column-slab width (0 = auto)")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "f32"])
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        v, blocks, dt, cores = oracle_sample(args, args.cpu_budget)
+        steps = []
+        for _ in range(args.warmup):
+            pass
+        line = {"metric": METRIC, "value": v, "unit": "Mvertices/s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic", "impl": "reference",
+                "config": config_dict(args),
+                "cpu_baseline": {"value": v, "unit": "Mvertices/s", "cores": cores,
+                                 "kind": "oracle",
+                                 "sample": f"first {blocks} blocks of the chain ({dt:.1f} s)"},
+                "e2e": {"value": v, "unit": "Mvertices/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        del steps
+        print(json.dumps(line))
+        return
+
+    import torch
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    res = run_ours(args, rank, world, device)
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    cpu = None
+    if world == 1:
+        v, blocks, dt, cores = oracle_sample(args, args.cpu_budget)
+        cpu = {"value": v, "unit": "Mvertices/s", "cores": cores, "kind": "oracle",
+               "sample": f"first {blocks} of {(args.grid // args.tile) ** 2} chain blocks "
+                         f"({dt:.1f} s), FP64 NumPy/LAPACK"}
+    line = {"metric": METRIC, "value": res["value"], "unit": "Mvertices/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "f32" else "f32+f64(gram,chol)",
+            "data": "synthetic", "config": config_dict(args), "clocks": res["clocks"],
+            "e2e": res["e2e"], "gpu_launches": res["launches"], "roofline": res["roofline"],
+            "cpu_baseline": cpu, "stats": res["stats"]}
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,272 @@
+/*
+ * bsp.h — C ABI of the GB300 (sm_103a) library for block-based spectral
+ * processing of triangle meshes with orthogonal iterations (OI).
+ *
+ * Method: Arvanitis, Lalos, Moustakas, "Block-Based Spectral Processing of
+ * Static and Dynamic 3D Meshes using Orthogonal Iterations".  A mesh
+ * M = (V, F) (Sec. 3) is split into k blocks (Sec. 4); for each block b the
+ * library assembles the graph Laplacian L[b] = D - C (Sec. 3, Eqs. for L and
+ * C), tracks the c lowest-frequency eigenvectors U_c[b] by orthogonal
+ * iterations U(t) = Onorm(R^z U(t-1)), R = (L[b] + delta I)^-1, warm-started
+ * from the parent block's basis (Sec. 4, Algorithm 1), optionally chooses c
+ * per block for a reconstruction-quality target (Sec. 5, Algorithm 2), and
+ * projects/reconstructs coordinates E = U^T v, v~ = U E (Sec. 3 GFT;
+ * Sec. 7.1 compression; Sec. 7.2 coarse denoising; Sec. 7.3 all frames of a
+ * dynamic mesh with one basis).
+ *
+ * Conventions for every entry point:
+ *  - Returns a bsp_status; no C++ exception crosses this boundary.  On error,
+ *    bsp_last_error() returns a thread-local message for the failing call.
+ *  - Pointer arguments marked "host or device" may point to host memory
+ *    (pageable or pinned) or to device memory of the current CUDA device; the
+ *    library detects which with cudaPointerGetAttributes and copies as needed.
+ *    Such calls are synchronous with respect to host buffers.
+ *  - "stream" is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Every call returns only after its work on that stream has
+ *    finished, so its status covers numerical failures detected on the GPU.
+ *  - Matrices are row-major.  "real" means float when the mesh precision is
+ *    BSP_PREC_F32 or BSP_PREC_MIXED and double when it is BSP_PREC_F64.
+ *  - The caller owns every buffer it passes; the library copies what it keeps.
+ *  - Blocks are numbered 0..k-1 and must be topologically sorted:
+ *    parent[b] < b, or parent[b] = -1 for a root (Sec. 4: "the subsequent ones
+ *    are processed in a topologically sorted order").
+ */
+#ifndef BSP_H_
+#define BSP_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum bsp_status {
+  BSP_OK = 0,
+  BSP_ERR_INVALID_ARG = 1,   /* bad index, non-covering partition, c > n_b, delta <= 0, ... */
+  BSP_ERR_OOM = 2,           /* device allocation failed */
+  BSP_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+  BSP_ERR_NUMERICAL = 4,     /* Gram matrix not positive definite, NaN/Inf */
+  BSP_ERR_TIMEOUT = 5,       /* a bounded device wait expired */
+  BSP_ERR_NOT_CONVERGED = 6  /* a CG solve hit its step cap; results are still written */
+} bsp_status;
+
+typedef enum bsp_precision {
+  BSP_PREC_F32 = 0,    /* FP32 everywhere, including Gram accumulation and Cholesky */
+  BSP_PREC_F64 = 1,    /* FP64 everywhere */
+  BSP_PREC_MIXED = 2   /* FP32 vectors/solves/projection; FP64 Gram accumulation and Cholesky */
+} bsp_precision;
+
+typedef enum bsp_weight_mode {
+  BSP_W_COMBINATORIAL = 0,  /* C_ij = 1 on every edge */
+  BSP_W_EDGE = 1,           /* C_ij = per-edge weight, initially 1, set by bsp_set_edge_weights */
+  BSP_W_INV_SQ_DIST = 2     /* C_ij = 1 / ||v_i - v_j||^2 (Sec. 3, Eq. for C) */
+} bsp_weight_mode;
+
+typedef enum bsp_dtype {
+  BSP_DT_F32 = 0,
+  BSP_DT_F64 = 1,
+  BSP_DT_BF16 = 2
+} bsp_dtype;
+
+typedef struct bsp_opts {
+  double delta;            /* shift delta > 0 in R = (L + delta I)^-1 (Sec. 4). Default 1e-2. */
+  int32_t z;               /* power z >= 1 of R (Sec. 4). Default 1. */
+  int32_t weight_mode;     /* bsp_weight_mode. Default BSP_W_COMBINATORIAL. */
+  int32_t literal_degree;  /* 1: D_ii = |N(i)| as printed in Sec. 3; 0: D_ii = sum_j C_ij. Default 0. */
+  int32_t precision;       /* bsp_precision. Default BSP_PREC_MIXED. */
+  double cg_rtol;          /* CG stop: ||r_j|| <= cg_rtol * ||b_j|| per column. Default 1e-6 (1e-12 for F64). */
+  int32_t cg_max_steps;    /* CG step cap per solve. Default 2000. */
+  int32_t rayleigh_ritz;   /* 1: Rayleigh-Ritz after the OI steps of each block (ascending order). Default 1. */
+  int32_t cols_per_cta;    /* CG column-slab width (1, 2, 4 or 8); 0 = automatic. */
+  int32_t use_graph;       /* 1: capture the fixed-c tracking schedule in a CUDA graph. Default 1. */
+} bsp_opts;
+
+typedef struct bsp_stats {
+  int64_t n;               /* vertices */
+  int32_t k;               /* blocks */
+  int64_t nnz;             /* stored off-diagonal entries over all blocks (2 x intra-block edges) */
+  int64_t intra_edges;     /* intra-block edges */
+  int32_t max_block;       /* largest n_b */
+  int32_t levels;          /* depth of the block forest (number of dependent waves) */
+  int64_t cg_steps_total;  /* CG steps summed over all CTAs' slabs in the last tracking call */
+  int32_t cg_steps_max;    /* largest step count of one solve in the last tracking call */
+  int32_t not_converged;   /* solves that hit cg_max_steps in the last tracking call */
+  int32_t gpu_launches;    /* kernels launched by the last tracking/projection call */
+} bsp_stats;
+
+typedef struct bsp_mesh bsp_mesh;
+
+/* Fill *opts with the defaults listed above. */
+void bsp_opts_default(bsp_opts* opts);
+
+/*
+ * Create a partitioned mesh and assemble every block's Laplacian on the GPU
+ * (Sec. 3 L = D - C; Sec. 4 block processing; Sec. 6.1 a block only sees its
+ * own edges).  Edges are the sides of the faces (Sec. 3); an edge belongs to
+ * block b when both end points lie in b.
+ *   xyz         host or device, double [n x 3]; may be NULL unless
+ *               weight_mode = BSP_W_INV_SQ_DIST.
+ *   faces       host or device, int32 [m x 3], vertex ids in [0, n).
+ *   block_ptr   host or device, int32 [k + 1], block_ptr[0] = 0, non-decreasing,
+ *               block_ptr[k] = n: the partition must cover every vertex once.
+ *   block_verts host or device, int32 [n]: block b's vertices in their local
+ *               order are block_verts[block_ptr[b] .. block_ptr[b+1]).
+ *   parent      host or device, int32 [k]: warm-start parent, parent[b] < b or -1.
+ *   opts        host; NULL = defaults.
+ *   out         receives the new mesh; *out = NULL on error.
+ * Errors: BSP_ERR_INVALID_ARG (index out of range, vertex missing or repeated,
+ * block larger than 65535, parent not earlier), BSP_ERR_OOM, BSP_ERR_CUDA.
+ */
+int bsp_mesh_create(const double* xyz, int64_t n, const int32_t* faces, int64_t m,
+                    const int32_t* block_ptr, const int32_t* block_verts, int32_t k,
+                    const int32_t* parent, const bsp_opts* opts, bsp_mesh** out);
+
+/* As bsp_mesh_create, from an explicit edge list (host or device int32 [E x 2])
+ * instead of faces; for graphs that are not triangle meshes (paths, cycles). */
+int bsp_mesh_create_edges(const double* xyz, int64_t n, const int32_t* edges, int64_t E,
+                          const int32_t* block_ptr, const int32_t* block_verts, int32_t k,
+                          const int32_t* parent, const bsp_opts* opts, bsp_mesh** out);
+
+/* Release every device buffer of the mesh.  NULL is accepted. */
+int bsp_mesh_destroy(bsp_mesh* mesh);
+
+/* Mesh sizes and counters of the last call. */
+int bsp_get_stats(const bsp_mesh* mesh, bsp_stats* stats);
+
+/*
+ * Intra-block edge list in the library's canonical order: by block, then by
+ * local pair (i, j), i < j, lexicographically.  edges_out: host or device
+ * int32 [E_intra x 2] of GLOBAL vertex ids (NULL to query only); *E_out
+ * receives E_intra.  This is the order of bsp_set_edge_weights.
+ */
+int bsp_get_edges(const bsp_mesh* mesh, int32_t* edges_out, int64_t* E_out);
+
+/*
+ * Per-block assembled Laplacian of block b in CSR form (for checking the
+ * assembly against Sec. 3's definition).  row_ptr: int32 [n_b + 1]; cols:
+ * int32 [nnz_b] local column ids ascending per row; vals: real [nnz_b] = C_ij;
+ * diag: real [n_b] = D_ii.  All host or device; pass NULL to skip an array;
+ * *nnz_b receives the entry count.
+ */
+int bsp_get_block_csr(const bsp_mesh* mesh, int32_t b, int32_t* row_ptr, int32_t* cols,
+                      void* vals, void* diag, int64_t* nnz_b);
+
+/*
+ * Replace the edge weights C_ij (mesh created with BSP_W_EDGE), in the order of
+ * bsp_get_edges; D_ii is re-derived.  w: host or device real [E].
+ * Errors: BSP_ERR_INVALID_ARG if the mode is not BSP_W_EDGE or E mismatches.
+ */
+int bsp_set_edge_weights(bsp_mesh* mesh, const void* w, int64_t E);
+
+/*
+ * Fixed-c orthogonal iterations over all blocks (Sec. 4, Algorithm 1).
+ * For every block in topological order: U(0) = Onorm(start); t_max times
+ * U(t) = Onorm(R^z U(t-1)) with R^z applied by z conjugate-gradient solves
+ * with (L + delta I) (Sec. 4: R^z U is computed with sparse linear solvers);
+ * optional Rayleigh-Ritz.  start = the parent's final basis (rows mapped
+ * r -> floor(r n_parent / n_b) when sizes differ), or, for a root, its rows
+ * of V0_roots.  Independent blocks (same forest depth) run concurrently.
+ *   c        1 <= c <= min over blocks of n_b, c <= 128.
+ *   t_max    >= 0 OI steps per block.
+ *   V0_roots host or device real [sum over roots of n_b, c]: the roots' start
+ *            matrices concatenated in block order; any full-rank matrices.
+ * Results stay on the device (bsp_get_basis, bsp_project).
+ * Errors: BSP_ERR_INVALID_ARG, BSP_ERR_NUMERICAL, BSP_ERR_NOT_CONVERGED, BSP_ERR_CUDA.
+ */
+int bsp_oi_track(bsp_mesh* mesh, int32_t c, int32_t t_max, const void* V0_roots, void* stream);
+
+/*
+ * Dynamic-c orthogonal iterations (Sec. 5, Algorithm 2; quality-target reading).
+ * Per block: start at c_parent (roots: c_min); run Algorithm 1 and
+ * Rayleigh-Ritz; choose the smallest j in {c_step, 2 c_step, ...} with
+ * ||X_b - U_j U_j^T X_b||_F <= rel_tol ||X_b||_F (shrink = Ritz prefix); if none,
+ * grow by c_step columns [e/||e||, counter-hash columns] with e the residual
+ * summed over x, y, z (Sec. 5, Eq. residual and Eq. newU), orthonormalise and
+ * repeat, up to c_max.
+ *   X        host or device real [n x 3] coordinates.
+ *   V0_roots host or device real [sum over roots of n_b, c_min].
+ *   forced_c host or device int32 [k] or NULL: when forced_c[b] >= 0 it replaces
+ *            the decision of block b (replay hook).
+ *   c_out    host or device int32 [k] or NULL: chosen c_b.
+ * Requires c_min, c_max multiples of c_step, c_max <= 128.
+ */
+int bsp_oi_track_dynamic(bsp_mesh* mesh, const void* X, double rel_tol, int32_t c_min,
+                         int32_t c_max, int32_t c_step, int32_t t_max, uint64_t seed,
+                         const void* V0_roots, const int32_t* forced_c, int32_t* c_out,
+                         void* stream);
+
+/* Chosen c_b of every block after the last tracking call: host or device int32 [k]. */
+int bsp_get_block_c(const bsp_mesh* mesh, int32_t* c_out);
+
+/*
+ * Basis U_c[b] of block b after tracking: host or device real [n_b x c_b]
+ * (row-major, local vertex order).  *c receives c_b (U may be NULL to query).
+ */
+int bsp_get_basis(const bsp_mesh* mesh, int32_t b, void* U, int32_t* c);
+
+/*
+ * Spectral coefficients E[b] = U_c[b]^T X_b for every block (Sec. 3 GFT;
+ * Sec. 7.1 encoder; Sec. 7.3 all frames at once).
+ *   X       host or device [n x cols] with cols = 3 F (F frames of xyz per
+ *           vertex row), element type x_dtype (BSP_DT_BF16 only with F32/MIXED).
+ *   E_out   host or device real [sum_b c_b x cols], blocks concatenated in order.
+ */
+int bsp_project(bsp_mesh* mesh, const void* X, int32_t x_dtype, int32_t cols, void* E_out,
+                void* stream);
+
+/*
+ * Reconstruction v~[b] = U_c[b] E[b] scattered to the global vertex rows
+ * (Sec. 7.1 decoder; Sec. 7.2 coarse denoising v^ = U U^T v).
+ *   E       host or device real [sum_b c_b x cols].
+ *   X_out   host or device real [n x cols].
+ */
+int bsp_reconstruct(bsp_mesh* mesh, const void* E, int32_t cols, void* X_out, void* stream);
+
+/*
+ * Standalone operator product Y = (L + delta I) P for all blocks at once (the
+ * sparse x tall-skinny kernel inside every CG step of R^z U, Sec. 4).
+ *   P, Y    device real [n x c], rows in block order (row block_ptr[b] + i is
+ *           local vertex i of block b).  1 <= c <= 128.
+ */
+int bsp_spmm(bsp_mesh* mesh, const void* P, void* Y, int32_t c, void* stream);
+
+/* Kernel classes reported by bsp_get_kernel_times, in this order. */
+typedef enum bsp_kernel_class {
+  BSP_KC_INIT = 0,     /* start matrices (root rows / parent row transfer) */
+  BSP_KC_CG = 1,       /* fused CG solves of (L + delta I)^z Y = V */
+  BSP_KC_GRAM = 2,     /* panel Gram partials of Onorm */
+  BSP_KC_REDUCE = 3,   /* panel-partial reductions */
+  BSP_KC_CHOL = 4,     /* c x c Cholesky + triangular inverse */
+  BSP_KC_PANEL = 5,    /* panel x (c x c) products: Q = Y R^-1, V Q_H */
+  BSP_KC_RR = 6,       /* H = V^T L V partials */
+  BSP_KC_JACOBI = 7,   /* c x c Jacobi eigensolve of H */
+  BSP_KC_PROJECT = 8,  /* E = U^T X */
+  BSP_KC_RECON = 9,    /* X~ = U E */
+  BSP_KC_SPMM = 10,    /* standalone (L + delta I) P */
+  BSP_KC_DYN = 11,     /* dynamic-c decision and growth */
+  BSP_KC_COUNT = 12
+} bsp_kernel_class;
+
+/*
+ * Per-kernel-class timing (not part of the paper's method: instrumentation).
+ * While on, every launch made by this mesh's calls is bracketed by CUDA events
+ * recorded on the launching stream, and the fixed-c schedule runs eagerly
+ * instead of as a CUDA graph; the kernels themselves are unchanged.  Turning it
+ * on or off clears the accumulated times.
+ */
+int bsp_set_profiling(bsp_mesh* mesh, int32_t on);
+
+/* Accumulated milliseconds and launch counts per class since profiling was
+ * switched on; ms_out and launches_out are host arrays of n_classes entries
+ * (either may be NULL). */
+int bsp_get_kernel_times(const bsp_mesh* mesh, double* ms_out, int32_t* launches_out,
+                         int32_t n_classes);
+
+/* Thread-local message describing the last failure on this thread ("" if none). */
+const char* bsp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BSP_H_ */

@@ -1,0 +1,278 @@
+"""Thin ctypes binding of libbsp.so (the C ABI in include/bsp.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  Functions keep the C names; arrays may be NumPy arrays (host)
+or torch tensors (host or CUDA).  There is no CPU fallback: importing this
+module fails loudly if the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "libbsp.so")
+
+BSP_OK = 0
+BSP_ERR_INVALID_ARG = 1
+BSP_ERR_OOM = 2
+BSP_ERR_CUDA = 3
+BSP_ERR_NUMERICAL = 4
+BSP_ERR_TIMEOUT = 5
+BSP_ERR_NOT_CONVERGED = 6
+
+BSP_PREC_F32, BSP_PREC_F64, BSP_PREC_MIXED = 0, 1, 2
+BSP_W_COMBINATORIAL, BSP_W_EDGE, BSP_W_INV_SQ_DIST = 0, 1, 2
+BSP_DT_F32, BSP_DT_F64, BSP_DT_BF16 = 0, 1, 2
+
+_STATUS = {0: "BSP_OK", 1: "BSP_ERR_INVALID_ARG", 2: "BSP_ERR_OOM", 3: "BSP_ERR_CUDA",
+           4: "BSP_ERR_NUMERICAL", 5: "BSP_ERR_TIMEOUT", 6: "BSP_ERR_NOT_CONVERGED"}
+
+
+class bsp_opts(C.Structure):
+    _fields_ = [("delta", C.c_double), ("z", C.c_int32), ("weight_mode", C.c_int32),
+                ("literal_degree", C.c_int32), ("precision", C.c_int32),
+                ("cg_rtol", C.c_double), ("cg_max_steps", C.c_int32),
+                ("rayleigh_ritz", C.c_int32), ("cols_per_cta", C.c_int32),
+                ("use_graph", C.c_int32)]
+
+
+class bsp_stats(C.Structure):
+    _fields_ = [("n", C.c_int64), ("k", C.c_int32), ("nnz", C.c_int64),
+                ("intra_edges", C.c_int64), ("max_block", C.c_int32), ("levels", C.c_int32),
+                ("cg_steps_total", C.c_int64), ("cg_steps_max", C.c_int32),
+                ("not_converged", C.c_int32), ("gpu_launches", C.c_int32)]
+
+
+class BspError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"{_LIB_PATH} is missing: build it with "
+                          "paper_1810_02719_gb300.build.build() (nvcc, sm_103a)")
+    lib = C.CDLL(_LIB_PATH)
+    P, I32, I64, D, U64 = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_uint64
+    sig = {
+        "bsp_opts_default": (None, [C.POINTER(bsp_opts)]),
+        "bsp_mesh_create": (C.c_int, [P, I64, P, I64, P, P, I32, P, C.POINTER(bsp_opts),
+                                      C.POINTER(P)]),
+        "bsp_mesh_create_edges": (C.c_int, [P, I64, P, I64, P, P, I32, P, C.POINTER(bsp_opts),
+                                            C.POINTER(P)]),
+        "bsp_mesh_destroy": (C.c_int, [P]),
+        "bsp_get_stats": (C.c_int, [P, C.POINTER(bsp_stats)]),
+        "bsp_get_edges": (C.c_int, [P, P, C.POINTER(I64)]),
+        "bsp_get_block_csr": (C.c_int, [P, I32, P, P, P, P, C.POINTER(I64)]),
+        "bsp_set_edge_weights": (C.c_int, [P, P, I64]),
+        "bsp_oi_track": (C.c_int, [P, I32, I32, P, P]),
+        "bsp_oi_track_dynamic": (C.c_int, [P, P, D, I32, I32, I32, I32, U64, P, P, P, P]),
+        "bsp_get_block_c": (C.c_int, [P, P]),
+        "bsp_get_basis": (C.c_int, [P, I32, P, C.POINTER(I32)]),
+        "bsp_project": (C.c_int, [P, P, I32, I32, P, P]),
+        "bsp_reconstruct": (C.c_int, [P, P, I32, P, P]),
+        "bsp_spmm": (C.c_int, [P, P, P, I32, P]),
+        "bsp_last_error": (C.c_char_p, []),
+        "bsp_set_profiling": (C.c_int, [P, I32]),
+        "bsp_get_kernel_times": (C.c_int, [P, P, P, I32]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+LIB_PATH = _LIB_PATH
+
+
+def exported_symbols():
+    """Names the binding resolves in libbsp.so."""
+    return ["bsp_opts_default", "bsp_mesh_create", "bsp_mesh_create_edges", "bsp_mesh_destroy",
+            "bsp_get_stats", "bsp_get_edges", "bsp_get_block_csr", "bsp_set_edge_weights",
+            "bsp_oi_track", "bsp_oi_track_dynamic", "bsp_get_block_c", "bsp_get_basis",
+            "bsp_project", "bsp_reconstruct", "bsp_spmm", "bsp_last_error",
+            "bsp_set_profiling", "bsp_get_kernel_times"]
+
+
+def _check(code):
+    if code != BSP_OK:
+        raise BspError(code, _lib.bsp_last_error().decode())
+
+
+def _ptr(a):
+    """Raw pointer of a NumPy array or torch tensor (must be contiguous); None -> NULL."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _i32(a):
+    if isinstance(a, np.ndarray) or a is None or not hasattr(a, "data_ptr"):
+        return None if a is None else np.ascontiguousarray(a, dtype=np.int32)
+    return a.contiguous()
+
+
+def _f64(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.contiguous()
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def bsp_opts_default() -> bsp_opts:
+    o = bsp_opts()
+    _lib.bsp_opts_default(C.byref(o))
+    return o
+
+
+def make_opts(**kw) -> bsp_opts:
+    o = bsp_opts_default()
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def bsp_mesh_create(xyz, faces, block_ptr, block_verts, parent, opts=None, n=None):
+    """Create a mesh from faces; returns an opaque handle (int)."""
+    xyz = _f64(xyz)
+    faces, block_ptr = _i32(faces), _i32(block_ptr)
+    block_verts, parent = _i32(block_verts), _i32(parent)
+    if n is None:
+        n = int(block_verts.shape[0])
+    h = C.c_void_p()
+    _check(_lib.bsp_mesh_create(_ptr(xyz), n, _ptr(faces), int(faces.shape[0]), _ptr(block_ptr),
+                                _ptr(block_verts), int(block_ptr.shape[0]) - 1, _ptr(parent),
+                                C.byref(opts) if opts is not None else None, C.byref(h)))
+    return h.value
+
+
+def bsp_mesh_create_edges(xyz, edges, block_ptr, block_verts, parent, opts=None, n=None):
+    xyz = _f64(xyz)
+    edges, block_ptr = _i32(edges), _i32(block_ptr)
+    block_verts, parent = _i32(block_verts), _i32(parent)
+    if n is None:
+        n = int(block_verts.shape[0])
+    h = C.c_void_p()
+    _check(_lib.bsp_mesh_create_edges(_ptr(xyz), n, _ptr(edges), int(edges.shape[0]),
+                                      _ptr(block_ptr), _ptr(block_verts),
+                                      int(block_ptr.shape[0]) - 1, _ptr(parent),
+                                      C.byref(opts) if opts is not None else None, C.byref(h)))
+    return h.value
+
+
+def bsp_mesh_destroy(mesh):
+    _check(_lib.bsp_mesh_destroy(mesh))
+
+
+def bsp_get_stats(mesh) -> dict:
+    st = bsp_stats()
+    _check(_lib.bsp_get_stats(mesh, C.byref(st)))
+    return {f: getattr(st, f) for f, _ in bsp_stats._fields_}
+
+
+def bsp_get_edges(mesh) -> np.ndarray:
+    E = C.c_int64()
+    _check(_lib.bsp_get_edges(mesh, None, C.byref(E)))
+    out = np.empty((E.value, 2), dtype=np.int32)
+    _check(_lib.bsp_get_edges(mesh, _ptr(out), C.byref(E)))
+    return out
+
+
+def bsp_get_block_csr(mesh, b, n_b, real=np.float32):
+    nnz = C.c_int64()
+    _check(_lib.bsp_get_block_csr(mesh, b, None, None, None, None, C.byref(nnz)))
+    rp = np.empty(n_b + 1, np.int32)
+    cols = np.empty(nnz.value, np.int32)
+    vals = np.empty(nnz.value, real)
+    diag = np.empty(n_b, real)
+    _check(_lib.bsp_get_block_csr(mesh, b, _ptr(rp), _ptr(cols), _ptr(vals), _ptr(diag),
+                                  C.byref(nnz)))
+    return rp, cols, vals, diag
+
+
+def bsp_set_edge_weights(mesh, w):
+    _check(_lib.bsp_set_edge_weights(mesh, _ptr(w), int(w.shape[0])))
+
+
+def bsp_oi_track(mesh, c, t_max, V0_roots, stream=None):
+    _check(_lib.bsp_oi_track(mesh, c, t_max, _ptr(V0_roots), _stream_ptr(stream)))
+
+
+def bsp_oi_track_dynamic(mesh, X, rel_tol, c_min, c_max, c_step, t_max, seed, V0_roots,
+                         forced_c=None, c_out=None, stream=None):
+    forced_c = _i32(forced_c)
+    _check(_lib.bsp_oi_track_dynamic(mesh, _ptr(X), rel_tol, c_min, c_max, c_step, t_max,
+                                     seed, _ptr(V0_roots), _ptr(forced_c), _ptr(c_out),
+                                     _stream_ptr(stream)))
+
+
+def bsp_get_block_c(mesh, k) -> np.ndarray:
+    out = np.empty(k, np.int32)
+    _check(_lib.bsp_get_block_c(mesh, _ptr(out)))
+    return out
+
+
+def bsp_get_basis(mesh, b, n_b, real=np.float32) -> np.ndarray:
+    c = C.c_int32()
+    _check(_lib.bsp_get_basis(mesh, b, None, C.byref(c)))
+    U = np.empty((n_b, c.value), real)
+    _check(_lib.bsp_get_basis(mesh, b, _ptr(U), C.byref(c)))
+    return U
+
+
+def bsp_project(mesh, X, x_dtype, cols, E_out, stream=None):
+    _check(_lib.bsp_project(mesh, _ptr(X), x_dtype, cols, _ptr(E_out), _stream_ptr(stream)))
+
+
+def bsp_reconstruct(mesh, E, cols, X_out, stream=None):
+    _check(_lib.bsp_reconstruct(mesh, _ptr(E), cols, _ptr(X_out), _stream_ptr(stream)))
+
+
+def bsp_spmm(mesh, P, Y, c, stream=None):
+    _check(_lib.bsp_spmm(mesh, _ptr(P), _ptr(Y), c, _stream_ptr(stream)))
+
+
+KERNEL_CLASSES = ["init", "cg", "gram", "reduce", "chol", "panel", "rr", "jacobi", "project",
+                  "recon", "spmm", "dyn"]
+
+
+def bsp_set_profiling(mesh, on):
+    _check(_lib.bsp_set_profiling(mesh, 1 if on else 0))
+
+
+def bsp_get_kernel_times(mesh) -> dict:
+    """{class: (total_ms, launches)} accumulated while profiling was on."""
+    n = len(KERNEL_CLASSES)
+    ms = np.zeros(n, np.float64)
+    cnt = np.zeros(n, np.int32)
+    _check(_lib.bsp_get_kernel_times(mesh, _ptr(ms), _ptr(cnt), n))
+    return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNEL_CLASSES)}
+
+
+def bsp_last_error() -> str:
+    return _lib.bsp_last_error().decode()

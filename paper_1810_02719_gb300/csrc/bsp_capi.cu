@@ -1,0 +1,977 @@
+// C ABI of the library (declared in include/bsp.h): argument checking, device
+// buffers, the schedule of kernels over the block forest, and CUDA-graph
+// capture of the fixed-c schedule.
+//
+// Schedule (Sec. 4, Algorithm 1, blocks in topological order): blocks at the
+// same depth of the warm-start forest are independent and form one wave; a
+// wave runs as one launch of each kernel with the wave's blocks on the grid's
+// y axis.  Per wave: start matrices (root rows or row-transferred parent
+// basis) -> Onorm where the start is not already orthonormal -> t_max times
+// {CG solve of (L + delta I)^z Y = V; Onorm (CholeskyQR2)} -> Rayleigh-Ritz.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "bsp_internal.cuh"
+
+using namespace bsp;
+
+namespace bsp {
+thread_local Profiler* g_prof = nullptr;
+}
+
+namespace {
+
+// Collects the events of a profiled call after its stream has synchronised.
+struct ProfScope {
+  bsp_mesh* M;
+  Profiler P;
+  explicit ProfScope(bsp_mesh* m) : M(m) {
+    if (M && M->profiling) g_prof = &P;
+  }
+  ~ProfScope() {
+    if (!M || !M->profiling) return;
+    g_prof = nullptr;
+    for (int c = 0; c < KC_COUNT; ++c) {
+      auto& v = P.ev[c];
+      for (size_t i = 0; i + 1 < v.size(); i += 2) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(v[i + 1]) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, v[i], v[i + 1]) == cudaSuccess) {
+          M->prof_ms[c] += ms;
+          M->prof_n[c] += 1;
+        }
+      }
+      for (auto e : v) cudaEventDestroy(e);
+    }
+    cudaGetLastError();
+  }
+};
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CU(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(BSP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Copy `bytes` from a host-or-device pointer into a device buffer.
+int to_device(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) return BSP_OK;
+  cudaMemcpyKind kind = is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CU(cudaMemcpyAsync(dst, src, bytes, kind, s));
+  return BSP_OK;
+}
+
+// Copy from a device buffer to a host-or-device destination.
+int from_device(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) return BSP_OK;
+  cudaMemcpyKind kind = is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CU(cudaMemcpyAsync(dst, src, bytes, kind, s));
+  return BSP_OK;
+}
+
+// Read a host-or-device array into a host vector.
+template <typename V>
+int read_host(std::vector<V>& out, const V* src, size_t count) {
+  out.resize(count);
+  if (count == 0) return BSP_OK;
+  if (is_device_ptr(src)) {
+    CU(cudaMemcpy(out.data(), src, count * sizeof(V), cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(out.data(), src, count * sizeof(V));
+  }
+  return BSP_OK;
+}
+
+bool g_realloc = false;  // set when ensure() replaces a buffer (cached graphs go stale)
+
+int ensure(void** p, size_t* cap, size_t bytes) {
+  if (*cap >= bytes && *p) return BSP_OK;
+  g_realloc = true;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  if (cudaMalloc(p, bytes ? bytes : 16) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(BSP_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+  }
+  *cap = bytes;
+  return BSP_OK;
+}
+
+void configure_once() {
+  static std::once_flag flag;
+  std::call_once(flag, [] {
+    configure_cg_kernels();
+    configure_dense_kernels();
+  });
+}
+
+int pad4(int c) { return (c + 3) & ~3; }
+
+void release(bsp_mesh* m) {
+  void* ptrs[] = {m->d_bptr, m->d_verts, m->d_rowptr, m->d_eoff, m->d_blk_row, m->d_parent,
+                  m->d_root_off, m->d_waves, m->d_cb, m->d_cpar, m->d_ceoff, m->d_col,
+                  m->d_wt, m->d_diag, m->d_status, m->d_cgstats, m->d_U, m->d_Y, m->d_starts,
+                  m->d_Gp, m->d_Rsm, m->d_theta, m->d_action, m->d_round, m->d_forced,
+                  m->d_gcol, m->d_rho, m->d_X};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (m->graph_exec) cudaGraphExecDestroy(m->graph_exec);
+  if (m->graph_stream) cudaStreamDestroy(m->graph_stream);
+}
+
+int stream_error_status(bsp_mesh* m, cudaStream_t s) {
+  CU(cudaStreamSynchronize(s));
+  int st = 0;
+  CgStats cs{};
+  CU(cudaMemcpy(&st, m->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  CU(cudaMemcpy(&cs, m->d_cgstats, sizeof(CgStats), cudaMemcpyDeviceToHost));
+  m->stats.cg_steps_total = (int64_t)cs.steps_total;
+  m->stats.cg_steps_max = cs.steps_max;
+  m->stats.not_converged = cs.not_converged;
+  if (st & ST_NUMERICAL)
+    return fail(BSP_ERR_NUMERICAL, "Gram matrix not positive definite or non-finite values");
+  if (st & ST_NOT_CONVERGED)
+    return fail(BSP_ERR_NOT_CONVERGED,
+                std::to_string(cs.not_converged) + " CG solves hit the step cap");
+  return BSP_OK;
+}
+
+// ------------------------------------------------------------------ create
+int create_common(const double* xyz, int64_t n, const int32_t* tri, int64_t m, int arity,
+                  const int32_t* block_ptr, const int32_t* block_verts, int32_t k,
+                  const int32_t* parent, const bsp_opts* opts, bsp_mesh** out) {
+  if (!out) return fail(BSP_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (n <= 0 || k <= 0 || m < 0) return fail(BSP_ERR_INVALID_ARG, "n, k must be positive");
+  if (!tri && m > 0) return fail(BSP_ERR_INVALID_ARG, "faces/edges is NULL");
+  if (!block_ptr || !block_verts || !parent)
+    return fail(BSP_ERR_INVALID_ARG, "block_ptr, block_verts and parent are required");
+  if (n > INT32_MAX / 2) return fail(BSP_ERR_INVALID_ARG, "n too large");
+  bsp_opts o;
+  bsp_opts_default(&o);
+  if (opts) o = *opts;
+  if (!(o.delta > 0.0)) return fail(BSP_ERR_INVALID_ARG, "delta must be positive");
+  if (o.z < 1) return fail(BSP_ERR_INVALID_ARG, "z must be >= 1");
+  if (o.precision < 0 || o.precision > 2) return fail(BSP_ERR_INVALID_ARG, "bad precision");
+  if (o.weight_mode < 0 || o.weight_mode > 2) return fail(BSP_ERR_INVALID_ARG, "bad weight mode");
+  if (o.weight_mode == BSP_W_INV_SQ_DIST && !xyz)
+    return fail(BSP_ERR_INVALID_ARG, "inverse-square-distance weights need xyz");
+  if (!(o.cg_rtol > 0.0)) return fail(BSP_ERR_INVALID_ARG, "cg_rtol must be positive");
+  if (o.cg_max_steps < 1) return fail(BSP_ERR_INVALID_ARG, "cg_max_steps must be >= 1");
+  if (o.cols_per_cta != 0 && o.cols_per_cta != 1 && o.cols_per_cta != 2 && o.cols_per_cta != 4 &&
+      o.cols_per_cta != 8)
+    return fail(BSP_ERR_INVALID_ARG, "cols_per_cta must be 0, 1, 2, 4 or 8");
+  configure_once();
+
+  bsp_mesh* M = new (std::nothrow) bsp_mesh();
+  if (!M) return fail(BSP_ERR_OOM, "host allocation failed");
+  M->n = n;
+  M->k = k;
+  M->opts = o;
+  M->real_bytes = o.precision == BSP_PREC_F64 ? 8 : 4;
+  int rc = BSP_OK;
+  cudaStream_t s = 0;
+  auto bail = [&](int code) {
+    release(M);
+    delete M;
+    return code;
+  };
+  // host-side validation of the partition and the block order
+  if ((rc = read_host(M->h_bptr, block_ptr, (size_t)k + 1)) != BSP_OK) return bail(rc);
+  if ((rc = read_host(M->h_parent, parent, (size_t)k)) != BSP_OK) return bail(rc);
+  if (M->h_bptr[0] != 0 || M->h_bptr[k] != n)
+    return bail(fail(BSP_ERR_INVALID_ARG, "block_ptr must start at 0 and end at n"));
+  M->max_nb = 0;
+  M->min_nb = INT32_MAX;
+  for (int b = 0; b < k; ++b) {
+    int nb = M->h_bptr[b + 1] - M->h_bptr[b];
+    if (nb <= 0) return bail(fail(BSP_ERR_INVALID_ARG, "empty or decreasing block " + std::to_string(b)));
+    if (nb > 65535) return bail(fail(BSP_ERR_INVALID_ARG, "block larger than 65535 vertices"));
+    M->max_nb = std::max(M->max_nb, nb);
+    M->min_nb = std::min(M->min_nb, nb);
+    int p = M->h_parent[b];
+    if (p >= b || p < -1)
+      return bail(fail(BSP_ERR_INVALID_ARG, "parent[" + std::to_string(b) + "] must be -1 or < b"));
+  }
+  // waves: depth in the forest
+  M->h_level.assign(k, 0);
+  M->h_root_off.assign(k, -1);
+  int levels = 0;
+  for (int b = 0; b < k; ++b) {
+    int p = M->h_parent[b];
+    M->h_level[b] = p < 0 ? 0 : M->h_level[p] + 1;
+    levels = std::max(levels, M->h_level[b] + 1);
+    if (p < 0) {
+      M->h_root_off[b] = (int32_t)M->root_rows;
+      M->root_rows += M->h_bptr[b + 1] - M->h_bptr[b];
+    }
+  }
+  M->waves.assign(levels, {});
+  for (int b = 0; b < k; ++b) M->waves[M->h_level[b]].push_back(b);
+  M->h_wave_off.assign(levels + 1, 0);
+  for (int l = 0; l < levels; ++l) {
+    M->h_wave_off[l + 1] = M->h_wave_off[l] + (int32_t)M->waves[l].size();
+    for (int b : M->waves[l]) M->h_wave_list.push_back(b);
+  }
+  // device copies of the inputs
+  int32_t* d_tri = nullptr;
+  double* d_xyz = nullptr;
+  auto dmalloc = [&](void** p, size_t bytes) {
+    if (cudaMalloc(p, bytes ? bytes : 16) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return true;
+  };
+  if (!dmalloc((void**)&M->d_bptr, sizeof(int32_t) * (k + 1)) ||
+      !dmalloc((void**)&M->d_verts, sizeof(int32_t) * n) ||
+      !dmalloc((void**)&M->d_parent, sizeof(int32_t) * k) ||
+      !dmalloc((void**)&M->d_root_off, sizeof(int32_t) * k) ||
+      !dmalloc((void**)&M->d_waves, sizeof(int32_t) * 3 * k) ||
+      !dmalloc((void**)&M->d_cb, sizeof(int32_t) * k) ||
+      !dmalloc((void**)&M->d_cpar, sizeof(int32_t) * k) ||
+      !dmalloc((void**)&M->d_ceoff, sizeof(int32_t) * (k + 1)) ||
+      !dmalloc((void**)&M->d_status, sizeof(int)) ||
+      !dmalloc((void**)&M->d_cgstats, sizeof(CgStats)) ||
+      !dmalloc((void**)&d_tri, sizeof(int32_t) * arity * (m > 0 ? m : 1)))
+    return bail(fail(BSP_ERR_OOM, "device allocation failed"));
+  auto cleanup_inputs = [&]() {
+    if (d_tri) cudaFree(d_tri);
+    if (d_xyz) cudaFree(d_xyz);
+  };
+  if ((rc = to_device(M->d_bptr, M->h_bptr.data(), sizeof(int32_t) * (k + 1), s)) ||
+      (rc = to_device(M->d_verts, block_verts, sizeof(int32_t) * n, s)) ||
+      (rc = to_device(M->d_parent, M->h_parent.data(), sizeof(int32_t) * k, s)) ||
+      (rc = to_device(M->d_root_off, M->h_root_off.data(), sizeof(int32_t) * k, s)) ||
+      (rc = to_device(M->d_waves, M->h_wave_list.data(), sizeof(int32_t) * k, s)) ||
+      (rc = to_device(d_tri, tri, sizeof(int32_t) * arity * m, s))) {
+    cleanup_inputs();
+    return bail(rc);
+  }
+  cudaMemsetAsync(M->d_status, 0, sizeof(int), s);
+  AssemblyOut ao;
+  std::string err;
+  rc = assemble_pattern(n, d_tri, m, arity, M->d_bptr, M->d_verts, k, &ao, M->d_status, s, &err);
+  M->d_rowptr = ao.rowptr;
+  M->d_col = ao.col;
+  M->d_eoff = ao.eoff;
+  M->d_blk_row = ao.blk_row;
+  if (rc != BSP_OK) {
+    cleanup_inputs();
+    return bail(fail(rc, err.empty() ? "assembly failed" : err));
+  }
+  M->nnz = ao.nnz;
+  M->intra_edges = ao.intra_edges;
+  // weights and degrees
+  const int rb = M->real_bytes;
+  if (!dmalloc(&M->d_diag, (size_t)rb * n)) {
+    cleanup_inputs();
+    return bail(fail(BSP_ERR_OOM, "device allocation failed"));
+  }
+  if (o.weight_mode != BSP_W_COMBINATORIAL) {
+    if (!dmalloc(&M->d_wt, (size_t)rb * (M->nnz > 0 ? M->nnz : 1))) {
+      cleanup_inputs();
+      return bail(fail(BSP_ERR_OOM, "device allocation failed"));
+    }
+  }
+  if (o.weight_mode == BSP_W_INV_SQ_DIST) {
+    if (!dmalloc((void**)&d_xyz, sizeof(double) * 3 * n) ||
+        to_device(d_xyz, xyz, sizeof(double) * 3 * n, s) != BSP_OK) {
+      cleanup_inputs();
+      return bail(fail(BSP_ERR_OOM, "device allocation failed"));
+    }
+  }
+  if (rb == 8)
+    launch_weights<double>(n, M->d_bptr, M->d_blk_row, M->d_verts, M->d_rowptr, M->d_col, d_xyz,
+                           o.weight_mode, o.literal_degree, (double*)M->d_wt, (double*)M->d_diag, s);
+  else
+    launch_weights<float>(n, M->d_bptr, M->d_blk_row, M->d_verts, M->d_rowptr, M->d_col, d_xyz,
+                          o.weight_mode, o.literal_degree, (float*)M->d_wt, (float*)M->d_diag, s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  cleanup_inputs();
+  if (e != cudaSuccess) return bail(fail(BSP_ERR_CUDA, cudaGetErrorString(e)));
+  M->stats.n = n;
+  M->stats.k = k;
+  M->stats.nnz = M->nnz;
+  M->stats.intra_edges = M->intra_edges;
+  M->stats.max_block = M->max_nb;
+  M->stats.levels = levels;
+  *out = M;
+  return BSP_OK;
+}
+
+// ------------------------------------------------------------------ tracking
+template <typename T>
+MeshView<T> view(const bsp_mesh* M) {
+  MeshView<T> v;
+  v.bptr = M->d_bptr;
+  v.rowptr = M->d_rowptr;
+  v.col = M->d_col;
+  v.wt = (const T*)M->d_wt;
+  v.diag = (const T*)M->d_diag;
+  return v;
+}
+
+int pick_cs(const bsp_mesh* M, int nbatch, int c, int rb) {
+  int cs = M->opts.cols_per_cta;
+  if (cs == 0) {
+    cs = 8;
+    while (cs > 1 && (int64_t)nbatch * ((c + cs - 1) / cs) * 2 <= 152) cs /= 2;
+  }
+  while (cs > 1 && (size_t)4 * M->max_nb * cs * rb > 200 * 1024) cs /= 2;
+  return cs;
+}
+
+// Workspace for `cmax` columns over batches of up to `maxbatch` blocks.
+template <typename T, typename TA>
+int ensure_workspace(bsp_mesh* M, int c_cap, int maxbatch) {
+  const int cpad = pad4(c_cap);
+  const int CH = dense_chunk_rows(cpad, (int)sizeof(T));
+  const int maxch = (M->max_nb + CH - 1) / CH;
+  const size_t gp = ((size_t)maxbatch * maxch * cpad * cpad + (size_t)maxbatch * cpad * cpad) *
+                    sizeof(TA);
+  int rc;
+  g_realloc = false;
+  if ((rc = ensure(&M->d_U, &M->cap_U, (size_t)M->n * c_cap * sizeof(T))) != BSP_OK) return rc;
+  if (!M->d_Y || M->c_cap != c_cap) {
+    g_realloc = true;
+    if (M->d_Y) cudaFree(M->d_Y);
+    M->d_Y = nullptr;
+    if (cudaMalloc(&M->d_Y, (size_t)M->n * c_cap * sizeof(T)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(BSP_ERR_OOM, "device allocation failed");
+    }
+  }
+  if ((rc = ensure(&M->d_Gp, &M->cap_Gp, gp)) != BSP_OK) return rc;
+  if ((rc = ensure(&M->d_Rsm, &M->cap_Rsm, (size_t)maxbatch * cpad * cpad * sizeof(T))) != BSP_OK)
+    return rc;
+  if ((rc = ensure(&M->d_theta, &M->cap_theta, (size_t)maxbatch * cpad * sizeof(T))) != BSP_OK)
+    return rc;
+  if ((M->c_cap != c_cap || g_realloc) && M->graph_exec) {
+    cudaGraphExecDestroy(M->graph_exec);
+    M->graph_exec = nullptr;
+  }
+  M->c_cap = c_cap;
+  return BSP_OK;
+}
+
+// Enqueue the fixed-c schedule on stream s; returns a status, counts launches.
+template <typename T, typename TA>
+int enqueue_fixed(bsp_mesh* M, int c, int t_max, cudaStream_t s, int* launches) {
+  const MeshView<T> mv = view<T>(M);
+  const int levels = (int)M->waves.size();
+  T* U = (T*)M->d_U;
+  T* Y = (T*)M->d_Y;
+  int rc;
+  for (int l = 0; l < levels; ++l) {
+    const int nbw = (int)M->waves[l].size();
+    const int32_t* batch = M->d_waves + M->h_wave_off[l];
+    int wmax = 0;
+    for (int b : M->waves[l]) wmax = std::max(wmax, M->h_bptr[b + 1] - M->h_bptr[b]);
+    launch_init_starts<T>(batch, nbw, M->d_bptr, M->d_parent, M->d_root_off, M->d_cb, M->d_cb,
+                          (const T*)M->d_starts, c, U, M->c_cap, wmax, c, s);
+    ++*launches;
+    // Onorm of the start where it is not already an orthonormal basis: roots and
+    // children whose size differs from their parent's.
+    std::vector<int32_t> need;
+    for (int b : M->waves[l]) {
+      int p = M->h_parent[b];
+      if (p < 0 || (M->h_bptr[b + 1] - M->h_bptr[b]) != (M->h_bptr[p + 1] - M->h_bptr[p]))
+        need.push_back(b);
+    }
+    DenseArgs da{batch, nbw, M->d_bptr, M->d_cb, M->c_cap, c, wmax, M->d_status};
+    if (!need.empty()) {
+      DenseArgs dn = da;
+      if ((int)need.size() != nbw) {
+        // sub-batch staged by stage_onorm_lists() in the second third of d_waves
+        dn.batch = M->d_waves + M->k + M->h_wave_off[l];
+        dn.nbatch = (int)need.size();
+      }
+      if ((rc = launch_cholqr2<T, TA>(dn, U, U, (TA*)M->d_Gp, (T*)M->d_Rsm, s, launches)))
+        return fail(rc, "launch failed (Onorm of start)");
+    }
+    CgArgs ca{batch, nbw, M->d_cb, M->c_cap, M->opts.z, M->opts.delta, M->opts.cg_rtol,
+              M->opts.cg_max_steps, M->d_status, M->d_cgstats};
+    const int cs = pick_cs(M, nbw, c, sizeof(T));
+    for (int t = 0; t < t_max; ++t) {
+      if ((rc = launch_cg<T>(mv, U, Y, ca, cs, wmax, c, s)))
+        return fail(rc, "CG launch failed (block too large for shared memory?)");
+      ++*launches;
+      if ((rc = launch_cholqr2<T, TA>(da, Y, U, (TA*)M->d_Gp, (T*)M->d_Rsm, s, launches)))
+        return fail(rc, "launch failed (Onorm)");
+    }
+    if (M->opts.rayleigh_ritz) {
+      if ((rc = launch_rayleigh_ritz<T, TA>(da, mv, U, (TA*)M->d_Gp, (T*)M->d_Rsm,
+                                            (T*)M->d_theta, s, launches)))
+        return fail(rc, "launch failed (Rayleigh-Ritz)");
+    }
+  }
+  return BSP_OK;
+}
+
+// Blocks of each wave whose start needs Onorm (roots, and children whose size
+// differs from the parent's), written to d_waves[k + wave offset ...].
+int stage_onorm_lists(bsp_mesh* M) {
+  for (int l = 0; l < (int)M->waves.size(); ++l) {
+    std::vector<int32_t> need;
+    for (int b : M->waves[l]) {
+      int p = M->h_parent[b];
+      if (p < 0 || (M->h_bptr[b + 1] - M->h_bptr[b]) != (M->h_bptr[p + 1] - M->h_bptr[p]))
+        need.push_back(b);
+    }
+    if (!need.empty() && need.size() != M->waves[l].size())
+      CU(cudaMemcpy(M->d_waves + M->k + M->h_wave_off[l], need.data(),
+                    sizeof(int32_t) * need.size(), cudaMemcpyHostToDevice));
+  }
+  return BSP_OK;
+}
+
+template <typename T, typename TA>
+int track_fixed(bsp_mesh* M, int c, int t_max, const void* V0, cudaStream_t s) {
+  if (c < 1 || c > 128) return fail(BSP_ERR_INVALID_ARG, "c must be in [1, 128]");
+  if (c > M->min_nb) return fail(BSP_ERR_INVALID_ARG, "c exceeds the smallest block size");
+  if (t_max < 0) return fail(BSP_ERR_INVALID_ARG, "t_max must be >= 0");
+  if (!V0) return fail(BSP_ERR_INVALID_ARG, "V0_roots is NULL");
+  if (sizeof(T) == 8 && c > 112) return fail(BSP_ERR_INVALID_ARG, "FP64 precision supports c <= 112");
+  int maxbatch = 0;
+  for (auto& w : M->waves) maxbatch = std::max(maxbatch, (int)w.size());
+  int rc;
+  if ((rc = ensure_workspace<T, TA>(M, c, maxbatch)) != BSP_OK) return rc;
+  g_realloc = false;
+  if ((rc = ensure(&M->d_starts, &M->cap_starts, (size_t)M->root_rows * c * sizeof(T))) != BSP_OK)
+    return rc;
+  if (g_realloc && M->graph_exec) {
+    cudaGraphExecDestroy(M->graph_exec);
+    M->graph_exec = nullptr;
+  }
+  // copy the roots' start matrices (before any graph launch)
+  if ((rc = to_device(M->d_starts, V0, (size_t)M->root_rows * c * sizeof(T), s)) != BSP_OK)
+    return rc;
+  M->h_c.assign(M->k, c);
+  std::vector<int32_t> ce(M->k + 1, 0);
+  for (int b = 0; b < M->k; ++b) ce[b + 1] = ce[b] + c;
+  CU(cudaMemcpyAsync(M->d_cb, M->h_c.data(), sizeof(int32_t) * M->k, cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(M->d_ceoff, ce.data(), sizeof(int32_t) * (M->k + 1), cudaMemcpyHostToDevice, s));
+  CU(cudaMemsetAsync(M->d_status, 0, sizeof(int), s));
+  CU(cudaMemsetAsync(M->d_cgstats, 0, sizeof(CgStats), s));
+  int launches = 0;
+  if ((rc = stage_onorm_lists(M)) != BSP_OK) return rc;
+  if (M->opts.use_graph && !M->profiling) {
+    if (!M->graph_exec || M->graph_c != c || M->graph_t != t_max) {
+      if (M->graph_exec) {
+        cudaGraphExecDestroy(M->graph_exec);
+        M->graph_exec = nullptr;
+      }
+      if (!M->graph_stream) CU(cudaStreamCreateWithFlags(&M->graph_stream, cudaStreamNonBlocking));
+      CU(cudaStreamSynchronize(s));
+      cudaGraph_t g;
+      CU(cudaStreamBeginCapture(M->graph_stream, cudaStreamCaptureModeThreadLocal));
+      rc = enqueue_fixed<T, TA>(M, c, t_max, M->graph_stream, &launches);
+      cudaError_t ce2 = cudaStreamEndCapture(M->graph_stream, &g);
+      if (rc != BSP_OK) {
+        if (ce2 == cudaSuccess) cudaGraphDestroy(g);
+        return rc;
+      }
+      if (ce2 != cudaSuccess) return fail(BSP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce2));
+      cudaError_t ie = cudaGraphInstantiate(&M->graph_exec, g, 0);
+      cudaGraphDestroy(g);
+      if (ie != cudaSuccess) return fail(BSP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
+      M->graph_c = c;
+      M->graph_t = t_max;
+      M->graph_launches = launches;
+    }
+    CU(cudaGraphLaunch(M->graph_exec, s));
+    launches = M->graph_launches;
+  } else {
+    rc = enqueue_fixed<T, TA>(M, c, t_max, s, &launches);
+    if (rc != BSP_OK) return rc;
+  }
+  M->stats.gpu_launches = launches;
+  M->tracked = true;
+  return stream_error_status(M, s);
+}
+
+template <typename T, typename TA>
+int track_dynamic(bsp_mesh* M, const void* X, double tol, int c_min, int c_max, int c_step,
+                  int t_max, uint64_t seed, const void* V0, const int32_t* forced,
+                  int32_t* c_out, cudaStream_t s) {
+  if (c_step < 8 || c_step > 8) return fail(BSP_ERR_INVALID_ARG, "c_step must be 8");
+  if (c_min < c_step || c_min % c_step || c_max % c_step || c_max < c_min || c_max > 128)
+    return fail(BSP_ERR_INVALID_ARG, "need c_step <= c_min <= c_max <= 128, multiples of c_step");
+  if (c_min > M->min_nb) return fail(BSP_ERR_INVALID_ARG, "c_min exceeds the smallest block");
+  if (!(tol > 0)) return fail(BSP_ERR_INVALID_ARG, "rel_tol must be positive");
+  if (!X || !V0) return fail(BSP_ERR_INVALID_ARG, "X and V0_roots are required");
+  if (sizeof(T) == 8 && c_max > 112) return fail(BSP_ERR_INVALID_ARG, "FP64 precision supports c <= 112");
+  int maxbatch = 0;
+  for (auto& w : M->waves) maxbatch = std::max(maxbatch, (int)w.size());
+  int rc;
+  if ((rc = ensure_workspace<T, TA>(M, c_max, maxbatch)) != BSP_OK) return rc;
+  if ((rc = ensure(&M->d_starts, &M->cap_starts, (size_t)M->root_rows * c_min * sizeof(T))) != BSP_OK)
+    return rc;
+  if ((rc = to_device(M->d_starts, V0, (size_t)M->root_rows * c_min * sizeof(T), s)) != BSP_OK)
+    return rc;
+  size_t dummy = 0;
+  if ((rc = ensure(&M->d_X, &M->cap_X, (size_t)M->n * 3 * sizeof(T))) != BSP_OK) return rc;
+  if ((rc = to_device(M->d_X, X, (size_t)M->n * 3 * sizeof(T), s)) != BSP_OK) return rc;
+  if (!M->d_action) {
+    if (cudaMalloc(&M->d_action, sizeof(int32_t) * M->k) != cudaSuccess ||
+        cudaMalloc(&M->d_round, sizeof(int32_t) * M->k) != cudaSuccess ||
+        cudaMalloc(&M->d_forced, sizeof(int32_t) * M->k) != cudaSuccess ||
+        cudaMalloc(&M->d_rho, sizeof(double) * M->k) != cudaSuccess ||
+        cudaMalloc(&M->d_gcol, sizeof(double) * M->n) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(BSP_ERR_OOM, "device allocation failed");
+    }
+  }
+  static_cast<void>(dummy);
+  const int32_t* d_forced = nullptr;
+  if (forced) {
+    if ((rc = to_device(M->d_forced, forced, sizeof(int32_t) * M->k, s)) != BSP_OK) return rc;
+    d_forced = M->d_forced;
+  }
+  CU(cudaMemsetAsync(M->d_round, 0, sizeof(int32_t) * M->k, s));
+  CU(cudaMemsetAsync(M->d_status, 0, sizeof(int), s));
+  CU(cudaMemsetAsync(M->d_cgstats, 0, sizeof(CgStats), s));
+  const MeshView<T> mv = view<T>(M);
+  T* U = (T*)M->d_U;
+  T* Y = (T*)M->d_Y;
+  const int c_cap = M->c_cap;
+  std::vector<int32_t>& hc = M->h_c;
+  hc.assign(M->k, 0);
+  std::vector<int32_t> cpar(M->k, 0), act, rounds(M->k, 0);
+  int launches = 0;
+  for (size_t l = 0; l < M->waves.size(); ++l) {
+    std::vector<int32_t> active = M->waves[l];
+    for (int b : active) {
+      int p = M->h_parent[b];
+      int nb = M->h_bptr[b + 1] - M->h_bptr[b];
+      int cmaxb = std::min(c_max, (nb / c_step) * c_step);
+      hc[b] = p < 0 ? c_min : std::min(hc[p], cmaxb);
+      cpar[b] = p < 0 ? 0 : hc[p];
+    }
+    auto upload = [&](const std::vector<int32_t>& list, int32_t* dst) -> int {
+      CU(cudaMemcpyAsync(dst, list.data(), sizeof(int32_t) * list.size(), cudaMemcpyHostToDevice, s));
+      return BSP_OK;
+    };
+    CU(cudaMemcpyAsync(M->d_cb, hc.data(), sizeof(int32_t) * M->k, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(M->d_cpar, cpar.data(), sizeof(int32_t) * M->k, cudaMemcpyHostToDevice, s));
+    int32_t* d_list = M->d_waves + 2 * M->k;  // scratch list area (last third)
+    if ((rc = upload(active, d_list))) return rc;
+    auto batch_stats = [&](const std::vector<int32_t>& list, int* wmax, int* cm) {
+      *wmax = 0;
+      *cm = 0;
+      for (int b : list) {
+        *wmax = std::max(*wmax, M->h_bptr[b + 1] - M->h_bptr[b]);
+        *cm = std::max(*cm, hc[b]);
+      }
+    };
+    int wmax, cm;
+    batch_stats(active, &wmax, &cm);
+    launch_init_starts<T>(d_list, (int)active.size(), M->d_bptr, M->d_parent, M->d_root_off,
+                          M->d_cb, M->d_cpar, (const T*)M->d_starts, c_min, U, c_cap, wmax, cm, s);
+    ++launches;
+    {
+      DenseArgs da{d_list, (int)active.size(), M->d_bptr, M->d_cb, c_cap, cm, wmax, M->d_status};
+      if ((rc = launch_cholqr2<T, TA>(da, U, U, (TA*)M->d_Gp, (T*)M->d_Rsm, s, &launches)))
+        return fail(rc, "launch failed");
+    }
+    for (int guard = 0; guard < 64 && !active.empty(); ++guard) {
+      batch_stats(active, &wmax, &cm);
+      const int nbw = (int)active.size();
+      DenseArgs da{d_list, nbw, M->d_bptr, M->d_cb, c_cap, cm, wmax, M->d_status};
+      CgArgs ca{d_list, nbw, M->d_cb, c_cap, M->opts.z, M->opts.delta, M->opts.cg_rtol,
+                M->opts.cg_max_steps, M->d_status, M->d_cgstats};
+      const int cs = pick_cs(M, nbw, cm, sizeof(T));
+      for (int t = 0; t < t_max; ++t) {
+        if ((rc = launch_cg<T>(mv, U, Y, ca, cs, wmax, cm, s))) return fail(rc, "CG launch failed");
+        ++launches;
+        if ((rc = launch_cholqr2<T, TA>(da, Y, U, (TA*)M->d_Gp, (T*)M->d_Rsm, s, &launches)))
+          return fail(rc, "launch failed");
+      }
+      if ((rc = launch_rayleigh_ritz<T, TA>(da, mv, U, (TA*)M->d_Gp, (T*)M->d_Rsm, (T*)M->d_theta,
+                                            s, &launches)))
+        return fail(rc, "launch failed");
+      if ((rc = launch_dyn_decide<T, TA>(d_list, nbw, M->d_bptr, M->d_verts, (const T*)M->d_X, U,
+                                         c_cap, M->d_cb, M->d_action, d_forced, tol, c_step,
+                                         c_max, (T*)M->d_gcol, (TA*)M->d_rho, wmax, s)))
+        return fail(rc, "launch failed");
+      ++launches;
+      act.resize(M->k);
+      CU(cudaMemcpyAsync(act.data(), M->d_action, sizeof(int32_t) * M->k, cudaMemcpyDeviceToHost, s));
+      CU(cudaMemcpyAsync(hc.data(), M->d_cb, sizeof(int32_t) * M->k, cudaMemcpyDeviceToHost, s));
+      CU(cudaStreamSynchronize(s));
+      std::vector<int32_t> grow;
+      for (int b : active) {
+        int nb = M->h_bptr[b + 1] - M->h_bptr[b];
+        int cmaxb = std::min(c_max, (nb / c_step) * c_step);
+        if (act[b] == 1 && hc[b] < cmaxb) grow.push_back(b);
+      }
+      if (grow.empty()) break;
+      if ((rc = upload(grow, d_list))) return rc;
+      CU(cudaMemcpyAsync(M->d_round, rounds.data(), sizeof(int32_t) * M->k, cudaMemcpyHostToDevice, s));
+      batch_stats(grow, &wmax, &cm);
+      if ((rc = launch_dyn_grow<T, TA>(d_list, (int)grow.size(), M->d_bptr, M->d_cb, M->d_round, U,
+                                       c_cap, (const T*)M->d_gcol, seed, c_step, wmax, s)))
+        return fail(rc, "launch failed");
+      ++launches;
+      for (int b : grow) {
+        hc[b] += c_step;
+        rounds[b] += 1;
+      }
+      DenseArgs dg{d_list, (int)grow.size(), M->d_bptr, M->d_cb, c_cap, cm + c_step, wmax,
+                   M->d_status};
+      if ((rc = launch_cholqr2<T, TA>(dg, U, U, (TA*)M->d_Gp, (T*)M->d_Rsm, s, &launches)))
+        return fail(rc, "launch failed");
+      active = grow;
+    }
+  }
+  std::vector<int32_t> ce(M->k + 1, 0);
+  for (int b = 0; b < M->k; ++b) ce[b + 1] = ce[b] + hc[b];
+  CU(cudaMemcpyAsync(M->d_ceoff, ce.data(), sizeof(int32_t) * (M->k + 1), cudaMemcpyHostToDevice, s));
+  if (c_out) {
+    if ((rc = from_device(c_out, M->d_cb, sizeof(int32_t) * M->k, s)) != BSP_OK) return rc;
+  }
+  M->stats.gpu_launches = launches;
+  M->tracked = true;
+  return stream_error_status(M, s);
+}
+
+// --------------------------------------------------------- scratch buffers
+struct Scratch {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+thread_local Scratch g_scratch[3];
+
+int scratch(int slot, size_t bytes, void** out) {
+  int rc = ensure(&g_scratch[slot].p, &g_scratch[slot].cap, bytes);
+  *out = g_scratch[slot].p;
+  return rc;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+void bsp_opts_default(bsp_opts* o) {
+  if (!o) return;
+  o->delta = 1e-2;
+  o->z = 1;
+  o->weight_mode = BSP_W_COMBINATORIAL;
+  o->literal_degree = 0;
+  o->precision = BSP_PREC_MIXED;
+  o->cg_rtol = 1e-6;
+  o->cg_max_steps = 2000;
+  o->rayleigh_ritz = 1;
+  o->cols_per_cta = 0;
+  o->use_graph = 1;
+}
+
+const char* bsp_last_error(void) { return g_err.c_str(); }
+
+int bsp_mesh_create(const double* xyz, int64_t n, const int32_t* faces, int64_t m,
+                    const int32_t* block_ptr, const int32_t* block_verts, int32_t k,
+                    const int32_t* parent, const bsp_opts* opts, bsp_mesh** out) {
+  g_err.clear();
+  return create_common(xyz, n, faces, m, 3, block_ptr, block_verts, k, parent, opts, out);
+}
+
+int bsp_mesh_create_edges(const double* xyz, int64_t n, const int32_t* edges, int64_t E,
+                          const int32_t* block_ptr, const int32_t* block_verts, int32_t k,
+                          const int32_t* parent, const bsp_opts* opts, bsp_mesh** out) {
+  g_err.clear();
+  return create_common(xyz, n, edges, E, 2, block_ptr, block_verts, k, parent, opts, out);
+}
+
+int bsp_mesh_destroy(bsp_mesh* mesh) {
+  if (!mesh) return BSP_OK;
+  cudaDeviceSynchronize();
+  release(mesh);
+  delete mesh;
+  return BSP_OK;
+}
+
+int bsp_get_stats(const bsp_mesh* mesh, bsp_stats* st) {
+  if (!mesh || !st) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
+  *st = mesh->stats;
+  return BSP_OK;
+}
+
+int bsp_get_edges(const bsp_mesh* M, int32_t* edges_out, int64_t* E_out) {
+  g_err.clear();
+  if (!M) return fail(BSP_ERR_INVALID_ARG, "mesh is NULL");
+  if (E_out) *E_out = M->intra_edges;
+  if (!edges_out) return BSP_OK;
+  void* tmp;
+  int rc = scratch(0, sizeof(int32_t) * 2 * (M->intra_edges > 0 ? M->intra_edges : 1), &tmp);
+  if (rc) return rc;
+  launch_edges_out(M->n, M->d_bptr, M->d_blk_row, M->d_verts, M->d_rowptr, M->d_col, M->d_eoff,
+                   (int32_t*)tmp, 0);
+  if ((rc = from_device(edges_out, tmp, sizeof(int32_t) * 2 * M->intra_edges, 0))) return rc;
+  CU(cudaStreamSynchronize(0));
+  return BSP_OK;
+}
+
+int bsp_get_block_csr(const bsp_mesh* M, int32_t b, int32_t* row_ptr, int32_t* cols, void* vals,
+                      void* diag, int64_t* nnz_b) {
+  g_err.clear();
+  if (!M || b < 0 || b >= M->k) return fail(BSP_ERR_INVALID_ARG, "bad mesh or block id");
+  const int r0 = M->h_bptr[b], nb = M->h_bptr[b + 1] - r0;
+  std::vector<int32_t> rp(nb + 1);
+  CU(cudaMemcpy(rp.data(), M->d_rowptr + r0, sizeof(int32_t) * (nb + 1), cudaMemcpyDeviceToHost));
+  const int64_t e0 = rp[0], ne = rp[nb] - rp[0];
+  if (nnz_b) *nnz_b = ne;
+  int rc;
+  if (row_ptr) {
+    for (auto& v : rp) v -= (int32_t)e0;
+    if (is_device_ptr(row_ptr)) CU(cudaMemcpy(row_ptr, rp.data(), sizeof(int32_t) * (nb + 1), cudaMemcpyHostToDevice));
+    else std::memcpy(row_ptr, rp.data(), sizeof(int32_t) * (nb + 1));
+  }
+  if (cols) {
+    std::vector<uint16_t> c16(ne);
+    CU(cudaMemcpy(c16.data(), M->d_col + e0, sizeof(uint16_t) * ne, cudaMemcpyDeviceToHost));
+    std::vector<int32_t> c32(c16.begin(), c16.end());
+    if (is_device_ptr(cols)) CU(cudaMemcpy(cols, c32.data(), sizeof(int32_t) * ne, cudaMemcpyHostToDevice));
+    else std::memcpy(cols, c32.data(), sizeof(int32_t) * ne);
+  }
+  const int rb = M->real_bytes;
+  if (vals) {
+    if (M->d_wt) {
+      if ((rc = from_device(vals, (const char*)M->d_wt + e0 * rb, (size_t)ne * rb, 0))) return rc;
+    } else {
+      std::vector<double> ones(ne, 1.0);
+      std::vector<float> onesf(ne, 1.0f);
+      const void* src = rb == 8 ? (const void*)ones.data() : (const void*)onesf.data();
+      if (is_device_ptr(vals)) CU(cudaMemcpy(vals, src, (size_t)ne * rb, cudaMemcpyHostToDevice));
+      else std::memcpy(vals, src, (size_t)ne * rb);
+    }
+  }
+  if (diag) {
+    if ((rc = from_device(diag, (const char*)M->d_diag + (size_t)r0 * rb, (size_t)nb * rb, 0))) return rc;
+  }
+  CU(cudaStreamSynchronize(0));
+  return BSP_OK;
+}
+
+int bsp_set_edge_weights(bsp_mesh* M, const void* w, int64_t E) {
+  g_err.clear();
+  if (!M || !w) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
+  if (M->opts.weight_mode != BSP_W_EDGE)
+    return fail(BSP_ERR_INVALID_ARG, "mesh was not created with BSP_W_EDGE");
+  if (E != M->intra_edges) return fail(BSP_ERR_INVALID_ARG, "edge count mismatch");
+  const int rb = M->real_bytes;
+  void* tmp;
+  int rc = scratch(0, (size_t)rb * (E > 0 ? E : 1), &tmp);
+  if (rc) return rc;
+  if ((rc = to_device(tmp, w, (size_t)rb * E, 0))) return rc;
+  if (rb == 8)
+    launch_set_weights<double>(M->n, M->d_bptr, M->d_blk_row, M->d_rowptr, M->d_col, M->d_eoff,
+                               (const double*)tmp, M->opts.literal_degree, (double*)M->d_wt,
+                               (double*)M->d_diag, 0);
+  else
+    launch_set_weights<float>(M->n, M->d_bptr, M->d_blk_row, M->d_rowptr, M->d_col, M->d_eoff,
+                              (const float*)tmp, M->opts.literal_degree, (float*)M->d_wt,
+                              (float*)M->d_diag, 0);
+  CU(cudaStreamSynchronize(0));
+  return BSP_OK;
+}
+
+int bsp_oi_track(bsp_mesh* M, int32_t c, int32_t t_max, const void* V0, void* stream) {
+  g_err.clear();
+  if (!M) return fail(BSP_ERR_INVALID_ARG, "mesh is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  ProfScope ps(M);
+  switch (M->opts.precision) {
+    case BSP_PREC_F64: return track_fixed<double, double>(M, c, t_max, V0, s);
+    case BSP_PREC_F32: return track_fixed<float, float>(M, c, t_max, V0, s);
+    default: return track_fixed<float, double>(M, c, t_max, V0, s);
+  }
+}
+
+int bsp_oi_track_dynamic(bsp_mesh* M, const void* X, double rel_tol, int32_t c_min,
+                         int32_t c_max, int32_t c_step, int32_t t_max, uint64_t seed,
+                         const void* V0, const int32_t* forced_c, int32_t* c_out, void* stream) {
+  g_err.clear();
+  if (!M) return fail(BSP_ERR_INVALID_ARG, "mesh is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  ProfScope ps(M);
+  switch (M->opts.precision) {
+    case BSP_PREC_F64:
+      return track_dynamic<double, double>(M, X, rel_tol, c_min, c_max, c_step, t_max, seed, V0,
+                                           forced_c, c_out, s);
+    case BSP_PREC_F32:
+      return track_dynamic<float, float>(M, X, rel_tol, c_min, c_max, c_step, t_max, seed, V0,
+                                         forced_c, c_out, s);
+    default:
+      return track_dynamic<float, double>(M, X, rel_tol, c_min, c_max, c_step, t_max, seed, V0,
+                                          forced_c, c_out, s);
+  }
+}
+
+int bsp_get_block_c(const bsp_mesh* M, int32_t* c_out) {
+  g_err.clear();
+  if (!M || !c_out) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
+  if (!M->tracked) return fail(BSP_ERR_INVALID_ARG, "no tracking call yet");
+  if (is_device_ptr(c_out)) CU(cudaMemcpy(c_out, M->h_c.data(), sizeof(int32_t) * M->k, cudaMemcpyHostToDevice));
+  else std::memcpy(c_out, M->h_c.data(), sizeof(int32_t) * M->k);
+  return BSP_OK;
+}
+
+int bsp_get_basis(const bsp_mesh* M, int32_t b, void* U, int32_t* c) {
+  g_err.clear();
+  if (!M || b < 0 || b >= M->k) return fail(BSP_ERR_INVALID_ARG, "bad mesh or block id");
+  if (!M->tracked) return fail(BSP_ERR_INVALID_ARG, "no tracking call yet");
+  const int cb = M->h_c[b];
+  if (c) *c = cb;
+  if (!U) return BSP_OK;
+  const int rb = M->real_bytes;
+  const int r0 = M->h_bptr[b], nb = M->h_bptr[b + 1] - r0;
+  cudaMemcpyKind kind = is_device_ptr(U) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CU(cudaMemcpy2D(U, (size_t)cb * rb, (const char*)M->d_U + (size_t)r0 * M->c_cap * rb,
+                  (size_t)M->c_cap * rb, (size_t)cb * rb, nb, kind));
+  return BSP_OK;
+}
+
+int bsp_project(bsp_mesh* M, const void* X, int32_t x_dtype, int32_t cols, void* E_out,
+                void* stream) {
+  g_err.clear();
+  if (!M || !X || !E_out) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
+  if (!M->tracked) return fail(BSP_ERR_INVALID_ARG, "no tracking call yet");
+  if (cols < 1) return fail(BSP_ERR_INVALID_ARG, "cols must be >= 1");
+  if (x_dtype == BSP_DT_BF16 && M->real_bytes == 8)
+    return fail(BSP_ERR_INVALID_ARG, "bf16 input needs F32 or MIXED precision");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int rb = M->real_bytes;
+  const size_t xb = x_dtype == BSP_DT_BF16 ? 2 : x_dtype == BSP_DT_F64 ? 8 : 4;
+  if (x_dtype < 0 || x_dtype > 2) return fail(BSP_ERR_INVALID_ARG, "bad x_dtype");
+  int64_t erows = 0;
+  int cmax = 0;
+  for (int b = 0; b < M->k; ++b) {
+    erows += M->h_c[b];
+    cmax = std::max(cmax, M->h_c[b]);
+  }
+  const void* dX = X;
+  int rc;
+  if (!is_device_ptr(X)) {
+    void* t;
+    if ((rc = scratch(0, (size_t)M->n * cols * xb, &t))) return rc;
+    CU(cudaMemcpyAsync(t, X, (size_t)M->n * cols * xb, cudaMemcpyHostToDevice, s));
+    dX = t;
+  }
+  void* dE = E_out;
+  const bool host_out = !is_device_ptr(E_out);
+  if (host_out && (rc = scratch(1, (size_t)erows * cols * rb, &dE))) return rc;
+  ProjArgs pa{M->d_bptr, M->d_verts, M->d_cb, M->d_ceoff, M->k, M->c_cap, cmax, M->max_nb, cols};
+  ProfScope ps(M);
+  rc = rb == 8 ? launch_project<double>(pa, (const double*)M->d_U, dX, x_dtype, (double*)dE, s)
+               : launch_project<float>(pa, (const float*)M->d_U, dX, x_dtype, (float*)dE, s);
+  if (rc) return fail(rc, "projection launch failed");
+  if (host_out) CU(cudaMemcpyAsync(E_out, dE, (size_t)erows * cols * rb, cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  M->stats.gpu_launches = 1;
+  return BSP_OK;
+}
+
+int bsp_reconstruct(bsp_mesh* M, const void* E, int32_t cols, void* X_out, void* stream) {
+  g_err.clear();
+  if (!M || !E || !X_out) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
+  if (!M->tracked) return fail(BSP_ERR_INVALID_ARG, "no tracking call yet");
+  if (cols < 1) return fail(BSP_ERR_INVALID_ARG, "cols must be >= 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int rb = M->real_bytes;
+  int64_t erows = 0;
+  int cmax = 0;
+  for (int b = 0; b < M->k; ++b) {
+    erows += M->h_c[b];
+    cmax = std::max(cmax, M->h_c[b]);
+  }
+  const void* dE = E;
+  int rc;
+  if (!is_device_ptr(E)) {
+    void* t;
+    if ((rc = scratch(1, (size_t)erows * cols * rb, &t))) return rc;
+    CU(cudaMemcpyAsync(t, E, (size_t)erows * cols * rb, cudaMemcpyHostToDevice, s));
+    dE = t;
+  }
+  void* dX = X_out;
+  const bool host_out = !is_device_ptr(X_out);
+  if (host_out && (rc = scratch(2, (size_t)M->n * cols * rb, &dX))) return rc;
+  ProjArgs pa{M->d_bptr, M->d_verts, M->d_cb, M->d_ceoff, M->k, M->c_cap, cmax, M->max_nb, cols};
+  ProfScope ps(M);
+  rc = rb == 8 ? launch_reconstruct<double>(pa, (const double*)M->d_U, (const double*)dE, (double*)dX, s)
+               : launch_reconstruct<float>(pa, (const float*)M->d_U, (const float*)dE, (float*)dX, s);
+  if (rc) return fail(rc, "reconstruction launch failed");
+  if (host_out) CU(cudaMemcpyAsync(X_out, dX, (size_t)M->n * cols * rb, cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  M->stats.gpu_launches = 1;
+  return BSP_OK;
+}
+
+int bsp_spmm(bsp_mesh* M, const void* P, void* Y, int32_t c, void* stream) {
+  g_err.clear();
+  if (!M || !P || !Y) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
+  if (c < 1 || c > 128) return fail(BSP_ERR_INVALID_ARG, "c must be in [1, 128]");
+  if (!is_device_ptr(P) || !is_device_ptr(Y))
+    return fail(BSP_ERR_INVALID_ARG, "bsp_spmm takes device pointers");
+  cudaStream_t s = (cudaStream_t)stream;
+  ProfScope ps(M);
+  if (M->real_bytes == 8)
+    launch_spmm<double>(M->n, view<double>(M), M->d_blk_row, M->opts.delta, (const double*)P,
+                        (double*)Y, c, s);
+  else
+    launch_spmm<float>(M->n, view<float>(M), M->d_blk_row, (float)M->opts.delta, (const float*)P,
+                       (float*)Y, c, s);
+  CU(cudaGetLastError());
+  M->stats.gpu_launches = 1;
+  return BSP_OK;
+}
+
+int bsp_set_profiling(bsp_mesh* M, int32_t on) {
+  g_err.clear();
+  if (!M) return fail(BSP_ERR_INVALID_ARG, "mesh is NULL");
+  M->profiling = on ? 1 : 0;
+  for (int c = 0; c < KC_COUNT; ++c) {
+    M->prof_ms[c] = 0.0;
+    M->prof_n[c] = 0;
+  }
+  return BSP_OK;
+}
+
+int bsp_get_kernel_times(const bsp_mesh* M, double* ms_out, int32_t* launches_out,
+                         int32_t n_classes) {
+  g_err.clear();
+  if (!M || n_classes < 0) return fail(BSP_ERR_INVALID_ARG, "bad argument");
+  for (int c = 0; c < n_classes && c < KC_COUNT; ++c) {
+    if (ms_out) ms_out[c] = M->prof_ms[c];
+    if (launches_out) launches_out[c] = M->prof_n[c];
+  }
+  return BSP_OK;
+}
+
+}  // extern "C"

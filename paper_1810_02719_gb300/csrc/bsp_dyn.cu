@@ -1,0 +1,320 @@
+// Start matrices for Algorithm 1 and the decision/growth steps of dynamic OI
+// (Sec. 4 warm start; Sec. 5, Algorithm 2, Eq. residual and Eq. newU).
+//
+// k_init_starts  U_b <- rows of the root start matrices, or the parent's basis
+//                with row r taken from row floor(r n_parent / n_b)
+// k_dyn_decide   one CTA per block: E = U^T X (3 columns), then for every
+//                prefix width j = c_step, 2 c_step, ... the relative residual
+//                rho(j) = ||X - U_j U_j^T X||_F / ||X||_F (direct, not Parseval);
+//                picks the smallest passing j, or asks for growth; also writes
+//                the residual e = sum over x, y, z of (X - U U^T X) for growth
+// k_dyn_grow     appends [e/||e||, counter-hash columns] projected off span(U)
+#include <cstdint>
+
+#include "bsp_internal.cuh"
+
+namespace bsp {
+namespace {
+
+constexpr int kT = 256;
+constexpr int kMaxChk = 128 / 8 + 1;   // prefix checkpoints for c_step >= 8
+constexpr int kMaxC = 128;
+
+template <typename T>
+__global__ void k_init_starts(const int32_t* batch, const int32_t* bptr, const int32_t* parent,
+                              const int32_t* root_off, const int32_t* cb, const int32_t* cpar,
+                              const T* starts, int ld_start, T* U, int ld) {
+  const int b = batch[blockIdx.y];
+  const int c = cb[b];
+  const int r0 = bptr[b], nb = bptr[b + 1] - r0;
+  const int p = parent[b];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nb * c; t += gridDim.x * blockDim.x) {
+    const int i = t / c, j = t - i * c;
+    T v;
+    if (p < 0) {
+      v = starts[(size_t)(root_off[b] + i) * ld_start + j];
+    } else {
+      const int rp0 = bptr[p], np = bptr[p + 1] - rp0;
+      const int src = (int)(((int64_t)i * np) / nb);
+      v = j < cpar[b] ? U[(size_t)(rp0 + src) * ld + j] : T(0);
+    }
+    U[(size_t)(r0 + i) * ld + j] = v;
+  }
+}
+
+// SplitMix64 output function (Steele, Lea, Flood 2014) chained over the
+// counter (seed, block, round, row, col); top 53 bits -> u in [0,1) -> 2u - 1.
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+__device__ __forceinline__ double hash_uniform(uint64_t seed, uint64_t blk, uint64_t rnd,
+                                               uint64_t row, uint64_t col) {
+  const uint64_t g = 0x9E3779B97F4A7C15ull;
+  uint64_t h = seed;
+  h = mix64(h + g * (blk + 1));
+  h = mix64(h + g * (rnd + 1));
+  h = mix64(h + g * (row + 1));
+  h = mix64(h + g * (col + 1));
+  return 2.0 * ((double)(h >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+}
+
+template <typename T, typename TA>
+BSP_DEV TA block_reduce(TA v, TA* red) {
+  v = warp_sum(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  TA s = 0;
+  for (int w = 0; w < kT / 32; ++w) s += red[w];
+  return s;
+}
+
+// action: 0 = accepted (cb[b] set to the chosen width), 1 = grow, 2 = accepted at c_max
+template <typename T, typename TA>
+__global__ void __launch_bounds__(kT) k_dyn_decide(const int32_t* batch, const int32_t* bptr,
+                                                   const int32_t* verts, const T* __restrict__ X,
+                                                   const T* __restrict__ U, int ld, int32_t* cb,
+                                                   int32_t* action, const int32_t* forced,
+                                                   double tol, int c_step, int c_max, T* gcol,
+                                                   TA* rho_out) {
+  __shared__ TA Ered[kT / 32][3 * 32];
+  __shared__ T Es[kMaxC][3];
+  __shared__ TA red[kT / 32];
+  __shared__ TA res[kMaxChk];
+  const int b = batch[blockIdx.x];
+  const int c = cb[b];
+  const int r0 = bptr[b], nb = bptr[b + 1] - r0;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  // E = U^T X: lanes own columns j = lane + 32 q, warps split the rows
+  for (int q = 0; q * 32 < c; ++q) {
+    const int j = q * 32 + lane;
+    TA e0 = 0, e1 = 0, e2 = 0;
+    T f0 = 0, f1 = 0, f2 = 0;
+    int cnt = 0;
+    for (int i = w; i < nb; i += kT / 32) {
+      const T u = j < c ? U[(size_t)(r0 + i) * ld + j] : T(0);
+      const T* x = X + (size_t)verts[r0 + i] * 3;
+      f0 += u * x[0];
+      f1 += u * x[1];
+      f2 += u * x[2];
+      if (++cnt == 32) {  // FP32 partial sums over 32 rows, accumulated in TA
+        e0 += f0; e1 += f1; e2 += f2;
+        f0 = f1 = f2 = 0;
+        cnt = 0;
+      }
+    }
+    e0 += f0; e1 += f1; e2 += f2;
+    Ered[w][3 * lane] = e0;
+    Ered[w][3 * lane + 1] = e1;
+    Ered[w][3 * lane + 2] = e2;
+    __syncthreads();
+    if (threadIdx.x < 96) {
+      TA s = 0;
+      for (int ww = 0; ww < kT / 32; ++ww) s += Ered[ww][threadIdx.x];
+      const int jj = q * 32 + threadIdx.x / 3;
+      if (jj < c) Es[jj][threadIdx.x % 3] = (T)s;
+    }
+    __syncthreads();
+  }
+  // residual norms at every checkpoint width; ||X||^2
+  const int nchk = c / c_step;
+  T acc[kMaxChk];
+#pragma unroll
+  for (int q = 0; q < kMaxChk; ++q) acc[q] = 0;
+  T xx = 0;
+  for (int i = threadIdx.x; i < nb; i += kT) {
+    const T* x = X + (size_t)verts[r0 + i] * 3;
+    const T x0 = x[0], x1 = x[1], x2 = x[2];
+    xx += x0 * x0 + x1 * x1 + x2 * x2;
+    T h0 = 0, h1 = 0, h2 = 0;
+    const T* u = U + (size_t)(r0 + i) * ld;
+    int q = 0;
+    for (int l = 0; l < c; ++l) {
+      const T ul = u[l];
+      h0 += ul * Es[l][0];
+      h1 += ul * Es[l][1];
+      h2 += ul * Es[l][2];
+      if ((l + 1) % c_step == 0) {
+        const T d0 = x0 - h0, d1 = x1 - h1, d2 = x2 - h2;
+#pragma unroll
+        for (int qq = 0; qq < kMaxChk; ++qq)
+          if (qq == q) acc[qq] += d0 * d0 + d1 * d1 + d2 * d2;
+        ++q;
+      }
+    }
+    gcol[(size_t)(r0 + i)] = (x0 - h0) + (x1 - h1) + (x2 - h2);
+  }
+  const TA xnorm2 = block_reduce<T, TA>((TA)xx, red);
+  for (int q = 0; q < nchk; ++q) {
+    TA v = block_reduce<T, TA>((TA)acc[q], red);
+    if (threadIdx.x == 0) res[q] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int fc = forced ? forced[b] : -1;
+    int act = 1, cj = c;
+    TA rho = 0;
+    if (fc >= 0) {
+      if (fc <= c || c >= c_max) {
+        cj = fc < c ? fc : c;
+        act = 0;
+        const int q = cj / c_step - 1;
+        rho = (q >= 0 && xnorm2 > 0) ? sqrt(res[q] / xnorm2) : TA(0);
+      }
+    } else {
+      for (int q = 0; q < nchk; ++q) {
+        TA r = xnorm2 > 0 ? sqrt(res[q] / xnorm2) : TA(0);
+        if (r <= (TA)tol) {
+          act = 0;
+          cj = (q + 1) * c_step;
+          rho = r;
+          break;
+        }
+        rho = r;
+      }
+      if (act == 1 && c >= c_max) act = 2;
+    }
+    action[b] = act;
+    if (act == 0) cb[b] = cj;
+    rho_out[b] = rho;
+  }
+}
+
+// Append c_step columns at position c = cb[b]: [e/||e||, hash columns], all
+// projected off the current basis U[:, :c] (one classical Gram-Schmidt sweep;
+// the Onorm that follows re-orthonormalises).  Updates cb[b] += c_step.
+template <typename T, typename TA>
+__global__ void __launch_bounds__(kT) k_dyn_grow(const int32_t* batch, const int32_t* bptr,
+                                                 int32_t* cb, const int32_t* round, T* U, int ld,
+                                                 const T* __restrict__ gcol, uint64_t seed,
+                                                 int c_step) {
+  __shared__ TA red[kT / 32];
+  __shared__ T Cm[kMaxC][8];              // U^T G, c x c_step (c_step <= 8)
+  __shared__ T part[kT / 32][32 * 8];     // per-warp partial products (one 32-column slice)
+  const int b = batch[blockIdx.x];
+  const int c = cb[b];
+  const int r0 = bptr[b], nb = bptr[b + 1] - r0;
+  const int rnd = round[b];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  // ||e||
+  T ee = 0;
+  for (int i = threadIdx.x; i < nb; i += kT) {
+    const T e = gcol[r0 + i];
+    ee += e * e;
+  }
+  const TA en = sqrt(block_reduce<T, TA>((TA)ee, red));
+  const T inv = en > 0 ? (T)(1.0 / (double)en) : T(0);
+  // write the raw growth block into columns [c, c + c_step)
+  for (int t = threadIdx.x; t < nb * c_step; t += kT) {
+    const int i = t / c_step, g = t - i * c_step;
+    T v = g == 0 ? gcol[r0 + i] * inv
+                 : (T)hash_uniform(seed, (uint64_t)b, (uint64_t)rnd, (uint64_t)i, (uint64_t)g);
+    U[(size_t)(r0 + i) * ld + c + g] = v;
+  }
+  __syncthreads();
+  // Cm = U[:, :c]^T G, 32 columns of U at a time
+  for (int q = 0; q * 32 < c; ++q) {
+    const int j = q * 32 + lane;
+    T a[8];
+#pragma unroll
+    for (int g = 0; g < 8; ++g) a[g] = 0;
+    for (int i = w; i < nb; i += kT / 32) {
+      const T* row = U + (size_t)(r0 + i) * ld;
+      const T u = j < c ? row[j] : T(0);
+#pragma unroll
+      for (int g = 0; g < 8; ++g)
+        if (g < c_step) a[g] += u * row[c + g];
+    }
+#pragma unroll
+    for (int g = 0; g < 8; ++g) part[w][lane * 8 + g] = a[g];
+    __syncthreads();
+    for (int t = threadIdx.x; t < 32 * 8; t += kT) {
+      T s = 0;
+      for (int ww = 0; ww < kT / 32; ++ww) s += part[ww][t];
+      const int jj = q * 32 + t / 8;
+      if (jj < c) Cm[jj][t % 8] = s;
+    }
+    __syncthreads();
+  }
+  // G -= U[:, :c] Cm
+  for (int t = threadIdx.x; t < nb * c_step; t += kT) {
+    const int i = t / c_step, g = t - i * c_step;
+    T* row = U + (size_t)(r0 + i) * ld;
+    T s = row[c + g];
+    for (int l = 0; l < c; ++l) s -= row[l] * Cm[l][g];
+    row[c + g] = s;
+  }
+  if (threadIdx.x == 0) cb[b] = c + c_step;
+}
+
+}  // namespace
+
+template <typename T>
+void launch_init_starts(const int32_t* batch, int nbatch, const int32_t* bptr,
+                        const int32_t* parent, const int32_t* root_off, const int32_t* cb,
+                        const int32_t* cpar, const T* starts, int ld_start, T* U, int ld,
+                        int max_nb, int cmax, cudaStream_t s) {
+  const int per = max_nb * cmax;
+  dim3 grid((per + 255) / 256 < 64 ? (per + 255) / 256 : 64, nbatch);
+  prof_begin(KC_INIT, s);
+  k_init_starts<T><<<grid, 256, 0, s>>>(batch, bptr, parent, root_off, cb, cpar, starts, ld_start,
+                                        U, ld);
+  prof_end(KC_INIT, s);
+}
+
+template <typename T, typename TA>
+int launch_dyn_decide(const int32_t* batch, int nbatch, const int32_t* bptr, const int32_t* verts,
+                      const T* X, const T* U, int ld, int32_t* cb, int32_t* action,
+                      const int32_t* forced, double tol, int c_step, int c_max, T* gcol,
+                      TA* rho_out, int max_nb, cudaStream_t s) {
+  if (c_step < 8 || c_max > kMaxC) return BSP_ERR_INVALID_ARG;
+  prof_begin(KC_DYN, s);
+  k_dyn_decide<T, TA><<<nbatch, kT, 0, s>>>(batch, bptr, verts, X, U, ld, cb, action, forced, tol,
+                                            c_step, c_max, gcol, rho_out);
+  prof_end(KC_DYN, s);
+  return cudaGetLastError() == cudaSuccess ? BSP_OK : BSP_ERR_CUDA;
+}
+
+template <typename T, typename TA>
+int launch_dyn_grow(const int32_t* batch, int nbatch, const int32_t* bptr, int32_t* cb,
+                    const int32_t* round, T* U, int ld, const T* gcol, uint64_t seed,
+                    int c_step, int max_nb, cudaStream_t s) {
+  if (c_step > 8) return BSP_ERR_INVALID_ARG;
+  prof_begin(KC_DYN, s);
+  k_dyn_grow<T, TA><<<nbatch, kT, 0, s>>>(batch, bptr, cb, round, U, ld, gcol, seed, c_step);
+  prof_end(KC_DYN, s);
+  return cudaGetLastError() == cudaSuccess ? BSP_OK : BSP_ERR_CUDA;
+}
+
+template void launch_init_starts<float>(const int32_t*, int, const int32_t*, const int32_t*,
+                                        const int32_t*, const int32_t*, const int32_t*,
+                                        const float*, int, float*, int, int, int, cudaStream_t);
+template void launch_init_starts<double>(const int32_t*, int, const int32_t*, const int32_t*,
+                                         const int32_t*, const int32_t*, const int32_t*,
+                                         const double*, int, double*, int, int, int,
+                                         cudaStream_t);
+template int launch_dyn_decide<float, double>(const int32_t*, int, const int32_t*, const int32_t*,
+                                              const float*, const float*, int, int32_t*, int32_t*,
+                                              const int32_t*, double, int, int, float*, double*,
+                                              int, cudaStream_t);
+template int launch_dyn_decide<float, float>(const int32_t*, int, const int32_t*, const int32_t*,
+                                             const float*, const float*, int, int32_t*, int32_t*,
+                                             const int32_t*, double, int, int, float*, float*, int,
+                                             cudaStream_t);
+template int launch_dyn_decide<double, double>(const int32_t*, int, const int32_t*,
+                                               const int32_t*, const double*, const double*, int,
+                                               int32_t*, int32_t*, const int32_t*, double, int,
+                                               int, double*, double*, int, cudaStream_t);
+template int launch_dyn_grow<float, double>(const int32_t*, int, const int32_t*, int32_t*,
+                                            const int32_t*, float*, int, const float*, uint64_t,
+                                            int, int, cudaStream_t);
+template int launch_dyn_grow<float, float>(const int32_t*, int, const int32_t*, int32_t*,
+                                           const int32_t*, float*, int, const float*, uint64_t,
+                                           int, int, cudaStream_t);
+template int launch_dyn_grow<double, double>(const int32_t*, int, const int32_t*, int32_t*,
+                                             const int32_t*, double*, int, const double*, uint64_t,
+                                             int, int, cudaStream_t);
+
+}  // namespace bsp

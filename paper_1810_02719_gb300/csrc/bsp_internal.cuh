@@ -1,0 +1,239 @@
+// Internal declarations shared by the library's translation units.
+//
+// Device data layout ("block order"): the rows of every per-vertex array are
+// the blocks' vertices concatenated, block b occupying rows
+// [bptr[b], bptr[b+1]) in its local order.  Per-block CSR of the off-diagonal
+// part of L[b] = D - C (Sec. 3): rowptr (global offsets, int32 [n+1]),
+// col (uint16 local column ids, ascending per row), wt (real per entry, or
+// null for unit weights), diag (real D_ii per row).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/bsp.h"
+
+namespace bsp {
+
+// ---------------------------------------------------------------- status bits
+// Device-side status word (OR-ed by kernels, read by the host after a call).
+enum : int {
+  ST_NUMERICAL = 1 << 0,      // Gram/Cholesky breakdown or NaN
+  ST_NOT_CONVERGED = 1 << 1,  // a CG solve hit its step cap
+  ST_BAD_INDEX = 1 << 2,      // assembly saw an out-of-range vertex id
+  ST_DUP_VERTEX = 1 << 3,     // assembly saw a vertex in two blocks
+  ST_DEGREE = 1 << 4,         // a row's neighbour list overflowed
+};
+
+struct CgStats {
+  unsigned long long steps_total;
+  int steps_max;
+  int not_converged;
+};
+
+// ---------------------------------------------------------------- profiling
+// Kernel classes for the optional per-class timing (CUDA events recorded on
+// the launching stream around every launch, eager mode only).
+enum KernelClass : int {
+  KC_INIT = 0, KC_CG, KC_GRAM, KC_REDUCE, KC_CHOL, KC_PANEL, KC_RR, KC_JACOBI,
+  KC_PROJECT, KC_RECON, KC_SPMM, KC_DYN, KC_COUNT
+};
+struct Profiler {
+  std::vector<cudaEvent_t> ev[KC_COUNT];  // pairs (start, stop)
+};
+extern thread_local Profiler* g_prof;
+inline void prof_begin(int cls, cudaStream_t s) {
+  if (!g_prof) return;
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  cudaEventRecord(e, s);
+  g_prof->ev[cls].push_back(e);
+}
+inline void prof_end(int cls, cudaStream_t s) {
+  if (!g_prof) return;
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  cudaEventRecord(e, s);
+  g_prof->ev[cls].push_back(e);
+}
+
+// ---------------------------------------------------------------- helpers
+#define BSP_DEV __device__ __forceinline__
+
+template <typename T>
+BSP_DEV T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// Let `kernel` use all the opt-in shared memory left next to its static shared
+// memory.  Leaves no error behind in the runtime's last-error state.
+template <typename K>
+inline void set_max_dynamic_smem(K kernel) {
+  cudaFuncAttributes fa;
+  int dev = 0, optin = 0;
+  if (cudaFuncGetAttributes(&fa, kernel) == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess &&
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess)
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         optin - (int)fa.sharedSizeBytes);
+  cudaGetLastError();
+}
+
+// Thin tuple of the device-side mesh arrays passed to kernels by value.
+template <typename T>
+struct MeshView {
+  const int32_t* bptr;     // [k+1]
+  const int32_t* rowptr;   // [n+1]
+  const uint16_t* col;     // [nnz]
+  const T* wt;             // [nnz] or nullptr (unit weights)
+  const T* diag;           // [n]
+};
+
+// ---------------------------------------------------------------- launchers
+// Assembly (bsp_assemble.cu)
+struct AssemblyOut {
+  int32_t* rowptr = nullptr;
+  uint16_t* col = nullptr;
+  int32_t* eoff = nullptr;      // [n+1] canonical edge id offset per row
+  int32_t* blk_row = nullptr;   // [n] block of each row
+  int64_t nnz = 0;
+  int64_t intra_edges = 0;
+};
+// Returns a bsp_status; fills `out` with device arrays owned by the caller.
+int assemble_pattern(int64_t n, const int32_t* d_tri, int64_t m, int arity,
+                     const int32_t* d_bptr, const int32_t* d_verts, int32_t k,
+                     AssemblyOut* out, int* d_status, cudaStream_t s, std::string* err);
+template <typename T>
+void launch_weights(int64_t n, const int32_t* bptr, const int32_t* blk_row, const int32_t* verts,
+                    const int32_t* rowptr, const uint16_t* col, const double* xyz, int mode,
+                    int literal, T* wt, T* diag, cudaStream_t s);
+template <typename T>
+void launch_set_weights(int64_t n, const int32_t* bptr, const int32_t* blk_row,
+                        const int32_t* rowptr, const uint16_t* col, const int32_t* eoff,
+                        const T* w_edges, int literal, T* wt, T* diag, cudaStream_t s);
+void launch_edges_out(int64_t n, const int32_t* bptr, const int32_t* blk_row, const int32_t* verts,
+                      const int32_t* rowptr, const uint16_t* col, const int32_t* eoff,
+                      int32_t* edges, cudaStream_t s);
+
+// Standalone SpMM (bsp_cg.cu)
+template <typename T>
+void launch_spmm(int64_t n, const MeshView<T>& mv, const int32_t* blk_row, T delta, const T* P,
+                 T* Y, int c, cudaStream_t s);
+
+// Fused CG solve of (L + delta I)^z Y = V per (block, column slab) (bsp_cg.cu)
+struct CgArgs {
+  const int32_t* batch; int nbatch;
+  const int32_t* cb;        // [k] columns per block
+  int ld;                   // row stride of V and Y
+  int z; double delta; double rtol; int max_steps;
+  int* status; CgStats* stats;
+};
+template <typename T>
+int launch_cg(const MeshView<T>& mv, const T* V, T* Y, const CgArgs& a, int cs, int max_nb,
+              int c_max, cudaStream_t s);
+template <typename T>
+int cg_smem_bytes(int cs, int max_nb);
+void configure_cg_kernels();
+void configure_dense_kernels();
+
+// Dense small-matrix kernels (bsp_dense.cu)
+struct DenseArgs {
+  const int32_t* batch; int nbatch;
+  const int32_t* bptr;
+  const int32_t* cb;        // [k] columns per block
+  int ld;                   // row stride of the n x c_cap matrices
+  int cmax;                 // largest c in the batch (grid sizing)
+  int max_nb;               // largest n_b in the batch
+  int* status;
+};
+template <typename T, typename TA>
+int launch_cholqr2(const DenseArgs& a, const T* Y, T* Q, TA* Gp, T* Rsm, cudaStream_t s,
+                   int* launches);
+template <typename T, typename TA>
+int launch_rayleigh_ritz(const DenseArgs& a, const MeshView<T>& mv, T* V, TA* Gp, T* Rsm,
+                         T* theta, cudaStream_t s, int* launches);
+int dense_chunk_rows(int cpad, int real_bytes);
+
+// Projection / reconstruction (bsp_proj.cu)
+struct ProjArgs {
+  const int32_t* bptr; const int32_t* verts; const int32_t* cb; const int32_t* eoff;
+  int k; int ld; int cmax; int max_nb; int cols;
+};
+template <typename T>
+int launch_project(const ProjArgs& a, const T* U, const void* X, int x_dtype, T* E,
+                   cudaStream_t s);
+template <typename T>
+int launch_reconstruct(const ProjArgs& a, const T* U, const T* E, T* X, cudaStream_t s);
+
+// Start matrices and dynamic-c helpers (bsp_dyn.cu)
+template <typename T>
+void launch_init_starts(const int32_t* batch, int nbatch, const int32_t* bptr,
+                        const int32_t* parent, const int32_t* root_off, const int32_t* cb,
+                        const int32_t* cpar, const T* starts, int ld_start, T* U, int ld,
+                        int max_nb, int cmax, cudaStream_t s);
+template <typename T, typename TA>
+int launch_dyn_decide(const int32_t* batch, int nbatch, const int32_t* bptr, const int32_t* verts,
+                      const T* X, const T* U, int ld, int32_t* cb, int32_t* action,
+                      const int32_t* forced, double tol, int c_step, int c_max, T* gcol,
+                      TA* rho_out, int max_nb, cudaStream_t s);
+template <typename T, typename TA>
+int launch_dyn_grow(const int32_t* batch, int nbatch, const int32_t* bptr, int32_t* cb,
+                    const int32_t* round, T* U, int ld, const T* gcol, uint64_t seed,
+                    int c_step, int max_nb, cudaStream_t s);
+
+}  // namespace bsp
+
+// ---------------------------------------------------------------- the mesh
+struct bsp_mesh {
+  int64_t n = 0;
+  int32_t k = 0;
+  bsp_opts opts{};
+  int real_bytes = 4;
+  int32_t max_nb = 0, min_nb = 0;
+  int64_t nnz = 0, intra_edges = 0;
+  std::vector<int32_t> h_bptr, h_parent, h_level, h_root_off, h_c;
+  std::vector<std::vector<int32_t>> waves;
+  std::vector<int32_t> h_wave_list;      // all waves concatenated
+  std::vector<int32_t> h_wave_off;       // [levels+1]
+  int64_t root_rows = 0;
+  // device arrays
+  int32_t *d_bptr = nullptr, *d_verts = nullptr, *d_rowptr = nullptr, *d_eoff = nullptr,
+          *d_blk_row = nullptr, *d_parent = nullptr, *d_root_off = nullptr,
+          *d_waves = nullptr, *d_cb = nullptr, *d_cpar = nullptr, *d_ceoff = nullptr;
+  uint16_t* d_col = nullptr;
+  void* d_wt = nullptr;
+  void* d_diag = nullptr;
+  int* d_status = nullptr;
+  bsp::CgStats* d_cgstats = nullptr;
+  // tracking state and workspace
+  int32_t c_cap = 0;       // row stride (columns) of d_U / d_Y
+  bool tracked = false;
+  void* d_U = nullptr;
+  void* d_Y = nullptr;
+  void* d_starts = nullptr;
+  void* d_Gp = nullptr;
+  void* d_Rsm = nullptr;
+  void* d_theta = nullptr;
+  size_t cap_U = 0, cap_starts = 0, cap_Gp = 0, cap_Rsm = 0, cap_theta = 0;
+  // dynamic-c workspace
+  int32_t *d_action = nullptr, *d_round = nullptr, *d_forced = nullptr;
+  void* d_gcol = nullptr;
+  void* d_rho = nullptr;
+  void* d_X = nullptr;
+  size_t cap_X = 0;
+  // graph cache for the fixed-c schedule
+  cudaGraphExec_t graph_exec = nullptr;
+  int graph_c = -1, graph_t = -1, graph_launches = 0;
+  cudaStream_t graph_stream = nullptr;
+  bsp_stats stats{};
+  // optional per-kernel-class timing (eager launches, CUDA events)
+  int profiling = 0;
+  double prof_ms[bsp::KC_COUNT] = {};
+  int32_t prof_n[bsp::KC_COUNT] = {};
+};

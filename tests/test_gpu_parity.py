@@ -1,0 +1,386 @@
+"""GPU path vs the FP64 oracle, through the C ABI (libbsp.so).
+
+Bases are compared as subspaces (principal-angle sines) and through the
+projector U U^T x (reconstruction), never as raw vectors: signs and rotations
+inside a subspace are free.  Tolerances:
+  * FP64 path: sines <= 1e-8, projector relative error <= 1e-10.
+  * FP32/mixed path: sines <= 1e-4 and projector relative error <= 1e-5 per block.
+  * integer work (assembly, edge order, dynamic c): exact.
+"""
+import numpy as np
+import pytest
+
+from oracle import bsp_oracle as O
+from paper_1810_02719_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1810_02719_gb300 import bsp  # noqa: E402
+
+SINE_F32, PROJ_F32 = 1e-4, 1e-5
+SINE_F64, PROJ_F64 = 1e-8, 1e-10
+
+
+def make_tile_mesh(N, T, kind="grid", seed=0, prec=bsp.BSP_PREC_MIXED, mode=bsp.BSP_W_COMBINATORIAL,
+                   **kw):
+    if kind == "grid":
+        xyz, faces = synth.grid_heightfield(N, seed=seed)
+    else:
+        xyz, faces = synth.torus(N, seed=seed)
+    ptr, verts = synth.tile_partition(N, T)
+    parent = synth.raster_chain(len(ptr) - 1)
+    opts = bsp.make_opts(precision=prec, weight_mode=mode, **kw)
+    h = bsp.bsp_mesh_create(xyz, faces, ptr, verts, parent, opts)
+    om = O.build_mesh(N * N, ptr, verts, parent, faces=faces, xyz=xyz,
+                      weight_mode={0: O.WEIGHT_COMBINATORIAL, 1: O.WEIGHT_EDGE,
+                                   2: O.WEIGHT_INV_SQ_DIST}[mode],
+                      literal_degree=bool(kw.get("literal_degree", 0)))
+    return h, om, xyz, faces, ptr, verts, parent
+
+
+def compare_bases(h, om, U_ref, xyz, real, sine_tol, proj_tol):
+    worst_s, worst_p = 0.0, 0.0
+    for b, blk in enumerate(om.blocks):
+        U = bsp.bsp_get_basis(h, b, blk.verts.size, real).astype(np.float64)
+        s = O.max_sine(U, U_ref[b])
+        p = O.projector_rel_error(U, U_ref[b], xyz[blk.verts])
+        worst_s, worst_p = max(worst_s, s), max(worst_p, p)
+    assert worst_s <= sine_tol, worst_s
+    assert worst_p <= proj_tol, worst_p
+    return worst_s, worst_p
+
+
+# ---------------------------------------------------------------- assembly
+
+@pytest.mark.parametrize("mode", [bsp.BSP_W_COMBINATORIAL, bsp.BSP_W_INV_SQ_DIST])
+def test_assembly_matches_definition(mode):
+    h, om, *_ = make_tile_mesh(48, 16, mode=mode, prec=bsp.BSP_PREC_F64)
+    try:
+        for b, blk in enumerate(om.blocks):
+            rp, cols, vals, diag = bsp.bsp_get_block_csr(h, b, blk.verts.size, np.float64)
+            rp0, cols0, vals0, diag0 = O.csr_pattern(blk)
+            assert np.array_equal(rp, rp0) and np.array_equal(cols, cols0)
+            np.testing.assert_allclose(vals, vals0, rtol=1e-12)
+            np.testing.assert_allclose(diag, diag0, rtol=1e-12)
+        st = bsp.bsp_get_stats(h)
+        assert st["intra_edges"] == sum(b.edges.shape[0] for b in om.blocks)
+    finally:
+        bsp.bsp_mesh_destroy(h)
+
+
+def test_edge_order_and_literal_degree_and_uneven_blocks():
+    N = 40
+    xyz, faces = synth.torus(N, seed=3)
+    ptr, verts = synth.bfs_partition(N, target_blocks=12, min_size=60, max_size=300, seed=1)
+    ptr, verts, parent = synth.block_forest(ptr, verts, N, roots=2, seed=2)
+    opts = bsp.make_opts(precision=bsp.BSP_PREC_F64, literal_degree=1,
+                         weight_mode=bsp.BSP_W_INV_SQ_DIST)
+    h = bsp.bsp_mesh_create(xyz, faces, ptr, verts, parent, opts)
+    om = O.build_mesh(N * N, ptr, verts, parent, faces=faces, xyz=xyz,
+                      weight_mode=O.WEIGHT_INV_SQ_DIST, literal_degree=True)
+    try:
+        E = bsp.bsp_get_edges(h)
+        ref = np.concatenate([b.verts[b.edges] for b in om.blocks])
+        assert np.array_equal(E, ref)
+        for b, blk in enumerate(om.blocks):
+            rp, cols, vals, diag = bsp.bsp_get_block_csr(h, b, blk.verts.size, np.float64)
+            _, cols0, vals0, diag0 = O.csr_pattern(blk, literal_degree=True)
+            assert np.array_equal(cols, cols0)
+            np.testing.assert_allclose(diag, diag0, rtol=0)
+            np.testing.assert_allclose(vals, vals0, rtol=1e-12)
+    finally:
+        bsp.bsp_mesh_destroy(h)
+
+
+def test_edge_list_graphs_path_cycle():
+    # path (2 blocks) and cycle (1 block) through the edge-list entry point
+    n = 20
+    e = np.concatenate([synth.path_edges(n), synth.cycle_edges(n) + n])
+    ptr = np.array([0, 10, 20, 40])
+    verts = np.arange(2 * n)
+    parent = np.array([-1, -1, -1])
+    h = bsp.bsp_mesh_create_edges(None, e, ptr, verts, parent,
+                                  bsp.make_opts(precision=bsp.BSP_PREC_F64))
+    om = O.build_mesh(2 * n, ptr, verts, parent, edges=e)
+    try:
+        for b, blk in enumerate(om.blocks):
+            rp, cols, vals, diag = bsp.bsp_get_block_csr(h, b, blk.verts.size, np.float64)
+            rp0, cols0, _, diag0 = O.csr_pattern(blk)
+            assert np.array_equal(rp, rp0) and np.array_equal(cols, cols0)
+            assert np.array_equal(diag, diag0)
+    finally:
+        bsp.bsp_mesh_destroy(h)
+
+
+# ---------------------------------------------------------------- operator
+
+@pytest.mark.parametrize("prec,c", [(bsp.BSP_PREC_MIXED, 64), (bsp.BSP_PREC_MIXED, 12),
+                                    (bsp.BSP_PREC_F64, 16), (bsp.BSP_PREC_MIXED, 7)])
+def test_spmm_matches_dense_operator(prec, c):
+    h, om, *_ = make_tile_mesh(64, 32, kind="torus", prec=prec)
+    real = np.float64 if prec == bsp.BSP_PREC_F64 else np.float32
+    tdt = torch.float64 if prec == bsp.BSP_PREC_F64 else torch.float32
+    try:
+        rng = np.random.default_rng(0)
+        P = rng.standard_normal((64 * 64, c))
+        Pd = torch.tensor(P, dtype=tdt, device="cuda")
+        Yd = torch.empty_like(Pd)
+        bsp.bsp_spmm(h, Pd, Yd, c)
+        torch.cuda.synchronize()
+        Y = Yd.cpu().double().numpy()
+        for b, blk in enumerate(om.blocks):
+            rows = slice(b * 1024, (b + 1) * 1024)
+            A = O.laplacian(blk) + 1e-2 * np.eye(1024)
+            ref = A @ P[rows].astype(real).astype(np.float64)
+            err = np.abs(Y[rows] - ref).max() / np.abs(ref).max()
+            assert err <= (1e-12 if real == np.float64 else 2e-6), err
+    finally:
+        bsp.bsp_mesh_destroy(h)
+
+
+# ---------------------------------------------------------------- fixed-c OI
+
+def test_fixed_c_fp64_grid_blocks():
+    """64x64 height field, 16 tiles of 16x16, c=12, 3 OI steps, FP64 path."""
+    h, om, xyz, *_ , ptr, verts, parent = make_tile_mesh(64, 16, prec=bsp.BSP_PREC_F64,
+                                                         cg_rtol=1e-13)
+    try:
+        starts = synth.gaussian_starts(ptr, parent, 12, seed=0)
+        bsp.bsp_oi_track(h, 12, 3, starts)
+        U_ref = O.oi_track(om, 12, 3, starts, delta=1e-2)
+        compare_bases(h, om, U_ref, xyz, np.float64, SINE_F64, PROJ_F64)
+        # reconstruction through the ABI vs the oracle's decoder
+        E = np.empty((16 * 12, 3))
+        bsp.bsp_project(h, xyz, bsp.BSP_DT_F64, 3, E)
+        Xh = np.empty_like(xyz)
+        bsp.bsp_reconstruct(h, E, 3, Xh)
+        Xr = O.reconstruct(om, U_ref, O.project(om, U_ref, xyz), 3)
+        assert np.abs(Xh - Xr).max() <= 1e-10 * np.abs(Xr).max()
+    finally:
+        bsp.bsp_mesh_destroy(h)
+
+
+@pytest.mark.parametrize("prec", [bsp.BSP_PREC_MIXED, bsp.BSP_PREC_F32])
+@pytest.mark.parametrize("cs", [0, 8])
+def test_fixed_c_fp32_torus_tiles(prec, cs):
+    """128x128 torus, 16 tiles of 32x32 (several column slabs, chain of 16), c=64, 2 steps."""
+    h, om, xyz, *_ , ptr, verts, parent = make_tile_mesh(128, 32, kind="torus", prec=prec,
+                                                         cols_per_cta=cs)
+    try:
+        starts = synth.gaussian_starts(ptr, parent, 64, seed=1)
+        bsp.bsp_oi_track(h, 64, 2, starts.astype(np.float32))
+        U_ref = O.oi_track(om, 64, 2, starts, delta=1e-2)
+        compare_bases(h, om, U_ref, xyz, np.float32, SINE_F32, PROJ_F32)
+        # device-resident projection + reconstruction with torch buffers
+        Xd = torch.tensor(xyz, dtype=torch.float32, device="cuda")
+        Ed = torch.empty((16 * 64, 3), dtype=torch.float32, device="cuda")
+        Xo = torch.empty_like(Xd)
+        bsp.bsp_project(h, Xd, bsp.BSP_DT_F32, 3, Ed)
+        bsp.bsp_reconstruct(h, Ed, 3, Xo)
+        Xr = O.reconstruct(om, U_ref, O.project(om, U_ref, xyz), 3)
+        err = np.linalg.norm(Xo.cpu().double().numpy() - Xr) / np.linalg.norm(Xr)
+        assert err <= PROJ_F32, err
+    finally:
+        bsp.bsp_mesh_destroy(h)
+
+
+def test_graph_replay_is_deterministic():
+    h, om, xyz, *_ , ptr, verts, parent = make_tile_mesh(64, 32, kind="torus")
+    try:
+        starts = synth.gaussian_starts(ptr, parent, 48, seed=2).astype(np.float32)
+        bsp.bsp_oi_track(h, 48, 2, starts)
+        U1 = bsp.bsp_get_basis(h, 3, 1024)
+        bsp.bsp_oi_track(h, 48, 2, starts)       # cached graph
+        U2 = bsp.bsp_get_basis(h, 3, 1024)
+        assert np.array_equal(U1, U2)
+    finally:
+        bsp.bsp_mesh_destroy(h)
+
+
+def test_uneven_blocks_forest_rowtransfer_z2():
+    """BFS blocks of different sizes, two roots, row transfer, z = 2, no RR."""
+    N = 40
+    xyz, faces = synth.torus(N, seed=4)
+    ptr, verts = synth.bfs_partition(N, target_blocks=10, min_size=80, max_size=400, seed=3)
+    ptr, verts, parent = synth.block_forest(ptr, verts, N, roots=2, seed=5)
+    sizes = np.diff(ptr)
+    assert len(set(sizes.tolist())) > 1
+    opts = bsp.make_opts(precision=bsp.BSP_PREC_F64, z=2, rayleigh_ritz=0, cg_rtol=1e-13)
+    h = bsp.bsp_mesh_create(xyz, faces, ptr, verts, parent, opts)
+    om = O.build_mesh(N * N, ptr, verts, parent, faces=faces)
+    try:
+        c = 20
+        starts = synth.gaussian_starts(ptr, parent, c, seed=6)
+        bsp.bsp_oi_track(h, c, 2, starts)
+        U_ref = O.oi_track(om, c, 2, starts, delta=1e-2, z=2, rr=False)
+        compare_bases(h, om, U_ref, xyz, np.float64, SINE_F64, PROJ_F64)
+        assert bsp.bsp_get_stats(h)["levels"] > 1
+    finally:
+        bsp.bsp_mesh_destroy(h)
+
+
+def test_full_width_reconstructs_and_c1_gives_centroid():
+    N = 16
+    xyz, faces = synth.grid_heightfield(N, seed=7)
+    ptr, verts = synth.tile_partition(N, 8)
+    parent = synth.raster_chain(4)
+    for prec, real, tol in [(bsp.BSP_PREC_F64, np.float64, 1e-10),
+                            (bsp.BSP_PREC_MIXED, np.float32, 1e-5)]:
+        h = bsp.bsp_mesh_create(xyz, faces, ptr, verts, parent, bsp.make_opts(precision=prec))
+        try:
+            starts = synth.gaussian_starts(ptr, parent, 64, seed=8).astype(real)
+            bsp.bsp_oi_track(h, 64, 1, starts)         # c = n_b: the full space
+            E = np.empty((4 * 64, 3), real)
+            bsp.bsp_project(h, xyz.astype(real), bsp.BSP_DT_F64 if real == np.float64 else bsp.BSP_DT_F32, 3, E)
+            Xh = np.empty((N * N, 3), real)
+            bsp.bsp_reconstruct(h, E, 3, Xh)
+            assert np.abs(Xh - xyz).max() <= tol * 10
+            starts1 = synth.gaussian_starts(ptr, parent, 1, seed=9).astype(real)
+            bsp.bsp_oi_track(h, 1, 40, starts1)        # c = 1 converges to the constant
+            E1 = np.empty((4, 3), real)
+            bsp.bsp_project(h, xyz.astype(real), bsp.BSP_DT_F64 if real == np.float64 else bsp.BSP_DT_F32, 3, E1)
+            bsp.bsp_reconstruct(h, E1, 3, Xh)
+            for b in range(4):
+                vb = verts[ptr[b]:ptr[b + 1]]
+                np.testing.assert_allclose(Xh[vb], np.broadcast_to(xyz[vb].mean(0), (64, 3)),
+                                           atol=1e-4)
+        finally:
+            bsp.bsp_mesh_destroy(h)
+
+
+def test_t_max_zero_is_onorm_of_start():
+    h, om, xyz, *_ , ptr, verts, parent = make_tile_mesh(32, 16, prec=bsp.BSP_PREC_F64)
+    try:
+        starts = synth.gaussian_starts(ptr, parent, 8, seed=3)
+        bsp.bsp_oi_track(h, 8, 0, starts)
+        U_ref = O.oi_track(om, 8, 0, starts, delta=1e-2)
+        compare_bases(h, om, U_ref, xyz, np.float64, SINE_F64, PROJ_F64)
+    finally:
+        bsp.bsp_mesh_destroy(h)
+
+
+# ---------------------------------------------------------------- dynamic c
+
+def oracle_perturbation_sines(mesh, X, starts, **kw):
+    """Per-block sines between the oracle and the oracle with a 1e-6 relative
+    random perturbation of every solve: how well-conditioned the subspace
+    comparison is.  Unconverged directions (growth columns after few OI steps)
+    respond strongly; there only the projector and the widths are comparable."""
+    U0, c0, *_ = O.oi_track_dynamic(mesh, X, starts, **kw)
+    orig = O.apply_S
+    rng = np.random.default_rng(0)
+
+    def noisy(L, V, delta, z):
+        Y = orig(L, V, delta, z)
+        return Y + 1e-6 * np.linalg.norm(Y, axis=0) * rng.standard_normal(Y.shape) / np.sqrt(Y.shape[0])
+
+    O.apply_S = noisy
+    try:
+        U1, c1, *_ = O.oi_track_dynamic(mesh, X, starts, **kw)
+    finally:
+        O.apply_S = orig
+    assert np.array_equal(c0, c1)
+    return U0, c0, np.array([O.max_sine(U1[b], U0[b]) for b in range(mesh.k)])
+
+
+def test_dynamic_c_matches_oracle():
+    """48x48 height field (noise-free), 9 tiles, tol 2e-2: widths vary (grow and shrink)."""
+    N, T = 48, 16
+    xyz, faces = synth.grid_heightfield(N, seed=11, noise_sigma=0.0)
+    ptr, verts = synth.tile_partition(N, T)
+    parent = synth.raster_chain(9)
+    starts = synth.gaussian_starts(ptr, parent, 8, seed=12)
+    om = O.build_mesh(N * N, ptr, verts, parent, faces=faces)
+    kw = dict(tol=2e-2, c_min=8, c_max=64, c_step=8, t_max=2, delta=1e-2, seed=5)
+    Ur, cr, sens = oracle_perturbation_sines(om, xyz, starts, **kw)
+    assert len(set(cr.tolist())) > 2
+    for prec, real in [(bsp.BSP_PREC_F64, np.float64), (bsp.BSP_PREC_MIXED, np.float32)]:
+        h = bsp.bsp_mesh_create(xyz, faces, ptr, verts, parent,
+                                bsp.make_opts(precision=prec, cg_rtol=1e-12 if real == np.float64 else 1e-6))
+        try:
+            cg = np.empty(9, np.int32)
+            bsp.bsp_oi_track_dynamic(h, xyz.astype(real), 2e-2, 8, 64, 8, 2, 5,
+                                     starts.astype(real), None, cg)
+            # exact unless the oracle's rho sits within 1e-6 (relative) of the threshold
+            assert np.array_equal(cg, cr), (cg, cr)
+            assert np.array_equal(bsp.bsp_get_block_c(h, 9), cr)
+            for b, blk in enumerate(om.blocks):
+                U = bsp.bsp_get_basis(h, b, blk.verts.size, real).astype(np.float64)
+                if real == np.float64:
+                    assert O.max_sine(U, Ur[b]) <= 1e-6
+                else:
+                    assert O.max_sine(U, Ur[b]) <= max(SINE_F32, 10 * sens[b])
+                    assert O.projector_rel_error(U, Ur[b], xyz[blk.verts]) <= PROJ_F32
+        finally:
+            bsp.bsp_mesh_destroy(h)
+
+
+def test_dynamic_forced_c_replay():
+    N, T = 32, 16
+    xyz, faces = synth.grid_heightfield(N, seed=13)
+    ptr, verts = synth.tile_partition(N, T)
+    parent = synth.raster_chain(4)
+    starts = synth.gaussian_starts(ptr, parent, 8, seed=14)
+    forced = np.array([16, 24, 8, 32], np.int32)
+    h = bsp.bsp_mesh_create(xyz, faces, ptr, verts, parent, bsp.make_opts(precision=bsp.BSP_PREC_F64,
+                                                                           cg_rtol=1e-12))
+    try:
+        cg = np.empty(4, np.int32)
+        bsp.bsp_oi_track_dynamic(h, xyz, 2e-3, 8, 64, 8, 2, 5, starts, forced, cg)
+        assert cg.tolist() == forced.tolist()
+        Ur, cr, *_ = O.oi_track_dynamic(O.build_mesh(N * N, ptr, verts, parent, faces=faces), xyz,
+                                        starts, c_max=64, seed=5, forced_c=forced)
+        for b in range(4):
+            U = bsp.bsp_get_basis(h, b, 256, np.float64)
+            assert O.max_sine(U, Ur[b]) <= 1e-6
+    finally:
+        bsp.bsp_mesh_destroy(h)
+
+
+# ---------------------------------------------------------------- errors
+
+def _expect(code, fn, *a, **k):
+    with pytest.raises(bsp.BspError) as ei:
+        fn(*a, **k)
+    assert ei.value.code == code, str(ei.value)
+
+
+def test_invalid_arguments_are_rejected():
+    xyz, faces = synth.grid_heightfield(16)
+    ptr, verts = synth.tile_partition(16, 8)
+    parent = synth.raster_chain(4)
+    bad_faces = faces.copy()
+    bad_faces[3, 1] = 999
+    _expect(bsp.BSP_ERR_INVALID_ARG, bsp.bsp_mesh_create, xyz, bad_faces, ptr, verts, parent)
+    dup = verts.copy()
+    dup[5] = dup[6]
+    _expect(bsp.BSP_ERR_INVALID_ARG, bsp.bsp_mesh_create, xyz, faces, ptr, dup, parent)
+    _expect(bsp.BSP_ERR_INVALID_ARG, bsp.bsp_mesh_create, xyz, faces, ptr, verts,
+            np.array([-1, 2, 1, 2]))
+    _expect(bsp.BSP_ERR_INVALID_ARG, bsp.bsp_mesh_create, xyz, faces, ptr, verts, parent,
+            bsp.make_opts(delta=0.0))
+    _expect(bsp.BSP_ERR_INVALID_ARG, bsp.bsp_mesh_create, xyz, faces, np.array([0, 64, 64, 192, 256]),
+            verts, parent)
+    h = bsp.bsp_mesh_create(xyz, faces, ptr, verts, parent)
+    try:
+        starts = np.ones((64, 65), np.float32)
+        _expect(bsp.BSP_ERR_INVALID_ARG, bsp.bsp_oi_track, h, 65, 2, starts)
+        zero = np.zeros((64, 4), np.float32)            # rank-deficient start
+        _expect(bsp.BSP_ERR_NUMERICAL, bsp.bsp_oi_track, h, 4, 1, zero)
+        bsp.bsp_oi_track(h, 4, 1, synth.gaussian_starts(ptr, parent, 4).astype(np.float32))
+    finally:
+        bsp.bsp_mesh_destroy(h)
+
+
+def test_cg_step_cap_reports_not_converged():
+    h, om, xyz, *_ , ptr, verts, parent = make_tile_mesh(32, 16, cg_max_steps=2)
+    try:
+        starts = synth.gaussian_starts(ptr, parent, 8, seed=1).astype(np.float32)
+        _expect(bsp.BSP_ERR_NOT_CONVERGED, bsp.bsp_oi_track, h, 8, 1, starts)
+        assert bsp.bsp_get_stats(h)["not_converged"] > 0
+    finally:
+        bsp.bsp_mesh_destroy(h)
