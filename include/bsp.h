@@ -92,6 +92,7 @@ typedef struct bsp_stats {
   int32_t cg_steps_max;    /* largest step count of one solve in the last tracking call */
   int32_t not_converged;   /* solves that hit cg_max_steps in the last tracking call */
   int32_t gpu_launches;    /* kernels launched by the last tracking/projection call */
+  int32_t jacobi_sweeps;   /* Rayleigh-Ritz Jacobi sweeps summed over blocks, last tracking call */
 } bsp_stats;
 
 typedef struct bsp_mesh bsp_mesh;
@@ -166,7 +167,7 @@ int bsp_set_edge_weights(bsp_mesh* mesh, const void* w, int64_t E);
  * optional Rayleigh-Ritz.  start = the parent's final basis (rows mapped
  * r -> floor(r n_parent / n_b) when sizes differ), or, for a root, its rows
  * of V0_roots.  Independent blocks (same forest depth) run concurrently.
- *   c        1 <= c <= min over blocks of n_b, c <= 128.
+ *   c        1 <= c <= min over blocks of n_b, c <= 128 (c <= 64 with BSP_PREC_F64).
  *   t_max    >= 0 OI steps per block.
  *   V0_roots host or device real [sum over roots of n_b, c]: the roots' start
  *            matrices concatenated in block order; any full-rank matrices.

@@ -43,7 +43,8 @@ class bsp_stats(C.Structure):
     _fields_ = [("n", C.c_int64), ("k", C.c_int32), ("nnz", C.c_int64),
                 ("intra_edges", C.c_int64), ("max_block", C.c_int32), ("levels", C.c_int32),
                 ("cg_steps_total", C.c_int64), ("cg_steps_max", C.c_int32),
-                ("not_converged", C.c_int32), ("gpu_launches", C.c_int32)]
+                ("not_converged", C.c_int32), ("gpu_launches", C.c_int32),
+                ("jacobi_sweeps", C.c_int32)]
 
 
 class BspError(RuntimeError):

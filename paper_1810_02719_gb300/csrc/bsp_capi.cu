@@ -137,11 +137,14 @@ void release(bsp_mesh* m) {
                   m->d_root_off, m->d_waves, m->d_cb, m->d_cpar, m->d_ceoff, m->d_col,
                   m->d_wt, m->d_diag, m->d_status, m->d_cgstats, m->d_U, m->d_Y, m->d_starts,
                   m->d_Gp, m->d_Rsm, m->d_theta, m->d_action, m->d_round, m->d_forced,
-                  m->d_gcol, m->d_rho, m->d_X};
+                  m->d_gcol, m->d_rho, m->d_X, m->d_Gp_rr, m->d_Rsm_rr};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (m->graph_exec) cudaGraphExecDestroy(m->graph_exec);
   if (m->graph_stream) cudaStreamDestroy(m->graph_stream);
+  if (m->side_stream) cudaStreamDestroy(m->side_stream);
+  if (m->ev_fork) cudaEventDestroy(m->ev_fork);
+  if (m->ev_join) cudaEventDestroy(m->ev_join);
 }
 
 int stream_error_status(bsp_mesh* m, cudaStream_t s) {
@@ -153,6 +156,7 @@ int stream_error_status(bsp_mesh* m, cudaStream_t s) {
   m->stats.cg_steps_total = (int64_t)cs.steps_total;
   m->stats.cg_steps_max = cs.steps_max;
   m->stats.not_converged = cs.not_converged;
+  m->stats.jacobi_sweeps = cs.jacobi_sweeps;
   if (st & ST_NUMERICAL)
     return fail(BSP_ERR_NUMERICAL, "Gram matrix not positive definite or non-finite values");
   if (st & ST_NOT_CONVERGED)
@@ -287,6 +291,14 @@ int create_common(const double* xyz, int64_t n, const int32_t* tri, int64_t m, i
   }
   M->nnz = ao.nnz;
   M->intra_edges = ao.intra_edges;
+  {
+    std::vector<int32_t> rp(n + 1);
+    if (cudaMemcpy(rp.data(), M->d_rowptr, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cleanup_inputs();
+      return bail(fail(BSP_ERR_CUDA, "copy of row pointers failed"));
+    }
+    for (int64_t i = 0; i < n; ++i) M->max_deg = std::max(M->max_deg, rp[i + 1] - rp[i]);
+  }
   // weights and degrees
   const int rb = M->real_bytes;
   if (!dmalloc(&M->d_diag, (size_t)rb * n)) {
@@ -372,12 +384,36 @@ int ensure_workspace(bsp_mesh* M, int c_cap, int maxbatch) {
     return rc;
   if ((rc = ensure(&M->d_theta, &M->cap_theta, (size_t)maxbatch * cpad * sizeof(T))) != BSP_OK)
     return rc;
+  if ((rc = ensure(&M->d_Gp_rr, &M->cap_Gp_rr, gp)) != BSP_OK) return rc;
+  if ((rc = ensure(&M->d_Rsm_rr, &M->cap_Rsm_rr, (size_t)maxbatch * cpad * cpad * sizeof(T))) != BSP_OK)
+    return rc;
+  if (!M->side_stream && cudaStreamCreateWithFlags(&M->side_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(BSP_ERR_CUDA, "stream creation failed");
+  if (!M->ev_fork && (cudaEventCreateWithFlags(&M->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                      cudaEventCreateWithFlags(&M->ev_join, cudaEventDisableTiming) != cudaSuccess))
+    return fail(BSP_ERR_CUDA, "event creation failed");
   if ((M->c_cap != c_cap || g_realloc) && M->graph_exec) {
     cudaGraphExecDestroy(M->graph_exec);
     M->graph_exec = nullptr;
   }
   M->c_cap = c_cap;
   return BSP_OK;
+}
+
+// Rayleigh-Ritz of wave l on the side stream, ordered after everything
+// already enqueued on s.
+template <typename T, typename TA>
+int fork_rr(bsp_mesh* M, int l, int c, cudaStream_t s, int* launches) {
+  int wmax = 0;
+  for (int b : M->waves[l]) wmax = std::max(wmax, M->h_bptr[b + 1] - M->h_bptr[b]);
+  DenseArgs da{M->d_waves + M->h_wave_off[l], (int)M->waves[l].size(), M->d_bptr, M->d_cb,
+               M->c_cap, c, wmax, M->d_status};
+  da.sweeps = &M->d_cgstats->jacobi_sweeps;
+  CU(cudaEventRecord(M->ev_fork, s));
+  CU(cudaStreamWaitEvent(M->side_stream, M->ev_fork, 0));
+  int rc = launch_rayleigh_ritz<T, TA>(da, view<T>(M), (T*)M->d_U, (TA*)M->d_Gp_rr,
+                                       (T*)M->d_Rsm_rr, (T*)M->d_theta, M->side_stream, launches);
+  return rc ? fail(rc, "launch failed (Rayleigh-Ritz)") : BSP_OK;
 }
 
 // Enqueue the fixed-c schedule on stream s; returns a status, counts launches.
@@ -396,6 +432,11 @@ int enqueue_fixed(bsp_mesh* M, int c, int t_max, cudaStream_t s, int* launches) 
     launch_init_starts<T>(batch, nbw, M->d_bptr, M->d_parent, M->d_root_off, M->d_cb, M->d_cb,
                           (const T*)M->d_starts, c, U, M->c_cap, wmax, c, s);
     ++*launches;
+    // Rayleigh-Ritz of the previous wave leaves the critical path: the warm
+    // starts that read its bases have just been copied, and Rayleigh-Ritz does
+    // not change the spans that the remaining waves depend on.
+    if (l > 0 && M->opts.rayleigh_ritz && (rc = fork_rr<T, TA>(M, l - 1, c, s, launches)))
+      return rc;
     // Onorm of the start where it is not already an orthonormal basis: roots and
     // children whose size differs from their parent's.
     std::vector<int32_t> need;
@@ -416,20 +457,24 @@ int enqueue_fixed(bsp_mesh* M, int c, int t_max, cudaStream_t s, int* launches) 
         return fail(rc, "launch failed (Onorm of start)");
     }
     CgArgs ca{batch, nbw, M->d_cb, M->c_cap, M->opts.z, M->opts.delta, M->opts.cg_rtol,
-              M->opts.cg_max_steps, M->d_status, M->d_cgstats};
+              M->opts.cg_max_steps, M->d_status, M->d_cgstats, M->max_deg};
     const int cs = pick_cs(M, nbw, c, sizeof(T));
     for (int t = 0; t < t_max; ++t) {
       if ((rc = launch_cg<T>(mv, U, Y, ca, cs, wmax, c, s)))
         return fail(rc, "CG launch failed (block too large for shared memory?)");
       ++*launches;
-      if ((rc = launch_cholqr2<T, TA>(da, Y, U, (TA*)M->d_Gp, (T*)M->d_Rsm, s, launches)))
+      // Intermediate steps only need a well-conditioned basis for the next
+      // solve (span(S Q) = span(S Y)): one Cholesky-QR pass; the last step
+      // orthonormalises to working precision with CholeskyQR2.
+      const int passes = (t + 1 < t_max) ? 1 : 2;
+      if ((rc = launch_cholqr2<T, TA>(da, Y, U, (TA*)M->d_Gp, (T*)M->d_Rsm, s, launches, passes)))
         return fail(rc, "launch failed (Onorm)");
     }
-    if (M->opts.rayleigh_ritz) {
-      if ((rc = launch_rayleigh_ritz<T, TA>(da, mv, U, (TA*)M->d_Gp, (T*)M->d_Rsm,
-                                            (T*)M->d_theta, s, launches)))
-        return fail(rc, "launch failed (Rayleigh-Ritz)");
-    }
+  }
+  if (M->opts.rayleigh_ritz && levels > 0) {
+    if ((rc = fork_rr<T, TA>(M, levels - 1, c, s, launches))) return rc;
+    CU(cudaEventRecord(M->ev_join, M->side_stream));   // join the side branch
+    CU(cudaStreamWaitEvent(s, M->ev_join, 0));
   }
   return BSP_OK;
 }
@@ -457,7 +502,7 @@ int track_fixed(bsp_mesh* M, int c, int t_max, const void* V0, cudaStream_t s) {
   if (c > M->min_nb) return fail(BSP_ERR_INVALID_ARG, "c exceeds the smallest block size");
   if (t_max < 0) return fail(BSP_ERR_INVALID_ARG, "t_max must be >= 0");
   if (!V0) return fail(BSP_ERR_INVALID_ARG, "V0_roots is NULL");
-  if (sizeof(T) == 8 && c > 112) return fail(BSP_ERR_INVALID_ARG, "FP64 precision supports c <= 112");
+  if (sizeof(T) == 8 && c > 64) return fail(BSP_ERR_INVALID_ARG, "FP64 precision supports c <= 64");
   int maxbatch = 0;
   for (auto& w : M->waves) maxbatch = std::max(maxbatch, (int)w.size());
   int rc;
@@ -526,7 +571,7 @@ int track_dynamic(bsp_mesh* M, const void* X, double tol, int c_min, int c_max, 
   if (c_min > M->min_nb) return fail(BSP_ERR_INVALID_ARG, "c_min exceeds the smallest block");
   if (!(tol > 0)) return fail(BSP_ERR_INVALID_ARG, "rel_tol must be positive");
   if (!X || !V0) return fail(BSP_ERR_INVALID_ARG, "X and V0_roots are required");
-  if (sizeof(T) == 8 && c_max > 112) return fail(BSP_ERR_INVALID_ARG, "FP64 precision supports c <= 112");
+  if (sizeof(T) == 8 && c_max > 64) return fail(BSP_ERR_INVALID_ARG, "FP64 precision supports c <= 64");
   int maxbatch = 0;
   for (auto& w : M->waves) maxbatch = std::max(maxbatch, (int)w.size());
   int rc;
@@ -605,7 +650,7 @@ int track_dynamic(bsp_mesh* M, const void* X, double tol, int c_min, int c_max, 
       const int nbw = (int)active.size();
       DenseArgs da{d_list, nbw, M->d_bptr, M->d_cb, c_cap, cm, wmax, M->d_status};
       CgArgs ca{d_list, nbw, M->d_cb, c_cap, M->opts.z, M->opts.delta, M->opts.cg_rtol,
-                M->opts.cg_max_steps, M->d_status, M->d_cgstats};
+                M->opts.cg_max_steps, M->d_status, M->d_cgstats, M->max_deg};
       const int cs = pick_cs(M, nbw, cm, sizeof(T));
       for (int t = 0; t < t_max; ++t) {
         if ((rc = launch_cg<T>(mv, U, Y, ca, cs, wmax, cm, s))) return fail(rc, "CG launch failed");
@@ -613,6 +658,7 @@ int track_dynamic(bsp_mesh* M, const void* X, double tol, int c_min, int c_max, 
         if ((rc = launch_cholqr2<T, TA>(da, Y, U, (TA*)M->d_Gp, (T*)M->d_Rsm, s, &launches)))
           return fail(rc, "launch failed");
       }
+      da.sweeps = &M->d_cgstats->jacobi_sweeps;
       if ((rc = launch_rayleigh_ritz<T, TA>(da, mv, U, (TA*)M->d_Gp, (T*)M->d_Rsm, (T*)M->d_theta,
                                             s, &launches)))
         return fail(rc, "launch failed");

@@ -339,6 +339,185 @@ __global__ void k_spmm_scalar(int64_t n, MeshView<T> mv, const int32_t* __restri
   }
 }
 
+
+// ---- one column per CTA, latency-optimised (the warm-started chain case).
+// Chronopoulos-Gear CG: one fused reduction of (r, r) and (A r, r) per step and
+// two barriers; each thread keeps its rows' x, r, p, s = A p, w = A r and the
+// rows' ELL pattern (width ELLW) in registers, only r goes through shared
+// memory for the neighbour reads.  Rows: i = threadIdx.x + 256 m, m < MAXR.
+template <typename T, int MAXR, int ELLW>
+__global__ void __launch_bounds__(kThreads) k_cg1(MeshView<T> mv, const T* __restrict__ V,
+                                                  T* __restrict__ Y, CgArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T red[2][kWarps][2];
+  const int b = a.batch[blockIdx.y];
+  const int col = blockIdx.x;
+  if (col >= a.cb[b]) return;
+  const int r0 = mv.bptr[b];
+  const int nb = mv.bptr[b + 1] - r0;
+  T* rs = reinterpret_cast<T*>(smem_raw);          // nb entries: the vector being multiplied
+  const T delta = (T)a.delta;
+  const T rtol2 = (T)(a.rtol * a.rtol);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  // pattern and diagonal of my rows
+  uint16_t nbr[MAXR][ELLW];
+  T wt[MAXR][ELLW];
+  T dd[MAXR];
+  int deg[MAXR];
+#pragma unroll
+  for (int m = 0; m < MAXR; ++m) {
+    const int i = threadIdx.x + kThreads * m;
+    deg[m] = 0;
+    dd[m] = 0;
+#pragma unroll
+    for (int e = 0; e < ELLW; ++e) { nbr[m][e] = 0; wt[m][e] = 0; }
+    if (i < nb) {
+      const int e0 = mv.rowptr[r0 + i], e1 = mv.rowptr[r0 + i + 1];
+      deg[m] = e1 - e0;
+      dd[m] = mv.diag[r0 + i] + delta;
+#pragma unroll
+      for (int e = 0; e < ELLW; ++e)
+        if (e < e1 - e0) {
+          nbr[m][e] = mv.col[e0 + e];
+          wt[m][e] = mv.wt ? mv.wt[e0 + e] : T(1);
+        }
+    }
+  }
+  int buf = 0;
+  // sum of two per-thread values over the CTA (one barrier, double buffered)
+  auto reduce2 = [&](T u, T v, T& su, T& sv) {
+    u = warp_sum(u);
+    v = warp_sum(v);
+    if (lane == 0) { red[buf][w][0] = u; red[buf][w][1] = v; }
+    __syncthreads();
+    su = 0; sv = 0;
+#pragma unroll
+    for (int q = 0; q < kWarps; ++q) { su += red[buf][q][0]; sv += red[buf][q][1]; }
+    buf ^= 1;
+  };
+  // out_m = (D + delta) v_m - sum C v_nbr, v taken from rs (shared)
+  auto apply = [&](const T (&v)[MAXR], T (&out)[MAXR]) {
+#pragma unroll
+    for (int m = 0; m < MAXR; ++m) {
+      T acc = dd[m] * v[m];
+#pragma unroll
+      for (int e = 0; e < ELLW; ++e)
+        if (e < deg[m]) acc -= wt[m][e] * rs[nbr[m][e]];
+      out[m] = acc;
+    }
+  };
+  T bvec[MAXR], x[MAXR], r[MAXR], p[MAXR], sv[MAXR], wv[MAXR];
+#pragma unroll
+  for (int m = 0; m < MAXR; ++m) {
+    const int i = threadIdx.x + kThreads * m;
+    bvec[m] = i < nb ? V[(size_t)(r0 + i) * a.ld + col] : T(0);
+  }
+  int steps_all = 0, steps_max = 0;
+  bool unconverged = false, bad = false;
+  for (int sol = 0; sol < a.z; ++sol) {
+    // initial guess x0 = b (b, b) / (b, A b)
+#pragma unroll
+    for (int m = 0; m < MAXR; ++m) {
+      const int i = threadIdx.x + kThreads * m;
+      if (i < nb) rs[i] = bvec[m];
+    }
+    __syncthreads();
+    apply(bvec, wv);
+    T bb = 0, bab = 0;
+#pragma unroll
+    for (int m = 0; m < MAXR; ++m) { bb += bvec[m] * bvec[m]; bab += bvec[m] * wv[m]; }
+    T sbb, sbab;
+    reduce2(bb, bab, sbb, sbab);
+    const T g = sbab > T(0) ? sbb / sbab : T(0);
+    const T bn2 = sbb;
+#pragma unroll
+    for (int m = 0; m < MAXR; ++m) {
+      x[m] = g * bvec[m];
+      r[m] = bvec[m] - g * wv[m];
+    }
+    // w0 = A r0 ; gamma = (r, r), delta = (w, r)
+#pragma unroll
+    for (int m = 0; m < MAXR; ++m) {
+      const int i = threadIdx.x + kThreads * m;
+      if (i < nb) rs[i] = r[m];
+    }
+    __syncthreads();
+    apply(r, wv);
+    T gl = 0, dl = 0;
+#pragma unroll
+    for (int m = 0; m < MAXR; ++m) { gl += r[m] * r[m]; dl += wv[m] * r[m]; }
+    T gam, dlt;
+    reduce2(gl, dl, gam, dlt);
+    T alpha = dlt > T(0) ? gam / dlt : T(0);
+#pragma unroll
+    for (int m = 0; m < MAXR; ++m) { p[m] = r[m]; sv[m] = wv[m]; }
+    int steps = 0;
+    while (gam > rtol2 * bn2) {
+      if (steps >= a.max_steps) { unconverged = true; break; }
+      if (!(dlt > T(0))) { bad = true; break; }
+#pragma unroll
+      for (int m = 0; m < MAXR; ++m) {
+        x[m] += alpha * p[m];
+        r[m] -= alpha * sv[m];
+      }
+#pragma unroll
+      for (int m = 0; m < MAXR; ++m) {
+        const int i = threadIdx.x + kThreads * m;
+        if (i < nb) rs[i] = r[m];
+      }
+      __syncthreads();
+      apply(r, wv);
+      gl = 0; dl = 0;
+#pragma unroll
+      for (int m = 0; m < MAXR; ++m) { gl += r[m] * r[m]; dl += wv[m] * r[m]; }
+      T gnew, dnew;
+      reduce2(gl, dl, gnew, dnew);
+      ++steps;
+      if (!(gnew > rtol2 * bn2)) { gam = gnew; break; }
+      const T beta = gnew / gam;
+      const T den = dnew - beta * gnew / alpha;
+      alpha = den > T(0) ? gnew / den : T(0);
+      if (!(den > T(0))) bad = true;
+      gam = gnew;
+      dlt = den;
+#pragma unroll
+      for (int m = 0; m < MAXR; ++m) {
+        p[m] = r[m] + beta * p[m];
+        sv[m] = wv[m] + beta * sv[m];
+      }
+    }
+    steps_all += steps;
+    steps_max = max(steps_max, steps);
+#pragma unroll
+    for (int m = 0; m < MAXR; ++m) bvec[m] = x[m];   // next right-hand side (z > 1)
+    __syncthreads();  // rs is rewritten by the next solve
+  }
+#pragma unroll
+  for (int m = 0; m < MAXR; ++m) {
+    const int i = threadIdx.x + kThreads * m;
+    if (i < nb) Y[(size_t)(r0 + i) * a.ld + col] = x[m];
+  }
+  if (threadIdx.x == 0) {
+    atomicAdd(&a.stats->steps_total, (unsigned long long)steps_all);
+    atomicMax(&a.stats->steps_max, steps_max);
+    if (unconverged) {
+      atomicAdd(&a.stats->not_converged, 1);
+      atomicOr(a.status, ST_NOT_CONVERGED);
+    }
+    if (bad) atomicOr(a.status, ST_NUMERICAL);
+  }
+}
+
+template <typename T, int MAXR, int ELLW>
+int launch_cg1_t(const MeshView<T>& mv, const T* V, T* Y, const CgArgs& a, int max_nb, int c_max,
+                 cudaStream_t s) {
+  dim3 grid(c_max, a.nbatch);
+  prof_begin(KC_CG, s);
+  k_cg1<T, MAXR, ELLW><<<grid, kThreads, (size_t)max_nb * sizeof(T), s>>>(mv, V, Y, a);
+  prof_end(KC_CG, s);
+  return cudaGetLastError() == cudaSuccess ? BSP_OK : BSP_ERR_CUDA;
+}
+
 template <typename T, int CS>
 int launch_cg_cs(const MeshView<T>& mv, const T* V, T* Y, const CgArgs& a, int max_nb, int c_max,
                  cudaStream_t s) {
@@ -352,6 +531,8 @@ int launch_cg_cs(const MeshView<T>& mv, const T* V, T* Y, const CgArgs& a, int m
 }
 
 }  // namespace
+
+bool g_disable_cg1 = false;
 
 // Opt every CG instantiation in to the full 227 KB of dynamic shared memory.
 void configure_cg_kernels() {
@@ -373,6 +554,15 @@ int cg_smem_bytes(int cs, int max_nb) {
 template <typename T>
 int launch_cg(const MeshView<T>& mv, const T* V, T* Y, const CgArgs& a, int cs, int max_nb,
               int c_max, cudaStream_t s) {
+  // one column per CTA with the pattern in registers when it fits
+  if (cs == 1 && a.max_deg > 0 && a.max_deg <= 16 && max_nb <= 4 * kThreads && !g_disable_cg1) {
+    const int mr = (max_nb + kThreads - 1) / kThreads;
+    if (a.max_deg <= 8)
+      return mr <= 1 ? launch_cg1_t<T, 1, 8>(mv, V, Y, a, max_nb, c_max, s)
+                     : launch_cg1_t<T, 4, 8>(mv, V, Y, a, max_nb, c_max, s);
+    return mr <= 1 ? launch_cg1_t<T, 1, 16>(mv, V, Y, a, max_nb, c_max, s)
+                   : launch_cg1_t<T, 4, 16>(mv, V, Y, a, max_nb, c_max, s);
+  }
   switch (cs) {
     case 1: return launch_cg_cs<T, 1>(mv, V, Y, a, max_nb, c_max, s);
     case 2: return launch_cg_cs<T, 2>(mv, V, Y, a, max_nb, c_max, s);

@@ -16,65 +16,13 @@
 #include <cfloat>
 #include <cmath>
 
-#include "bsp_internal.cuh"
+#include "bsp_dense_dev.cuh"
 
 namespace bsp {
 namespace {
 
-constexpr int kDT = 256;
+using namespace dev;
 constexpr int kJacobiSweeps = 20;
-
-__host__ __device__ inline int pad4(int c) { return (c + 3) & ~3; }
-
-template <typename T>
-BSP_DEV void stage_panel(const T* __restrict__ A, int ld, int row0, int nr, int c, int cpad,
-                         int CH, T* S) {
-  for (int t = threadIdx.x; t < CH * cpad; t += blockDim.x) {
-    int i = t / cpad, j = t - i * cpad;
-    S[t] = (i < nr && j < c) ? A[(size_t)(row0 + i) * ld + j] : T(0);
-  }
-}
-
-template <typename T>
-BSP_DEV void ld4(const T* p, T (&v)[4]) {
-  if constexpr (sizeof(T) == 4) {
-    float4 t = *reinterpret_cast<const float4*>(p);
-    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
-  } else {
-    double2 a = *reinterpret_cast<const double2*>(p);
-    double2 b = *reinterpret_cast<const double2*>(p + 2);
-    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-  }
-}
-
-// out[i][j] (cpad x cpad, TA) = sum_r S[r][i] * S2[r][j] over the panel's CH rows,
-// in 4x4 register tiles; `upper` computes only tiles with ti <= tj.
-template <typename T, typename TA>
-BSP_DEV void panel_gram(const T* S, const T* S2, int CH, int cpad, bool upper, TA* out) {
-  const int nt = cpad / 4;
-  for (int u = threadIdx.x; u < nt * nt; u += blockDim.x) {
-    const int ti = u / nt, tj = u - ti * nt;
-    if (upper && ti > tj) continue;
-    T acc[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = 0;
-    for (int r = 0; r < CH; ++r) {
-      T a[4], b[4];
-      ld4(S + r * cpad + 4 * ti, a);
-      ld4(S2 + r * cpad + 4 * tj, b);
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) out[(4 * ti + i) * cpad + 4 * tj + j] = (TA)acc[i][j];
-  }
-}
 
 template <typename T, typename TA>
 __global__ void __launch_bounds__(kDT) k_gram(DenseArgs a, const T* __restrict__ Y, int CH,
@@ -111,8 +59,128 @@ __global__ void k_reduce(DenseArgs a, int CH, int maxch, bool upper, const TA* _
   G[(size_t)blockIdx.y * cpad * cpad + e] = s;
 }
 
-// Cholesky G = R^T R (upper R) after Jacobi scaling, then M = R^-1 (upper) in T.
-// smem: A [cpad x cpad] TA, X [cpad x cpad] T, d [cpad] TA.
+// M = R^-1 (upper, T, cpad x cpad) for G = R^T R with G given by its upper
+// triangle g (type TG, stride cpad, global or shared memory); the Cholesky
+// runs in TA after Jacobi scaling D G D, D = diag(G)^-1/2.  Shared workspace:
+// A [cpad x cpad] TA (scaled G, updated in place), d [2 cpad] TA (scaling,
+// then the pivot row), Rr [CP x CP] T (R, zero-padded to the width CP >= c, a
+// power of two >= 32).  A must hold max(cpad^2 TA, 1.5 CP^2 T) bytes: R^-1
+// and its temporaries reuse it after the factorization.  *fail (shared) is set
+// on a non-positive or non-finite pivot; M is then the identity.  Called by
+// all threads; ends with a barrier.
+//
+// Factorization: right-looking, two barriers per column; the trailing update
+// of column k is tiled over a 16 x 16 thread grid (balanced, division-free).
+template <typename T, typename TA, typename TG, int CP>
+BSP_DEV void chol_inverse(const TG* g, int c, int cpad, TA* A, TA* d, T* Rr, T* M, int* fail) {
+  for (int t = threadIdx.x; t < CP * CP; t += blockDim.x) Rr[t] = T(0);
+  for (int t = threadIdx.x; t < c; t += blockDim.x) {
+    TA v = (TA)g[t * cpad + t];
+    if (!(v > TA(0)) || !isfinite((double)v)) {
+      *fail = 1;
+      v = TA(1);
+    }
+    d[t] = TA(1) / sqrt(v);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x >> 5; i < c; i += blockDim.x >> 5)
+    for (int jj = (threadIdx.x & 31) + i; jj < c; jj += 32)  // upper triangle only
+      A[i * cpad + jj] = (TA)g[i * cpad + jj] * d[i] * d[jj];
+  __syncthreads();
+  TA* lrow = d + cpad;  // scaled pivot row (TA)
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // 16 x 16 (256 threads)
+  for (int k = 0; k < c; ++k) {
+    if (ty == 0) {
+      TA piv = A[k * cpad + k];
+      if (!(piv > TA(0)) || !isfinite((double)piv)) {
+        *fail = 1;
+        piv = TA(1);
+      }
+      const TA inv = TA(1) / sqrt(piv);
+      for (int jj = k + tx; jj < c; jj += 16) {
+        const TA lj = A[k * cpad + jj] * inv;
+        lrow[jj] = lj;
+        Rr[k * CP + jj] = (T)lj;
+      }
+    }
+    __syncthreads();
+    for (int i = k + 1 + ty; i < c; i += 16) {
+      const TA li = lrow[i];
+      int j0 = k + 1 + tx;
+      if (j0 < i) j0 += ((i - j0 + 15) >> 4) << 4;   // first j >= i in this thread's lane
+      for (int jj = j0; jj < c; jj += 16) A[i * cpad + jj] -= li * lrow[jj];
+    }
+    __syncthreads();
+  }
+  // R^-1 by recursive blocking: rows/columns >= c act as the identity; the 16 x
+  // 16 diagonal blocks are inverted by per-thread back substitution (thread =
+  // column, 16 registers), then levels s = 16, 32, ... combine block pairs with
+  // X12 = -X11 R12 X22 as two small shared-memory GEMMs (four barriers/level).
+  T* X = reinterpret_cast<T*>(A);             // CP x CP
+  T* W = X + CP * CP;                         // CP x CP / 2 temporaries
+  for (int i = threadIdx.x; i < CP; i += blockDim.x)
+    if (i >= c) Rr[i * CP + i] = T(1);
+  for (int t = threadIdx.x; t < CP * CP; t += blockDim.x) X[t] = T(0);
+  __syncthreads();
+  if (threadIdx.x < CP) {
+    const int q0 = threadIdx.x & ~15, jl = threadIdx.x & 15;
+    T x[16];
+#pragma unroll
+    for (int i = 15; i >= 0; --i) {
+      T sum = (i == jl) ? T(1) : T(0);
+#pragma unroll
+      for (int l = i + 1; l < 16; ++l) sum -= Rr[(q0 + i) * CP + q0 + l] * x[l];
+      x[i] = sum / Rr[(q0 + i) * CP + q0 + i];
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) X[(q0 + i) * CP + q0 + jl] = i <= jl ? x[i] : T(0);
+  }
+  __syncthreads();
+  for (int sz = 16; sz < CP; sz <<= 1) {
+    int lg = 0;
+    while ((1 << lg) < sz) ++lg;
+    const int npair = CP / (2 * sz), tot = npair * sz * sz;
+    // W = R12 X22 for every pair (blocks at o = m 2 sz)
+    for (int u = threadIdx.x; u < tot; u += blockDim.x) {
+      const int m = u >> (2 * lg), rem = u & (sz * sz - 1);
+      const int i = rem >> lg, jj = rem & (sz - 1);
+      const int o = m * 2 * sz;
+      T acc = 0;
+      for (int l = 0; l < sz; ++l) acc += Rr[(o + i) * CP + o + sz + l] * X[(o + sz + l) * CP + o + sz + jj];
+      W[u] = acc;
+    }
+    __syncthreads();
+    // X12 = -X11 W
+    for (int u = threadIdx.x; u < tot; u += blockDim.x) {
+      const int m = u >> (2 * lg), rem = u & (sz * sz - 1);
+      const int i = rem >> lg, jj = rem & (sz - 1);
+      const int o = m * 2 * sz;
+      T acc = 0;
+      for (int l = 0; l < sz; ++l) acc += X[(o + i) * CP + o + l] * W[(m * sz + l) * sz + jj];
+      X[(o + i) * CP + o + sz + jj] = -acc;
+    }
+    __syncthreads();
+  }
+  // M = D R_s^-1 (undo the Jacobi scaling)
+  const bool bad = *fail != 0;
+  for (int i = threadIdx.x >> 5; i < cpad; i += blockDim.x >> 5)
+    for (int jj = threadIdx.x & 31; jj < cpad; jj += 32) {
+      T v = (i < c && jj < c && i <= jj) ? (T)d[i] * X[i * CP + jj] : T(0);
+      if (bad) v = (i == jj && i < c) ? T(1) : T(0);
+      M[i * cpad + jj] = v;
+    }
+  __syncthreads();
+}
+
+// Dispatch on the compile-time width.
+template <typename T, typename TA, typename TG>
+BSP_DEV void chol_inverse_any(const TG* g, int c, int cpad, TA* A, TA* d, T* Rr, T* M, int* fail) {
+  if (c <= 32) chol_inverse<T, TA, TG, 32>(g, c, cpad, A, d, Rr, M, fail);
+  else if (c <= 64) chol_inverse<T, TA, TG, 64>(g, c, cpad, A, d, Rr, M, fail);
+  else chol_inverse<T, TA, TG, 128>(g, c, cpad, A, d, Rr, M, fail);
+}
+
+// Cholesky + inverse for each block of the batch (one CTA per block).
 template <typename T, typename TA>
 __global__ void __launch_bounds__(kDT) k_chol(DenseArgs a, const TA* __restrict__ G,
                                               T* __restrict__ Mout) {
@@ -121,68 +189,14 @@ __global__ void __launch_bounds__(kDT) k_chol(DenseArgs a, const TA* __restrict_
   const int c = a.cb[b];
   const int cpad = pad4(a.cmax);
   TA* A = reinterpret_cast<TA*>(smem_raw);
-  T* X = reinterpret_cast<T*>(A + cpad * cpad);
-  TA* d = reinterpret_cast<TA*>(X + cpad * cpad);
+  TA* d = A + chol_a_elems<T, TA>(cpad, chol_cp(cpad));
+  T* Rr = reinterpret_cast<T*>(d + 2 * cpad);
   __shared__ int fail;
   if (threadIdx.x == 0) fail = 0;
-  const TA* g = G + (size_t)blockIdx.x * cpad * cpad;
-  for (int t = threadIdx.x; t < c; t += blockDim.x) {
-    TA v = g[t * cpad + t];
-    if (!(v > TA(0)) || !isfinite((double)v)) {
-      fail = 1;
-      v = TA(1);
-    }
-    d[t] = TA(1) / sqrt(v);
-  }
   __syncthreads();
-  for (int e = threadIdx.x; e < c * c; e += blockDim.x) {
-    int i = e / c, j = e - i * c;
-    A[i * cpad + j] = i <= j ? g[i * cpad + j] * d[i] * d[j] : TA(0);
-  }
-  __syncthreads();
-  for (int k = 0; k < c; ++k) {
-    if (threadIdx.x == 0) {
-      TA p = A[k * cpad + k];
-      if (!(p > TA(0)) || !isfinite((double)p)) {
-        fail = 1;
-        p = TA(1);
-      }
-      A[k * cpad + k] = sqrt(p);
-    }
-    __syncthreads();
-    const TA rkk = A[k * cpad + k];
-    for (int j = k + 1 + threadIdx.x; j < c; j += blockDim.x) A[k * cpad + j] /= rkk;
-    __syncthreads();
-    const int m = c - k - 1;
-    for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
-      int i = k + 1 + t / m, j = k + 1 + t % m;
-      if (i <= j) A[i * cpad + j] -= A[k * cpad + i] * A[k * cpad + j];
-    }
-    __syncthreads();
-  }
-  // X = R^-1 (upper) by back substitution, one column per thread, in T.
-  for (int j = threadIdx.x; j < cpad; j += blockDim.x) {
-    for (int i = cpad - 1; i >= 0; --i) {
-      T v = 0;
-      if (j < c && i <= j) {
-        T s = (i == j) ? T(1) : T(0);
-        for (int l = i + 1; l <= j; ++l) s -= (T)A[i * cpad + l] * X[l * cpad + j];
-        v = s / (T)A[i * cpad + i];
-      }
-      X[i * cpad + j] = v;
-    }
-  }
-  __syncthreads();
-  // undo the scaling: R_full = R_s D^-1  =>  R_full^-1 = D R_s^-1
-  T* M = Mout + (size_t)blockIdx.x * cpad * cpad;
-  const bool bad = fail != 0;
-  for (int e = threadIdx.x; e < cpad * cpad; e += blockDim.x) {
-    int i = e / cpad, j = e - i * cpad;
-    T v = (i < c && j < c) ? (T)d[i] * X[e] : T(0);
-    if (bad) v = (i == j && i < c) ? T(1) : T(0);
-    M[e] = v;
-  }
-  if (bad && threadIdx.x == 0) atomicOr(a.status, ST_NUMERICAL);
+  chol_inverse_any<T, TA, TA>(G + (size_t)blockIdx.x * cpad * cpad, c, cpad, A, d, Rr,
+                              Mout + (size_t)blockIdx.x * cpad * cpad, &fail);
+  if (fail && threadIdx.x == 0) atomicOr(a.status, ST_NUMERICAL);
 }
 
 // Out panel = Y panel (CH x c) x M (c x c); written to Q (may alias Y: every
@@ -319,20 +333,35 @@ __global__ void __launch_bounds__(kDT) k_jacobi(DenseArgs a, const TA* __restric
     hscale = m;
   }
   __syncthreads();
-  const T floor_abs = eps * (T)1e-2 * hscale;
+  // Rounding in T leaves off-diagonal noise of order eps * ||H||: pairs below
+  // that floor are treated as converged.
+  const T floor_abs = (T)8 * eps * hscale;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  int sweeps = 0;
   for (int sweep = 0; sweep < kJacobiSweeps; ++sweep) {
+    // any pair above threshold?  (checked before the sweep: a nearly diagonal
+    // H, the common case for a warm-started block, costs one pass)
     if (threadIdx.x == 0) rotated = 0;
     __syncthreads();
+    for (int i = warp; i < c; i += nwarp)
+      for (int jj = i + 1 + lane; jj < c; jj += 32) {
+        const T hij = H[i * ld + jj];
+        if (fabs(hij) > eps * sqrt(fabs(H[i * ld + i] * H[jj * ld + jj])) && fabs(hij) > floor_abs)
+          rotated = 1;
+      }
+    __syncthreads();
+    const int any = rotated;
+    if (!any) break;
+    ++sweeps;
     for (int rnd = 0; rnd < ne - 1; ++rnd) {
       for (int m = threadIdx.x; m < ne / 2; m += blockDim.x) {
-        // round-robin: position 0 fixed, others rotate
-        auto player = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + rnd) % (ne - 1); };
-        int p = player(m), q = player(ne - 1 - m);
+        // round-robin: position 0 fixed, the others rotate by one per round
+        int p = m == 0 ? 0 : 1 + (m - 1 + rnd) % (ne - 1);
+        int q = 1 + (ne - 2 - m + rnd) % (ne - 1);
         if (p > q) { int t = p; p = q; q = t; }
         T hpq = H[p * ld + q], hpp = H[p * ld + p], hqq = H[q * ld + q];
         T cth = 1, sth = 0;
         if (fabs(hpq) > eps * sqrt(fabs(hpp * hqq)) && fabs(hpq) > floor_abs) {
-          rotated = 1;
           T tau = (hqq - hpp) / (2 * hpq);
           T t = (tau >= 0 ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
           cth = T(1) / sqrt(T(1) + t * t);
@@ -341,35 +370,36 @@ __global__ void __launch_bounds__(kDT) k_jacobi(DenseArgs a, const TA* __restric
         pp[m] = p; qq[m] = q; cs[m] = cth; sn[m] = sth;
       }
       __syncthreads();
-      // rows p, q  <-  J^T H
-      for (int t = threadIdx.x; t < (ne / 2) * ne; t += blockDim.x) {
-        int m = t / ne, k = t - m * ne;
-        int p = pp[m], q = qq[m];
-        T cth = cs[m], sth = sn[m];
-        T hp = H[p * ld + k], hq = H[q * ld + k];
-        H[p * ld + k] = cth * hp - sth * hq;
-        H[q * ld + k] = sth * hp + cth * hq;
+      // rows p, q  <-  J^T H   (warp per pair, lane per column)
+      for (int m = warp; m < ne / 2; m += nwarp) {
+        const int p = pp[m], q = qq[m];
+        const T cth = cs[m], sth = sn[m];
+        if (sth == T(0)) continue;
+        for (int k = lane; k < ne; k += 32) {
+          const T hp = H[p * ld + k], hq = H[q * ld + k];
+          H[p * ld + k] = cth * hp - sth * hq;
+          H[q * ld + k] = sth * hp + cth * hq;
+        }
       }
       __syncthreads();
       // columns p, q  <-  H J ; eigenvectors Q <- Q J
-      for (int t = threadIdx.x; t < (ne / 2) * ne; t += blockDim.x) {
-        int m = t / ne, k = t - m * ne;
-        int p = pp[m], q = qq[m];
-        T cth = cs[m], sth = sn[m];
-        T hp = H[k * ld + p], hq = H[k * ld + q];
-        H[k * ld + p] = cth * hp - sth * hq;
-        H[k * ld + q] = sth * hp + cth * hq;
-        T qp = Qm[k * ld + p], qv = Qm[k * ld + q];
-        Qm[k * ld + p] = cth * qp - sth * qv;
-        Qm[k * ld + q] = sth * qp + cth * qv;
+      for (int m = warp; m < ne / 2; m += nwarp) {
+        const int p = pp[m], q = qq[m];
+        const T cth = cs[m], sth = sn[m];
+        if (sth == T(0)) continue;
+        for (int k = lane; k < ne; k += 32) {
+          const T hp = H[k * ld + p], hq = H[k * ld + q];
+          H[k * ld + p] = cth * hp - sth * hq;
+          H[k * ld + q] = sth * hp + cth * hq;
+          const T qp = Qm[k * ld + p], qv = Qm[k * ld + q];
+          Qm[k * ld + p] = cth * qp - sth * qv;
+          Qm[k * ld + q] = sth * qp + cth * qv;
+        }
       }
       __syncthreads();
     }
-    __syncthreads();
-    const int any = rotated;
-    __syncthreads();  // every thread has read the flag before thread 0 resets it
-    if (!any) break;
   }
+  if (threadIdx.x == 0 && a.sweeps) atomicAdd(a.sweeps, sweeps);
   // sort ascending: rank of each eigenvalue (ties broken by index)
   T* Qo = Qout + (size_t)blockIdx.x * cpad * cpad;
   T* th = theta + (size_t)blockIdx.x * cpad;
@@ -393,6 +423,7 @@ __global__ void __launch_bounds__(kDT) k_jacobi(DenseArgs a, const TA* __restric
   }
 }
 
+
 template <typename T, typename TA>
 size_t panel_smem(int CH, int cpad) {
   return (size_t)(2 * CH * cpad + cpad * cpad) * sizeof(T);
@@ -411,6 +442,8 @@ void configure_one() {
 
 }  // namespace
 
+bool g_disable_fused = false;
+
 int dense_chunk_rows(int cpad, int rb) {
   const int opts[3] = {128, 64, 32};
   for (int ch : opts)
@@ -422,16 +455,25 @@ void configure_dense_kernels() {
   configure_one<float, float>();
   configure_one<float, double>();
   configure_one<double, double>();
+  configure_fused_kernels();
 }
 
 // One Onorm: G1 = Y^T Y (TA), Cholesky (TA), Q1 = Y R1^-1 fused with G2 = Q1^T Q1
 // (T), Cholesky (T), Q = Q1 R2^-1.  Q may alias Y.
 template <typename T, typename TA>
 int launch_cholqr2(const DenseArgs& a, const T* Y, T* Q, TA* Gp, T* Rsm, cudaStream_t s,
-                   int* launches) {
+                   int* launches, int passes) {
   const int cpad = pad4(a.cmax);
   const int CH = dense_chunk_rows(cpad, sizeof(T));
   const int maxch = (a.max_nb + CH - 1) / CH;
+  // Fused path (c <= 64): one cluster launch per batch of blocks.
+  if (cpad <= 64 && !g_disable_fused) {
+    const int rc = launch_cholqr2_fused<T, TA>(a, Y, Q, Gp, maxch, s, passes);
+    if (rc != BSP_ERR_INVALID_ARG) {
+      if (launches) *launches += 1;
+      return rc;
+    }
+  }
   // partial-Gram area first, reduced Gram after it (both in the Gp workspace)
   TA* G = Gp + (size_t)a.nbatch * maxch * cpad * cpad;
   T* Gp2raw = reinterpret_cast<T*>(Gp);  // pass 2 partials in T reuse the same area
@@ -445,19 +487,28 @@ int launch_cholqr2(const DenseArgs& a, const T* Y, T* Q, TA* Gp, T* Rsm, cudaStr
   prof_begin(KC_REDUCE, s);
   k_reduce<TA><<<gr, kDT, 0, s>>>(a, CH, maxch, true, Gp, G);
   prof_end(KC_REDUCE, s);
-  const size_t sm_chol_a = (size_t)cpad * cpad * sizeof(TA) + (size_t)cpad * cpad * sizeof(T) +
-                           (size_t)cpad * sizeof(TA) + 16;
+  const int cpw = chol_cp(cpad);
+  const size_t sm_chol_a = (size_t)(chol_a_elems<T, TA>(cpad, cpw) + 2 * cpad) * sizeof(TA) +
+                           (size_t)cpw * cpw * sizeof(T);
   prof_begin(KC_CHOL, s);
   k_chol<T, TA><<<a.nbatch, kDT, sm_chol_a, s>>>(a, G, Rsm);
   prof_end(KC_CHOL, s);
   const size_t sm_mul = panel_smem<T, TA>(CH, cpad);
+  if (passes < 2) {
+    prof_begin(KC_PANEL, s);
+    k_panel_mul<T, T, true, false><<<gp, kDT, sm_mul, s>>>(a, Y, Q, Rsm, CH, maxch, (T*)nullptr);
+    prof_end(KC_PANEL, s);
+    if (launches) *launches += 4;
+    return cudaGetLastError() == cudaSuccess ? BSP_OK : BSP_ERR_CUDA;
+  }
   prof_begin(KC_PANEL, s);
   k_panel_mul<T, T, true, true><<<gp, kDT, sm_mul, s>>>(a, Y, Q, Rsm, CH, maxch, Gp2raw);
   prof_end(KC_PANEL, s);
   prof_begin(KC_REDUCE, s);
   k_reduce<T><<<gr, kDT, 0, s>>>(a, CH, maxch, true, Gp2raw, G2);
   prof_end(KC_REDUCE, s);
-  const size_t sm_chol_b = (size_t)cpad * cpad * sizeof(T) * 2 + (size_t)cpad * sizeof(T) + 16;
+  const size_t sm_chol_b = (size_t)(chol_a_elems<T, T>(cpad, cpw) + 2 * cpad) * sizeof(T) +
+                           (size_t)cpw * cpw * sizeof(T);
   prof_begin(KC_CHOL, s);
   k_chol<T, T><<<a.nbatch, kDT, sm_chol_b, s>>>(a, G2, Rsm);
   prof_end(KC_CHOL, s);
@@ -497,12 +548,10 @@ int launch_rayleigh_ritz(const DenseArgs& a, const MeshView<T>& mv, T* V, TA* Gp
   return cudaGetLastError() == cudaSuccess ? BSP_OK : BSP_ERR_CUDA;
 }
 
-template int launch_cholqr2<float, double>(const DenseArgs&, const float*, float*, double*,
-                                           float*, cudaStream_t, int*);
+template int launch_cholqr2<float, double>(const DenseArgs&, const float*, float*, double*, float*, cudaStream_t, int*, int);
 template int launch_cholqr2<float, float>(const DenseArgs&, const float*, float*, float*, float*,
-                                          cudaStream_t, int*);
-template int launch_cholqr2<double, double>(const DenseArgs&, const double*, double*, double*,
-                                            double*, cudaStream_t, int*);
+                                          cudaStream_t, int*, int);
+template int launch_cholqr2<double, double>(const DenseArgs&, const double*, double*, double*, double*, cudaStream_t, int*, int);
 template int launch_rayleigh_ritz<float, double>(const DenseArgs&, const MeshView<float>&,
                                                  float*, double*, float*, float*, cudaStream_t,
                                                  int*);

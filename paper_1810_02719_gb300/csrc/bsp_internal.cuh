@@ -32,6 +32,7 @@ struct CgStats {
   unsigned long long steps_total;
   int steps_max;
   int not_converged;
+  int jacobi_sweeps;
 };
 
 // ---------------------------------------------------------------- profiling
@@ -133,7 +134,9 @@ struct CgArgs {
   int ld;                   // row stride of V and Y
   int z; double delta; double rtol; int max_steps;
   int* status; CgStats* stats;
+  int max_deg = 0;          // largest row degree of the mesh (selects the register-ELL kernel)
 };
+extern bool g_disable_cg1;  // force the shared-memory CG kernel (A/B checks)
 template <typename T>
 int launch_cg(const MeshView<T>& mv, const T* V, T* Y, const CgArgs& a, int cs, int max_nb,
               int c_max, cudaStream_t s);
@@ -151,14 +154,21 @@ struct DenseArgs {
   int cmax;                 // largest c in the batch (grid sizing)
   int max_nb;               // largest n_b in the batch
   int* status;
+  int* sweeps = nullptr;    // optional: Jacobi sweeps performed (summed)
 };
 template <typename T, typename TA>
 int launch_cholqr2(const DenseArgs& a, const T* Y, T* Q, TA* Gp, T* Rsm, cudaStream_t s,
-                   int* launches);
+                   int* launches, int passes = 2);
 template <typename T, typename TA>
 int launch_rayleigh_ritz(const DenseArgs& a, const MeshView<T>& mv, T* V, TA* Gp, T* Rsm,
                          T* theta, cudaStream_t s, int* launches);
 int dense_chunk_rows(int cpad, int real_bytes);
+// Fused cluster Onorm (bsp_fused.cu); BSP_ERR_INVALID_ARG when the shape does not fit.
+template <typename T, typename TA>
+int launch_cholqr2_fused(const DenseArgs& a, const T* Y, T* Q, TA* Gp, int maxch, cudaStream_t s,
+                         int passes);
+void configure_fused_kernels();
+extern bool g_disable_fused;  // force the multi-kernel Onorm (A/B checks)
 
 // Projection / reconstruction (bsp_proj.cu)
 struct ProjArgs {
@@ -196,6 +206,7 @@ struct bsp_mesh {
   bsp_opts opts{};
   int real_bytes = 4;
   int32_t max_nb = 0, min_nb = 0;
+  int32_t max_deg = 0;     // largest number of intra-block neighbours of a vertex
   int64_t nnz = 0, intra_edges = 0;
   std::vector<int32_t> h_bptr, h_parent, h_level, h_root_off, h_c;
   std::vector<std::vector<int32_t>> waves;
@@ -227,6 +238,12 @@ struct bsp_mesh {
   void* d_rho = nullptr;
   void* d_X = nullptr;
   size_t cap_X = 0;
+  // Rayleigh-Ritz side branch: own workspace, stream and fork/join events
+  void* d_Gp_rr = nullptr;
+  void* d_Rsm_rr = nullptr;
+  size_t cap_Gp_rr = 0, cap_Rsm_rr = 0;
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // graph cache for the fixed-c schedule
   cudaGraphExec_t graph_exec = nullptr;
   int graph_c = -1, graph_t = -1, graph_launches = 0;

@@ -164,20 +164,22 @@ def test_fixed_c_fp64_grid_blocks():
         bsp.bsp_mesh_destroy(h)
 
 
-@pytest.mark.parametrize("prec", [bsp.BSP_PREC_MIXED, bsp.BSP_PREC_F32])
-@pytest.mark.parametrize("cs", [0, 8])
-def test_fixed_c_fp32_torus_tiles(prec, cs):
-    """128x128 torus, 16 tiles of 32x32 (several column slabs, chain of 16), c=64, 2 steps."""
+@pytest.mark.parametrize("prec,cs,c", [(bsp.BSP_PREC_MIXED, 0, 64), (bsp.BSP_PREC_F32, 0, 64),
+                                       (bsp.BSP_PREC_MIXED, 8, 64), (bsp.BSP_PREC_F32, 4, 64),
+                                       (bsp.BSP_PREC_MIXED, 0, 96), (bsp.BSP_PREC_F32, 2, 128)])
+def test_fixed_c_fp32_torus_tiles(prec, cs, c):
+    """128x128 torus, 16 tiles of 32x32 (chain of 16), 2 steps; c <= 64 takes the fused
+    cluster Onorm, c > 64 the multi-kernel one."""
     h, om, xyz, *_ , ptr, verts, parent = make_tile_mesh(128, 32, kind="torus", prec=prec,
                                                          cols_per_cta=cs)
     try:
-        starts = synth.gaussian_starts(ptr, parent, 64, seed=1)
-        bsp.bsp_oi_track(h, 64, 2, starts.astype(np.float32))
-        U_ref = O.oi_track(om, 64, 2, starts, delta=1e-2)
+        starts = synth.gaussian_starts(ptr, parent, c, seed=1)
+        bsp.bsp_oi_track(h, c, 2, starts.astype(np.float32))
+        U_ref = O.oi_track(om, c, 2, starts, delta=1e-2)
         compare_bases(h, om, U_ref, xyz, np.float32, SINE_F32, PROJ_F32)
         # device-resident projection + reconstruction with torch buffers
         Xd = torch.tensor(xyz, dtype=torch.float32, device="cuda")
-        Ed = torch.empty((16 * 64, 3), dtype=torch.float32, device="cuda")
+        Ed = torch.empty((16 * c, 3), dtype=torch.float32, device="cuda")
         Xo = torch.empty_like(Xd)
         bsp.bsp_project(h, Xd, bsp.BSP_DT_F32, 3, Ed)
         bsp.bsp_reconstruct(h, Ed, 3, Xo)
