@@ -263,6 +263,30 @@ int bsp_set_profiling(bsp_mesh* mesh, int32_t on);
 int bsp_get_kernel_times(const bsp_mesh* mesh, double* ms_out, int32_t* launches_out,
                          int32_t n_classes);
 
+/*
+ * Allocation-free orthonormalisation of one block (no counterpart in the
+ * paper: an interface for callers that may not allocate device memory).
+ * Q = Onorm(Y) by CholeskyQR2 in FP32 (the same fused kernel that Onorm uses
+ * inside bsp_oi_track), for callers that cannot call cudaMalloc while they
+ * run: a cudaMalloc can synchronise the whole device and has no latency
+ * bound, which a streaming pipeline orthonormalising submeshes as they
+ * arrive cannot afford, and some host applications own all device memory
+ * through their own allocator.  This call allocates nothing: its scratch is
+ * a fixed static device array of about 145 KiB (every GPU that loads the
+ * library holds it until the process exits).
+ *   Y, Q     device float [n x c], row-major (Q may alias Y); the caller owns both.
+ *   n, c     1 <= c <= n, n <= 2048, c <= 64; larger sizes return
+ *            BSP_ERR_INVALID_ARG without touching the GPU.
+ *   stream   cudaStream_t as void*; the call waits for its own work.
+ * The first call on each device looks up the scratch array's device address
+ * (and configures the kernel), so make that first call before any stream
+ * capture.  All calls share the one scratch array: calls that overlap on the
+ * GPU (other host threads, other streams) race and must be serialised by the
+ * caller.  Errors: BSP_ERR_INVALID_ARG, BSP_ERR_NUMERICAL (rank-deficient Y),
+ * BSP_ERR_CUDA.
+ */
+int bsp_onorm_noalloc(const float* Y, float* Q, int32_t n, int32_t c, void* stream);
+
 /* Thread-local message describing the last failure on this thread ("" if none). */
 const char* bsp_last_error(void);
 

@@ -80,6 +80,7 @@ def _load():
         "bsp_last_error": (C.c_char_p, []),
         "bsp_set_profiling": (C.c_int, [P, I32]),
         "bsp_get_kernel_times": (C.c_int, [P, P, P, I32]),
+        "bsp_onorm_noalloc": (C.c_int, [P, P, I32, I32, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -98,7 +99,7 @@ def exported_symbols():
             "bsp_get_stats", "bsp_get_edges", "bsp_get_block_csr", "bsp_set_edge_weights",
             "bsp_oi_track", "bsp_oi_track_dynamic", "bsp_get_block_c", "bsp_get_basis",
             "bsp_project", "bsp_reconstruct", "bsp_spmm", "bsp_last_error",
-            "bsp_set_profiling", "bsp_get_kernel_times"]
+            "bsp_set_profiling", "bsp_get_kernel_times", "bsp_onorm_noalloc"]
 
 
 def _check(code):
@@ -273,6 +274,12 @@ def bsp_get_kernel_times(mesh) -> dict:
     cnt = np.zeros(n, np.int32)
     _check(_lib.bsp_get_kernel_times(mesh, _ptr(ms), _ptr(cnt), n))
     return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNEL_CLASSES)}
+
+
+def bsp_onorm_noalloc(Y, Q, n, c, stream=None):
+    """Allocation-free Q = Onorm(Y) of one block (device float [n x c] buffers owned
+    by the caller), for callers that must not allocate device memory while running."""
+    _check(_lib.bsp_onorm_noalloc(_ptr(Y), _ptr(Q), n, c, _stream_ptr(stream)))
 
 
 def bsp_last_error() -> str:

@@ -26,6 +26,15 @@ thread_local Profiler* g_prof = nullptr;
 }
 
 namespace {
+thread_local std::string g_err;
+}
+
+namespace bsp {
+// The thread-local message returned by bsp_last_error().
+void set_last_error(const char* msg) { g_err = msg; }
+}
+
+namespace {
 
 // Collects the events of a profiled call after its stream has synchronised.
 struct ProfScope {
@@ -52,8 +61,6 @@ struct ProfScope {
     cudaGetLastError();
   }
 };
-
-thread_local std::string g_err;
 
 int fail(int code, const std::string& msg) {
   g_err = msg;

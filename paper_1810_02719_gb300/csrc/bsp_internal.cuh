@@ -168,6 +168,7 @@ template <typename T, typename TA>
 int launch_cholqr2_fused(const DenseArgs& a, const T* Y, T* Q, TA* Gp, int maxch, cudaStream_t s,
                          int passes);
 void configure_fused_kernels();
+void set_last_error(const char* msg);  // message for bsp_last_error() on this thread
 extern bool g_disable_fused;  // force the multi-kernel Onorm (A/B checks)
 
 // Projection / reconstruction (bsp_proj.cu)
