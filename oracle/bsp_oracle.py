@@ -456,3 +456,69 @@ def projector_rel_error(U: np.ndarray, W: np.ndarray, X: np.ndarray) -> float:
     a = U @ (U.T @ X)
     b = W @ (W.T @ X)
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+# ---------------------------------------------------------------------------
+# Differentiable block low-pass filter (not in the paper: the coarse denoising
+# filter v^ = U_c U_c^T v of Sec. 7.2 made differentiable in the per-edge
+# weights of an edge-weighted Laplacian that reduces to Sec. 3's at w = 1)
+# ---------------------------------------------------------------------------
+
+def filter_forward_torch(mesh: Mesh, X, w, c: int, t_max: int, starts, delta: float = 1e-2):
+    """Dense FP64 torch formulation of the filter, differentiable by torch autograd.
+
+    Per block in order: V0 = the parent's final basis, detached (stop-gradient;
+    a root starts from Onorm of its rows of ``starts``); t_max steps of
+    Algorithm 1 (Sec. 4) with L(w) = D(w) - C(w), C_ij = w_e on the block's
+    edges (``w`` concatenated over blocks in edge order), D_ii = sum_j C_ij,
+    exact dense solves and Householder QR with diag(R) > 0; then
+    X^_b = U_b U_b^T X_b.  Returns (X^ [n x 3] torch tensor, list of U).
+    """
+    import torch
+    out = torch.zeros_like(X)
+    U = [None] * mesh.k
+    woff = 0
+    root_off = {}
+    off = 0
+    for b in range(mesh.k):
+        if mesh.parent[b] < 0:
+            root_off[b] = off
+            off += mesh.blocks[b].verts.size
+    for b, blk in enumerate(mesh.blocks):
+        n_b = blk.verts.size
+        E_b = blk.edges.shape[0]
+        wb = w[woff:woff + E_b]
+        woff += E_b
+        i = torch.as_tensor(blk.edges[:, 0])
+        j = torch.as_tensor(blk.edges[:, 1])
+        C = torch.zeros(n_b, n_b, dtype=torch.float64)
+        C = C.index_put((i, j), wb).index_put((j, i), wb)
+        L = torch.diag(C.sum(dim=1)) - C
+        A = L + delta * torch.eye(n_b, dtype=torch.float64)
+        p = mesh.parent[b]
+        if p < 0:
+            V = torch.as_tensor(starts[root_off[b]:root_off[b] + n_b, :c], dtype=torch.float64)
+        else:
+            V = torch.as_tensor(row_transfer(U[p].detach().numpy(), n_b))
+        Q, R = torch.linalg.qr(V)
+        V = Q * torch.sign(torch.diagonal(R))[None, :]
+        for _ in range(t_max):
+            Y = torch.linalg.solve(A, V)
+            Q, R = torch.linalg.qr(Y)
+            V = Q * torch.sign(torch.diagonal(R))[None, :]
+        U[b] = V
+        vb = torch.as_tensor(blk.verts)
+        out = out.index_put((vb,), V @ (V.T @ X[vb]))
+    return out, U
+
+
+def filter_loss_grads(mesh: Mesh, X_noisy, X_clean, w, c: int, t_max: int, starts,
+                      delta: float = 1e-2):
+    """loss = ||filter(X_noisy) - X_clean||^2 and its gradients (d/dX_noisy, d/dw), FP64 autograd."""
+    import torch
+    X = torch.tensor(X_noisy, dtype=torch.float64, requires_grad=True)
+    W = torch.tensor(w, dtype=torch.float64, requires_grad=True)
+    Xh, _ = filter_forward_torch(mesh, X, W, c, t_max, starts, delta)
+    loss = ((Xh - torch.as_tensor(X_clean, dtype=torch.float64)) ** 2).sum()
+    loss.backward()
+    return float(loss), X.grad.numpy().copy(), W.grad.numpy().copy(), Xh.detach().numpy()

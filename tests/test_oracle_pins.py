@@ -439,3 +439,60 @@ def test_planted_mistakes_are_caught():
     for check, mut in mutants:
         with pytest.raises(AssertionError):
             check(O=mut)
+
+
+# --------------------------------------------------------------------------
+# Differentiable filter: the autograd oracle against central finite differences
+# --------------------------------------------------------------------------
+
+def test_filter_gradients_match_finite_differences():
+    """Sub-mesh gradients of ||filter(x) - x_clean||^2 by FP64 autograd vs central differences."""
+    import torch  # noqa: F401
+    N, T = 12, 6
+    clean, noisy, faces = synth.noisy_torus(N, seed=3)
+    # an open patch: the torus grid's interior tiles only
+    ptr, verts = synth.tile_partition(N, T)
+    parent = synth.raster_chain(len(ptr) - 1)
+    mesh = O.build_mesh(N * N, ptr, verts, parent, faces=faces, weight_mode=O.WEIGHT_EDGE)
+    E = sum(b.edges.shape[0] for b in mesh.blocks)
+    rng = np.random.default_rng(0)
+    w = 1.0 + 0.3 * rng.random(E)
+    c, t = 5, 3
+    starts = synth.gaussian_starts(ptr, parent, c, seed=4)
+    loss, gx, gw, _ = O.filter_loss_grads(mesh, noisy, clean, w, c, t, starts)
+    # The warm start is detached (stop-gradient), so the gradient is the
+    # derivative of the same computation with every block's start frozen at its
+    # unperturbed value: every block a root whose start is given.
+    import torch
+    _, U = O.filter_forward_torch(mesh, torch.tensor(noisy), torch.tensor(w), c, t, starts)
+    frozen = np.concatenate([
+        starts[:T * T, :c] if mesh.parent[b] < 0 else O.row_transfer(U[mesh.parent[b]].numpy(), T * T)
+        for b in range(mesh.k)])
+    roots = np.full(mesh.k, -1)
+    mesh_r = O.build_mesh(N * N, ptr, verts, roots, faces=faces, weight_mode=O.WEIGHT_EDGE)
+    _, gx_r, gw_r, _ = O.filter_loss_grads(mesh_r, noisy, clean, w, c, t, frozen)
+    assert np.allclose(gw_r, gw, rtol=1e-8, atol=1e-12)
+    assert np.allclose(gx_r, gx, rtol=1e-8, atol=1e-12)
+
+    def f(xv, wv):
+        return O.filter_loss_grads(mesh_r, xv, clean, wv, c, t, frozen)[0]
+
+    h = 1e-6
+    for e in rng.choice(E, 6, replace=False):
+        wp, wm = w.copy(), w.copy()
+        wp[e] += h
+        wm[e] -= h
+        fd = (f(noisy, wp) - f(noisy, wm)) / (2 * h)
+        assert fd == pytest.approx(gw[e], rel=1e-5, abs=1e-9)
+    for k in rng.choice(N * N * 3, 6, replace=False):
+        xp, xm = noisy.copy(), noisy.copy()
+        xp.flat[k] += h
+        xm.flat[k] -= h
+        fd = (f(xp, w) - f(xm, w)) / (2 * h)
+        assert fd == pytest.approx(gx.flat[k], rel=1e-5, abs=1e-9)
+    # at w = 1 the filter's Laplacian is the combinatorial one of Sec. 3
+    mesh1 = O.build_mesh(N * N, ptr, verts, parent, faces=faces)
+    U = O.oi_track(mesh1, c, t, starts, rr=False)
+    _, _, _, xh = O.filter_loss_grads(mesh, noisy, clean, np.ones(E), c, t, starts)
+    ref = O.reconstruct(mesh1, U, O.project(mesh1, U, noisy), 3)
+    assert np.allclose(xh, ref, atol=1e-10)
