@@ -231,6 +231,33 @@ int bsp_reconstruct(bsp_mesh* mesh, const void* E, int32_t cols, void* X_out, vo
  */
 int bsp_spmm(bsp_mesh* mesh, const void* P, void* Y, int32_t c, void* stream);
 
+/*
+ * Block low-pass filter X^ = U U^T X (Sec. 7.2, coarse denoising) made
+ * differentiable (not in the paper): every block runs t_max steps of
+ * Algorithm 1 on L(w) = D(w) - C(w), where the per-edge weights w are those of
+ * bsp_set_edge_weights (BSP_W_EDGE; the paper's combinatorial L at w = 1),
+ * with Onorm after every step and no Rayleigh-Ritz; the start of a block is
+ * its parent's final basis, treated as a constant (no gradient flows into
+ * the parent).  All steps are checkpointed on the device for the backward.
+ *   c, t_max   columns (1 <= c <= 64) and unrolled steps (>= 1).
+ *   V0_roots   host or device real [sum over roots of n_b, c].
+ *   X, X_out   host or device real [n x 3].
+ * Requires opts.z = 1.  The bases become the mesh's tracked bases.
+ */
+int bsp_filter_forward(bsp_mesh* mesh, int32_t c, int32_t t_max, const void* V0_roots,
+                       const void* X, void* X_out, void* stream);
+
+/*
+ * Gradients of a loss through the last bsp_filter_forward: given
+ * G = dLoss/dX^ (device real [n x 3]) and the filter input X (device real
+ * [n x 3]), writes dX = U U^T G (device real [n x 3]) and dW = dLoss/dw
+ * (device real [E_intra], order of bsp_get_edges).  The adjoint solves with
+ * (L + delta I) by the same CG (one solve per unrolled step) and uses
+ * dLoss/dA = -Lambda Y^T for A = L(w) + delta I.
+ */
+int bsp_filter_backward(bsp_mesh* mesh, const void* G, const void* X, void* dX, void* dW,
+                        void* stream);
+
 /* Kernel classes reported by bsp_get_kernel_times, in this order. */
 typedef enum bsp_kernel_class {
   BSP_KC_INIT = 0,     /* start matrices (root rows / parent row transfer) */

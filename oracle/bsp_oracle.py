@@ -521,4 +521,4 @@ def filter_loss_grads(mesh: Mesh, X_noisy, X_clean, w, c: int, t_max: int, start
     Xh, _ = filter_forward_torch(mesh, X, W, c, t_max, starts, delta)
     loss = ((Xh - torch.as_tensor(X_clean, dtype=torch.float64)) ** 2).sum()
     loss.backward()
-    return float(loss), X.grad.numpy().copy(), W.grad.numpy().copy(), Xh.detach().numpy()
+    return float(loss.detach()), X.grad.numpy().copy(), W.grad.numpy().copy(), Xh.detach().numpy()

@@ -81,6 +81,8 @@ def _load():
         "bsp_set_profiling": (C.c_int, [P, I32]),
         "bsp_get_kernel_times": (C.c_int, [P, P, P, I32]),
         "bsp_onorm_noalloc": (C.c_int, [P, P, I32, I32, P]),
+        "bsp_filter_forward": (C.c_int, [P, I32, I32, P, P, P, P]),
+        "bsp_filter_backward": (C.c_int, [P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -99,7 +101,8 @@ def exported_symbols():
             "bsp_get_stats", "bsp_get_edges", "bsp_get_block_csr", "bsp_set_edge_weights",
             "bsp_oi_track", "bsp_oi_track_dynamic", "bsp_get_block_c", "bsp_get_basis",
             "bsp_project", "bsp_reconstruct", "bsp_spmm", "bsp_last_error",
-            "bsp_set_profiling", "bsp_get_kernel_times", "bsp_onorm_noalloc"]
+            "bsp_set_profiling", "bsp_get_kernel_times", "bsp_onorm_noalloc",
+            "bsp_filter_forward", "bsp_filter_backward"]
 
 
 def _check(code):
@@ -280,6 +283,16 @@ def bsp_onorm_noalloc(Y, Q, n, c, stream=None):
     """Allocation-free Q = Onorm(Y) of one block (device float [n x c] buffers owned
     by the caller), for callers that must not allocate device memory while running."""
     _check(_lib.bsp_onorm_noalloc(_ptr(Y), _ptr(Q), n, c, _stream_ptr(stream)))
+
+
+def bsp_filter_forward(mesh, c, t_max, V0_roots, X, X_out, stream=None):
+    _check(_lib.bsp_filter_forward(mesh, c, t_max, _ptr(V0_roots), _ptr(X), _ptr(X_out),
+                                   _stream_ptr(stream)))
+
+
+def bsp_filter_backward(mesh, G, X, dX, dW, stream=None):
+    _check(_lib.bsp_filter_backward(mesh, _ptr(G), _ptr(X), _ptr(dX), _ptr(dW),
+                                    _stream_ptr(stream)))
 
 
 def bsp_last_error() -> str:

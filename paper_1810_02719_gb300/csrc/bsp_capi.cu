@@ -134,6 +134,7 @@ void configure_once() {
   std::call_once(flag, [] {
     configure_cg_kernels();
     configure_dense_kernels();
+    configure_adjoint_kernels();
   });
 }
 
@@ -144,7 +145,8 @@ void release(bsp_mesh* m) {
                   m->d_root_off, m->d_waves, m->d_cb, m->d_cpar, m->d_ceoff, m->d_col,
                   m->d_wt, m->d_diag, m->d_status, m->d_cgstats, m->d_U, m->d_Y, m->d_starts,
                   m->d_Gp, m->d_Rsm, m->d_theta, m->d_action, m->d_round, m->d_forced,
-                  m->d_gcol, m->d_rho, m->d_X, m->d_Gp_rr, m->d_Rsm_rr};
+                  m->d_gcol, m->d_rho, m->d_X, m->d_Gp_rr, m->d_Rsm_rr, m->d_ckV, m->d_ckY,
+                  m->d_adj_gp, m->d_adj_thin, m->d_adj_rows};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (m->graph_exec) cudaGraphExecDestroy(m->graph_exec);
@@ -714,6 +716,131 @@ int track_dynamic(bsp_mesh* M, const void* X, double tol, int c_min, int c_max, 
   return stream_error_status(M, s);
 }
 
+// ------------------------------------------------------- low-pass filter
+// Forward: Algorithm 1 without Rayleigh-Ritz, every step checkpointed
+// (V_0..V_t in d_ckV, Y_1..Y_t in d_ckY; Onorm by CholeskyQR2 at every step),
+// then X_out = U U^T X.  The next block's start is the parent's V_t.
+template <typename T, typename TA>
+int filter_forward(bsp_mesh* M, int c, int t_max, const void* V0, cudaStream_t s) {
+  if (c < 1 || c > 64 || c > M->min_nb)
+    return fail(BSP_ERR_INVALID_ARG, "the filter takes 1 <= c <= 64, c <= smallest block");
+  if (t_max < 1) return fail(BSP_ERR_INVALID_ARG, "t_max must be >= 1");
+  if (sizeof(T) == 8 && c > 64) return fail(BSP_ERR_INVALID_ARG, "FP64 precision supports c <= 64");
+  int maxbatch = 0;
+  for (auto& w : M->waves) maxbatch = std::max(maxbatch, (int)w.size());
+  int rc;
+  if ((rc = ensure_workspace<T, TA>(M, c, maxbatch)) != BSP_OK) return rc;
+  const size_t nc = (size_t)M->n * c;
+  if ((rc = ensure(&M->d_ckV, &M->cap_ckV, (t_max + 1) * nc * sizeof(T))) ||
+      (rc = ensure(&M->d_ckY, &M->cap_ckY, t_max * nc * sizeof(T))) ||
+      (rc = ensure(&M->d_starts, &M->cap_starts, (size_t)M->root_rows * c * sizeof(T))))
+    return rc;
+  if ((rc = to_device(M->d_starts, V0, (size_t)M->root_rows * c * sizeof(T), s))) return rc;
+  M->h_c.assign(M->k, c);
+  std::vector<int32_t> ce(M->k + 1, 0);
+  for (int b = 0; b < M->k; ++b) ce[b + 1] = ce[b] + c;
+  CU(cudaMemcpyAsync(M->d_cb, M->h_c.data(), sizeof(int32_t) * M->k, cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(M->d_ceoff, ce.data(), sizeof(int32_t) * (M->k + 1), cudaMemcpyHostToDevice, s));
+  CU(cudaMemsetAsync(M->d_status, 0, sizeof(int), s));
+  CU(cudaMemsetAsync(M->d_cgstats, 0, sizeof(CgStats), s));
+  if ((rc = stage_onorm_lists(M)) != BSP_OK) return rc;
+  const MeshView<T> mv = view<T>(M);
+  T* ckV = (T*)M->d_ckV;
+  T* ckY = (T*)M->d_ckY;
+  int launches = 0;
+  for (int l = 0; l < (int)M->waves.size(); ++l) {
+    const int nbw = (int)M->waves[l].size();
+    const int32_t* batch = M->d_waves + M->h_wave_off[l];
+    int wmax = 0;
+    for (int b : M->waves[l]) wmax = std::max(wmax, M->h_bptr[b + 1] - M->h_bptr[b]);
+    launch_init_starts<T>(batch, nbw, M->d_bptr, M->d_parent, M->d_root_off, M->d_cb, M->d_cb,
+                          (const T*)M->d_starts, c, ckV, c, wmax, c, s, ckV + t_max * nc);
+    ++launches;
+    std::vector<int32_t> need;
+    for (int b : M->waves[l]) {
+      int p = M->h_parent[b];
+      if (p < 0 || (M->h_bptr[b + 1] - M->h_bptr[b]) != (M->h_bptr[p + 1] - M->h_bptr[p]))
+        need.push_back(b);
+    }
+    DenseArgs da{batch, nbw, M->d_bptr, M->d_cb, c, c, wmax, M->d_status};
+    if (!need.empty()) {
+      DenseArgs dn = da;
+      if ((int)need.size() != nbw) {
+        dn.batch = M->d_waves + M->k + M->h_wave_off[l];
+        dn.nbatch = (int)need.size();
+      }
+      if ((rc = launch_cholqr2<T, TA>(dn, ckV, ckV, (TA*)M->d_Gp, (T*)M->d_Rsm, s, &launches)))
+        return fail(rc, "launch failed (Onorm of start)");
+    }
+    CgArgs ca{batch, nbw, M->d_cb, c, M->opts.z, M->opts.delta, M->opts.cg_rtol,
+              M->opts.cg_max_steps, M->d_status, M->d_cgstats, M->max_deg};
+    const int cs = pick_cs(M, nbw, c, sizeof(T));
+    for (int t = 1; t <= t_max; ++t) {
+      if ((rc = launch_cg<T>(mv, ckV + (t - 1) * nc, ckY + (t - 1) * nc, ca, cs, wmax, c, s)))
+        return fail(rc, "CG launch failed");
+      ++launches;
+      if ((rc = launch_cholqr2<T, TA>(da, ckY + (t - 1) * nc, ckV + t * nc, (TA*)M->d_Gp,
+                                      (T*)M->d_Rsm, s, &launches)))
+        return fail(rc, "launch failed (Onorm)");
+    }
+  }
+  // the final bases become the mesh's tracked bases (ld = c)
+  CU(cudaMemcpyAsync(M->d_U, ckV + t_max * nc, nc * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  M->filter_c = c;
+  M->filter_t = t_max;
+  M->tracked = true;
+  M->stats.gpu_launches = launches;
+  return stream_error_status(M, s);
+}
+
+template <typename T, typename TA>
+int filter_backward(bsp_mesh* M, const T* dG, const T* dX, T* dW, cudaStream_t s) {
+  const int c = M->filter_c, t_max = M->filter_t;
+  const int cpad = (c + 3) & ~3;
+  const int maxch = adjoint_maxch(M->max_nb);
+  const size_t nc = (size_t)M->n * c;
+  int rc;
+  if ((rc = ensure(&M->d_adj_gp, &M->cap_adj_gp,
+                   ((size_t)M->k * maxch * cpad * cpad + 2 * (size_t)M->k * cpad * cpad) * sizeof(TA))) ||
+      (rc = ensure(&M->d_adj_thin, &M->cap_adj_thin, (size_t)M->k * 3 * 128 * 2 * sizeof(T))) ||
+      (rc = ensure(&M->d_adj_rows, &M->cap_adj_rows, 3 * nc * sizeof(T))))
+    return rc;
+  CU(cudaMemsetAsync(M->d_status, 0, sizeof(int), s));
+  CU(cudaMemsetAsync(M->d_cgstats, 0, sizeof(CgStats), s));
+  AdjointArgs aa;
+  aa.batch = M->d_waves;
+  aa.k = M->k;
+  aa.bptr = M->d_bptr;
+  aa.cb = M->d_cb;
+  aa.verts = M->d_verts;
+  aa.blk_row = M->d_blk_row;
+  aa.eoff = M->d_eoff;
+  aa.n = M->n;
+  aa.n_edges = M->intra_edges;
+  aa.ld = c;
+  aa.c = c;
+  aa.t_max = t_max;
+  aa.max_nb = M->max_nb;
+  aa.X = dX;
+  aa.G = dG;
+  aa.ckV = M->d_ckV;
+  aa.ckY = M->d_ckY;
+  aa.ws_gp = M->d_adj_gp;
+  aa.ws_thin = M->d_adj_thin;
+  aa.ws_rows = M->d_adj_rows;
+  aa.dW = dW;
+  aa.status = M->d_status;
+  aa.cgstats = M->d_cgstats;
+  aa.z = M->opts.z;
+  aa.delta = M->opts.delta;
+  aa.rtol = M->opts.cg_rtol;
+  aa.max_steps = M->opts.cg_max_steps;
+  aa.max_deg = M->max_deg;
+  aa.cs = pick_cs(M, M->k, c, sizeof(T));
+  if ((rc = launch_filter_backward<T, TA>(aa, view<T>(M), s))) return fail(rc, "adjoint launch failed");
+  return stream_error_status(M, s);
+}
+
 // --------------------------------------------------------- scratch buffers
 struct Scratch {
   void* p = nullptr;
@@ -725,6 +852,43 @@ int scratch(int slot, size_t bytes, void** out) {
   int rc = ensure(&g_scratch[slot].p, &g_scratch[slot].cap, bytes);
   *out = g_scratch[slot].p;
   return rc;
+}
+
+// X_out = U U^T X for n x 3 coordinates (real type), through the projection
+// and reconstruction kernels; X and X_out host or device.
+int bsp_reconstruct_projected(bsp_mesh* M, const void* X, void* X_out, cudaStream_t s) {
+  const int rb = M->real_bytes;
+  int64_t erows = 0;
+  int cmax = 0;
+  for (int b = 0; b < M->k; ++b) {
+    erows += M->h_c[b];
+    cmax = std::max(cmax, M->h_c[b]);
+  }
+  const void* dX = X;
+  int rc;
+  if (!is_device_ptr(X)) {
+    void* t;
+    if ((rc = scratch(0, (size_t)M->n * 3 * rb, &t))) return rc;
+    CU(cudaMemcpyAsync(t, X, (size_t)M->n * 3 * rb, cudaMemcpyHostToDevice, s));
+    dX = t;
+  }
+  void* dE;
+  if ((rc = scratch(1, (size_t)erows * 3 * rb, &dE))) return rc;
+  void* dO = X_out;
+  const bool host_out = !is_device_ptr(X_out);
+  if (host_out && (rc = scratch(2, (size_t)M->n * 3 * rb, &dO))) return rc;
+  ProjArgs pa{M->d_bptr, M->d_verts, M->d_cb, M->d_ceoff, M->k, M->c_cap, cmax, M->max_nb, 3};
+  if (rb == 8) {
+    rc = launch_project<double>(pa, (const double*)M->d_U, dX, BSP_DT_F64, (double*)dE, s);
+    if (!rc) rc = launch_reconstruct<double>(pa, (const double*)M->d_U, (const double*)dE, (double*)dO, s);
+  } else {
+    rc = launch_project<float>(pa, (const float*)M->d_U, dX, BSP_DT_F32, (float*)dE, s);
+    if (!rc) rc = launch_reconstruct<float>(pa, (const float*)M->d_U, (const float*)dE, (float*)dO, s);
+  }
+  if (rc) return fail(rc, "projection launch failed");
+  if (host_out) CU(cudaMemcpyAsync(X_out, dO, (size_t)M->n * 3 * rb, cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  return BSP_OK;
 }
 
 }  // namespace
@@ -1003,6 +1167,44 @@ int bsp_spmm(bsp_mesh* M, const void* P, void* Y, int32_t c, void* stream) {
   CU(cudaGetLastError());
   M->stats.gpu_launches = 1;
   return BSP_OK;
+}
+
+int bsp_filter_forward(bsp_mesh* M, int32_t c, int32_t t_max, const void* V0_roots,
+                       const void* X, void* X_out, void* stream) {
+  g_err.clear();
+  if (!M || !V0_roots || !X || !X_out) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
+  if (M->opts.z != 1) return fail(BSP_ERR_INVALID_ARG, "the filter adjoint supports z = 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  ProfScope ps(M);
+  int rc;
+  switch (M->opts.precision) {
+    case BSP_PREC_F64: rc = filter_forward<double, double>(M, c, t_max, V0_roots, s); break;
+    case BSP_PREC_F32: rc = filter_forward<float, float>(M, c, t_max, V0_roots, s); break;
+    default: rc = filter_forward<float, double>(M, c, t_max, V0_roots, s); break;
+  }
+  if (rc != BSP_OK) return rc;
+  return bsp_reconstruct_projected(M, X, X_out, s);
+}
+
+int bsp_filter_backward(bsp_mesh* M, const void* G, const void* X, void* dX, void* dW,
+                        void* stream) {
+  g_err.clear();
+  if (!M || !G || !X || !dX || !dW) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
+  if (M->filter_t < 1) return fail(BSP_ERR_INVALID_ARG, "call bsp_filter_forward first");
+  if (!is_device_ptr(G) || !is_device_ptr(X) || !is_device_ptr(dX) || !is_device_ptr(dW))
+    return fail(BSP_ERR_INVALID_ARG, "bsp_filter_backward takes device pointers");
+  cudaStream_t s = (cudaStream_t)stream;
+  ProfScope ps(M);
+  int rc = bsp_reconstruct_projected(M, G, dX, s);   // dL/dX = U U^T G
+  if (rc != BSP_OK) return rc;
+  switch (M->opts.precision) {
+    case BSP_PREC_F64:
+      return filter_backward<double, double>(M, (const double*)G, (const double*)X, (double*)dW, s);
+    case BSP_PREC_F32:
+      return filter_backward<float, float>(M, (const float*)G, (const float*)X, (float*)dW, s);
+    default:
+      return filter_backward<float, double>(M, (const float*)G, (const float*)X, (float*)dW, s);
+  }
 }
 
 int bsp_set_profiling(bsp_mesh* M, int32_t on) {

@@ -23,7 +23,7 @@ constexpr int kMaxC = 128;
 template <typename T>
 __global__ void k_init_starts(const int32_t* batch, const int32_t* bptr, const int32_t* parent,
                               const int32_t* root_off, const int32_t* cb, const int32_t* cpar,
-                              const T* starts, int ld_start, T* U, int ld) {
+                              const T* starts, int ld_start, T* U, int ld, const T* Usrc) {
   const int b = batch[blockIdx.y];
   const int c = cb[b];
   const int r0 = bptr[b], nb = bptr[b + 1] - r0;
@@ -36,7 +36,7 @@ __global__ void k_init_starts(const int32_t* batch, const int32_t* bptr, const i
     } else {
       const int rp0 = bptr[p], np = bptr[p + 1] - rp0;
       const int src = (int)(((int64_t)i * np) / nb);
-      v = j < cpar[b] ? U[(size_t)(rp0 + src) * ld + j] : T(0);
+      v = j < cpar[b] ? Usrc[(size_t)(rp0 + src) * ld + j] : T(0);
     }
     U[(size_t)(r0 + i) * ld + j] = v;
   }
@@ -255,12 +255,12 @@ template <typename T>
 void launch_init_starts(const int32_t* batch, int nbatch, const int32_t* bptr,
                         const int32_t* parent, const int32_t* root_off, const int32_t* cb,
                         const int32_t* cpar, const T* starts, int ld_start, T* U, int ld,
-                        int max_nb, int cmax, cudaStream_t s) {
+                        int max_nb, int cmax, cudaStream_t s, const T* Usrc) {
   const int per = max_nb * cmax;
   dim3 grid((per + 255) / 256 < 64 ? (per + 255) / 256 : 64, nbatch);
   prof_begin(KC_INIT, s);
   k_init_starts<T><<<grid, 256, 0, s>>>(batch, bptr, parent, root_off, cb, cpar, starts, ld_start,
-                                        U, ld);
+                                        U, ld, Usrc ? Usrc : U);
   prof_end(KC_INIT, s);
 }
 
@@ -290,11 +290,12 @@ int launch_dyn_grow(const int32_t* batch, int nbatch, const int32_t* bptr, int32
 
 template void launch_init_starts<float>(const int32_t*, int, const int32_t*, const int32_t*,
                                         const int32_t*, const int32_t*, const int32_t*,
-                                        const float*, int, float*, int, int, int, cudaStream_t);
+                                        const float*, int, float*, int, int, int, cudaStream_t,
+                                        const float*);
 template void launch_init_starts<double>(const int32_t*, int, const int32_t*, const int32_t*,
                                          const int32_t*, const int32_t*, const int32_t*,
                                          const double*, int, double*, int, int, int,
-                                         cudaStream_t);
+                                         cudaStream_t, const double*);
 template int launch_dyn_decide<float, double>(const int32_t*, int, const int32_t*, const int32_t*,
                                               const float*, const float*, int, int32_t*, int32_t*,
                                               const int32_t*, double, int, int, float*, double*,

@@ -187,7 +187,7 @@ template <typename T>
 void launch_init_starts(const int32_t* batch, int nbatch, const int32_t* bptr,
                         const int32_t* parent, const int32_t* root_off, const int32_t* cb,
                         const int32_t* cpar, const T* starts, int ld_start, T* U, int ld,
-                        int max_nb, int cmax, cudaStream_t s);
+                        int max_nb, int cmax, cudaStream_t s, const T* Usrc = nullptr);
 template <typename T, typename TA>
 int launch_dyn_decide(const int32_t* batch, int nbatch, const int32_t* bptr, const int32_t* verts,
                       const T* X, const T* U, int ld, int32_t* cb, int32_t* action,
@@ -197,6 +197,24 @@ template <typename T, typename TA>
 int launch_dyn_grow(const int32_t* batch, int nbatch, const int32_t* bptr, int32_t* cb,
                     const int32_t* round, T* U, int ld, const T* gcol, uint64_t seed,
                     int c_step, int max_nb, cudaStream_t s);
+
+// Adjoint of the low-pass filter (bsp_adjoint.cu)
+struct AdjointArgs {
+  const int32_t* batch; int k;          // all blocks
+  const int32_t* bptr; const int32_t* cb; const int32_t* verts;
+  const int32_t* blk_row; const int32_t* eoff;
+  int64_t n; int64_t n_edges; int ld; int c; int t_max; int max_nb;
+  const void* X; const void* G;         // device [n x 3]
+  const void* ckV; const void* ckY;     // checkpoints: V_0..V_t, Y_1..Y_t, each [n x ld]
+  void* ws_gp; void* ws_thin; void* ws_rows;
+  void* dW;                             // device [n_edges]
+  int* status; CgStats* cgstats;
+  int z; double delta; double rtol; int max_steps; int max_deg; int cs;
+};
+int adjoint_maxch(int max_nb);
+template <typename T, typename TA>
+int launch_filter_backward(const AdjointArgs& aa, const MeshView<T>& mv, cudaStream_t s);
+void configure_adjoint_kernels();
 
 }  // namespace bsp
 
@@ -250,6 +268,14 @@ struct bsp_mesh {
   int graph_c = -1, graph_t = -1, graph_launches = 0;
   cudaStream_t graph_stream = nullptr;
   bsp_stats stats{};
+  // low-pass filter checkpoints (last bsp_filter_forward)
+  void* d_ckV = nullptr;
+  void* d_ckY = nullptr;
+  void* d_adj_gp = nullptr;
+  void* d_adj_thin = nullptr;
+  void* d_adj_rows = nullptr;
+  size_t cap_ckV = 0, cap_ckY = 0, cap_adj_gp = 0, cap_adj_thin = 0, cap_adj_rows = 0;
+  int filter_c = 0, filter_t = -1;
   // optional per-kernel-class timing (eager launches, CUDA events)
   int profiling = 0;
   double prof_ms[bsp::KC_COUNT] = {};

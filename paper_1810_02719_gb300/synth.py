@@ -19,7 +19,8 @@ import numpy as np
 __all__ = [
     "grid_heightfield", "torus", "tile_partition", "raster_chain",
     "gaussian_starts", "bfs_partition", "block_forest", "torus_frames",
-    "noisy_torus", "path_edges", "cycle_edges", "grid_edges",
+    "noisy_torus", "path_edges", "cycle_edges", "grid_edges", "rect_partition",
+    "noisy_torus_patch",
 ]
 
 
@@ -142,6 +143,35 @@ def tile_partition(N: int, T: int):
             g = (bi * T + li) * N + (bj * T + lj)
             verts[ptr[b]:ptr[b + 1]] = g.ravel()
     return ptr, verts
+
+
+def rect_partition(R: int, C: int, TR: int, TC: int):
+    """Partition an R x C vertex grid into (R/TR)(C/TC) rectangular tiles of TR x TC.
+
+    Raster tile order; row-major vertex order inside a tile.
+    Returns (block_ptr int32 [k+1], block_verts int32 [R*C]).
+    """
+    assert R % TR == 0 and C % TC == 0
+    nr, nc = R // TR, C // TC
+    ptr = np.arange(nr * nc + 1, dtype=np.int32) * (TR * TC)
+    verts = np.empty(R * C, dtype=np.int32)
+    li, lj = np.meshgrid(np.arange(TR), np.arange(TC), indexing="ij")
+    for bi in range(nr):
+        for bj in range(nc):
+            b = bi * nc + bj
+            verts[ptr[b]:ptr[b + 1]] = ((bi * TR + li) * C + (bj * TC + lj)).ravel()
+    return ptr, verts
+
+
+def noisy_torus_patch(R: int = 40, C: int = 50, N: int = 512, noise_factor: float = 0.3,
+                      seed: int = 0):
+    """An open R x C patch (rows/columns 0..R-1, 0..C-1) of the N x N noisy torus.
+
+    Returns (clean xyz [R*C, 3], noisy xyz [R*C, 3], faces of the open R x C grid).
+    """
+    clean, noisy, _ = noisy_torus(N=N, noise_factor=noise_factor, seed=seed)
+    idx = (np.arange(R)[:, None] * N + np.arange(C)[None, :]).ravel()
+    return clean[idx].copy(), noisy[idx].copy(), _quad_faces(R, C, wrap=False)
 
 
 def raster_chain(k: int) -> np.ndarray:
