@@ -224,6 +224,17 @@ int bsp_project(bsp_mesh* mesh, const void* X, int32_t x_dtype, int32_t cols, vo
 int bsp_reconstruct(bsp_mesh* mesh, const void* E, int32_t cols, void* X_out, void* stream);
 
 /*
+ * Reconstruction X~[b] = U[b] E[b] on tcgen05 tensor cores with BF16 operands
+ * (U and E rounded to bfloat16) and FP32 accumulation and output, for wide
+ * coordinate matrices (all frames of a dynamic mesh, Sec. 7.3).
+ *   E      device float [sum_b c_b x cols]; X_out device float [n x cols].
+ * Requires F32 or MIXED precision and c <= 128.  (bsp_project takes the
+ * tensor-core path itself when x_dtype is BSP_DT_BF16, cols % 8 == 0 and
+ * cols >= 64.)  Errors: BSP_ERR_INVALID_ARG, BSP_ERR_TIMEOUT, BSP_ERR_CUDA.
+ */
+int bsp_reconstruct_bf16(bsp_mesh* mesh, const float* E, int32_t cols, float* X_out, void* stream);
+
+/*
  * Standalone operator product Y = (L + delta I) P for all blocks at once (the
  * sparse x tall-skinny kernel inside every CG step of R^z U, Sec. 4).
  *   P, Y    device real [n x c], rows in block order (row block_ptr[b] + i is

@@ -83,6 +83,7 @@ def _load():
         "bsp_onorm_noalloc": (C.c_int, [P, P, I32, I32, P]),
         "bsp_filter_forward": (C.c_int, [P, I32, I32, P, P, P, P]),
         "bsp_filter_backward": (C.c_int, [P, P, P, P, P, P]),
+        "bsp_reconstruct_bf16": (C.c_int, [P, P, I32, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -102,7 +103,7 @@ def exported_symbols():
             "bsp_oi_track", "bsp_oi_track_dynamic", "bsp_get_block_c", "bsp_get_basis",
             "bsp_project", "bsp_reconstruct", "bsp_spmm", "bsp_last_error",
             "bsp_set_profiling", "bsp_get_kernel_times", "bsp_onorm_noalloc",
-            "bsp_filter_forward", "bsp_filter_backward"]
+            "bsp_filter_forward", "bsp_filter_backward", "bsp_reconstruct_bf16"]
 
 
 def _check(code):
@@ -256,6 +257,10 @@ def bsp_project(mesh, X, x_dtype, cols, E_out, stream=None):
 
 def bsp_reconstruct(mesh, E, cols, X_out, stream=None):
     _check(_lib.bsp_reconstruct(mesh, _ptr(E), cols, _ptr(X_out), _stream_ptr(stream)))
+
+
+def bsp_reconstruct_bf16(mesh, E, cols, X_out, stream=None):
+    _check(_lib.bsp_reconstruct_bf16(mesh, _ptr(E), cols, _ptr(X_out), _stream_ptr(stream)))
 
 
 def bsp_spmm(mesh, P, Y, c, stream=None):

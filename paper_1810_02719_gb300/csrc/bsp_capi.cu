@@ -135,6 +135,7 @@ void configure_once() {
     configure_cg_kernels();
     configure_dense_kernels();
     configure_adjoint_kernels();
+    configure_tc_kernels();
   });
 }
 
@@ -168,6 +169,7 @@ int stream_error_status(bsp_mesh* m, cudaStream_t s) {
   m->stats.jacobi_sweeps = cs.jacobi_sweeps;
   if (st & ST_NUMERICAL)
     return fail(BSP_ERR_NUMERICAL, "Gram matrix not positive definite or non-finite values");
+  if (st & ST_TIMEOUT) return fail(BSP_ERR_TIMEOUT, "a bounded device wait expired");
   if (st & ST_NOT_CONVERGED)
     return fail(BSP_ERR_NOT_CONVERGED,
                 std::to_string(cs.not_converged) + " CG solves hit the step cap");
@@ -1106,12 +1108,25 @@ int bsp_project(bsp_mesh* M, const void* X, int32_t x_dtype, int32_t cols, void*
   if (host_out && (rc = scratch(1, (size_t)erows * cols * rb, &dE))) return rc;
   ProjArgs pa{M->d_bptr, M->d_verts, M->d_cb, M->d_ceoff, M->k, M->c_cap, cmax, M->max_nb, cols};
   ProfScope ps(M);
-  rc = rb == 8 ? launch_project<double>(pa, (const double*)M->d_U, dX, x_dtype, (double*)dE, s)
-               : launch_project<float>(pa, (const float*)M->d_U, dX, x_dtype, (float*)dE, s);
+  bool tc = false;
+  if (x_dtype == BSP_DT_BF16 && rb == 4 && cols % 8 == 0 && cols >= 64 && cmax <= 256) {
+    CU(cudaMemsetAsync(M->d_status, 0, sizeof(int), s));
+    rc = launch_project_tc(pa, (const float*)M->d_U, dX, (float*)dE, M->d_status, s);
+    tc = rc == BSP_OK;
+  }
+  if (!tc) {
+    rc = rb == 8 ? launch_project<double>(pa, (const double*)M->d_U, dX, x_dtype, (double*)dE, s)
+                 : launch_project<float>(pa, (const float*)M->d_U, dX, x_dtype, (float*)dE, s);
+  }
   if (rc) return fail(rc, "projection launch failed");
   if (host_out) CU(cudaMemcpyAsync(E_out, dE, (size_t)erows * cols * rb, cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
   M->stats.gpu_launches = 1;
+  if (tc) {
+    int st = 0;
+    CU(cudaMemcpy(&st, M->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st & ST_TIMEOUT) return fail(BSP_ERR_TIMEOUT, "a bounded device wait expired");
+  }
   return BSP_OK;
 }
 
@@ -1146,6 +1161,31 @@ int bsp_reconstruct(bsp_mesh* M, const void* E, int32_t cols, void* X_out, void*
   if (rc) return fail(rc, "reconstruction launch failed");
   if (host_out) CU(cudaMemcpyAsync(X_out, dX, (size_t)M->n * cols * rb, cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
+  M->stats.gpu_launches = 1;
+  return BSP_OK;
+}
+
+int bsp_reconstruct_bf16(bsp_mesh* M, const float* E, int32_t cols, float* X_out, void* stream) {
+  g_err.clear();
+  if (!M || !E || !X_out) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
+  if (!M->tracked) return fail(BSP_ERR_INVALID_ARG, "no tracking call yet");
+  if (M->real_bytes != 4) return fail(BSP_ERR_INVALID_ARG, "needs F32 or MIXED precision");
+  if (cols < 1) return fail(BSP_ERR_INVALID_ARG, "cols must be >= 1");
+  if (!is_device_ptr(E) || !is_device_ptr(X_out))
+    return fail(BSP_ERR_INVALID_ARG, "bsp_reconstruct_bf16 takes device pointers");
+  int cmax = 0;
+  for (int b = 0; b < M->k; ++b) cmax = std::max(cmax, M->h_c[b]);
+  if (cmax > 128) return fail(BSP_ERR_INVALID_ARG, "c must be <= 128");
+  cudaStream_t s = (cudaStream_t)stream;
+  ProjArgs pa{M->d_bptr, M->d_verts, M->d_cb, M->d_ceoff, M->k, M->c_cap, cmax, M->max_nb, cols};
+  ProfScope ps(M);
+  CU(cudaMemsetAsync(M->d_status, 0, sizeof(int), s));
+  int rc = launch_recon_tc(pa, (const float*)M->d_U, E, X_out, M->d_status, s);
+  if (rc) return fail(rc, "reconstruction launch failed");
+  CU(cudaStreamSynchronize(s));
+  int st = 0;
+  CU(cudaMemcpy(&st, M->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st & ST_TIMEOUT) return fail(BSP_ERR_TIMEOUT, "a bounded device wait expired");
   M->stats.gpu_launches = 1;
   return BSP_OK;
 }

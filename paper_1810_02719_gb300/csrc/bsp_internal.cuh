@@ -26,6 +26,7 @@ enum : int {
   ST_BAD_INDEX = 1 << 2,      // assembly saw an out-of-range vertex id
   ST_DUP_VERTEX = 1 << 3,     // assembly saw a vertex in two blocks
   ST_DEGREE = 1 << 4,         // a row's neighbour list overflowed
+  ST_TIMEOUT = 1 << 5,        // a bounded device wait expired
 };
 
 struct CgStats {
@@ -181,6 +182,12 @@ int launch_project(const ProjArgs& a, const T* U, const void* X, int x_dtype, T*
                    cudaStream_t s);
 template <typename T>
 int launch_reconstruct(const ProjArgs& a, const T* U, const T* E, T* X, cudaStream_t s);
+// tcgen05 tensor-core versions, BF16 operands, FP32 accumulation (bsp_tc.cu)
+int launch_project_tc(const ProjArgs& a, const float* U, const void* X, float* E, int* status,
+                      cudaStream_t s);
+int launch_recon_tc(const ProjArgs& a, const float* U, const float* E, float* X, int* status,
+                    cudaStream_t s);
+void configure_tc_kernels();
 
 // Start matrices and dynamic-c helpers (bsp_dyn.cu)
 template <typename T>

@@ -386,3 +386,51 @@ def test_cg_step_cap_reports_not_converged():
         assert bsp.bsp_get_stats(h)["not_converged"] > 0
     finally:
         bsp.bsp_mesh_destroy(h)
+
+
+# ---------------------------------------------------------------- tensor cores
+
+def _bf16_round(a):
+    t = torch.tensor(a, dtype=torch.float32).to(torch.bfloat16).to(torch.float64)
+    return t.numpy()
+
+
+@pytest.mark.parametrize("c", [48, 32])
+def test_tensor_core_projection_and_reconstruction(c):
+    """All frames at once (Sec. 7.3): E = U^T X and X~ = U E on tcgen05 with BF16 operands."""
+    N, T, F = 64, 32, 200
+    frames, faces = synth.torus_frames(N, frames=F, seed=3)
+    xyz = frames[0]
+    ptr, verts = synth.tile_partition(N, T)
+    parent = synth.raster_chain(4)
+    cols = 3 * F
+    X = np.ascontiguousarray(frames.transpose(1, 0, 2).reshape(N * N, cols))
+    h = bsp.bsp_mesh_create(xyz, faces, ptr, verts, parent, bsp.make_opts(precision=bsp.BSP_PREC_F32))
+    try:
+        starts = synth.gaussian_starts(ptr, parent, c, seed=4).astype(np.float32)
+        bsp.bsp_oi_track(h, c, 2, starts)
+        Xb = torch.tensor(X, dtype=torch.float32, device="cuda").to(torch.bfloat16)
+        E = torch.empty(4 * c, cols, dtype=torch.float32, device="cuda")
+        bsp.bsp_project(h, Xb, bsp.BSP_DT_BF16, cols, E)
+        Xo = torch.empty(N * N, cols, dtype=torch.float32, device="cuda")
+        bsp.bsp_reconstruct_bf16(h, E, cols, Xo)
+        torch.cuda.synchronize()
+        En, Xon = E.cpu().double().numpy(), Xo.cpu().double().numpy()
+        Xq = Xb.to(torch.float64).cpu().numpy()
+        om = O.build_mesh(N * N, ptr, verts, parent, faces=faces)
+        for b, blk in enumerate(om.blocks):
+            U = bsp.bsp_get_basis(h, b, blk.verts.size).astype(np.float64)
+            Uq = _bf16_round(U)
+            Eb = En[b * c:(b + 1) * c]
+            Eref = Uq.T @ Xq[blk.verts]
+            assert np.abs(Eb - Eref).max() <= 1e-5 * np.abs(Eref).max()
+            Xref = Uq @ _bf16_round(Eb)
+            assert np.abs(Xon[blk.verts] - Xref).max() <= 1e-5 * np.abs(Xref).max()
+        # end to end against the FP64 oracle's filter output: BF16 operand rounding
+        # (2^-9 relative each for X, U and E) bounds the error at about 1e-2
+        U_ref = O.oi_track(om, c, 2, starts.astype(np.float64), delta=1e-2)
+        Xr = O.reconstruct(om, U_ref, O.project(om, U_ref, X), cols)
+        err = np.linalg.norm(Xon - Xr) / np.linalg.norm(Xr)
+        assert err <= 2e-2, err
+    finally:
+        bsp.bsp_mesh_destroy(h)
