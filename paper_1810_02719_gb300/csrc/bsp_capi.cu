@@ -152,9 +152,11 @@ void release(bsp_mesh* m) {
     if (p) cudaFree(p);
   if (m->graph_exec) cudaGraphExecDestroy(m->graph_exec);
   if (m->graph_stream) cudaStreamDestroy(m->graph_stream);
-  if (m->side_stream) cudaStreamDestroy(m->side_stream);
+  for (int i = 0; i < bsp_mesh::kSide; ++i) {
+    if (m->side_stream[i]) cudaStreamDestroy(m->side_stream[i]);
+    if (m->ev_join[i]) cudaEventDestroy(m->ev_join[i]);
+  }
   if (m->ev_fork) cudaEventDestroy(m->ev_fork);
-  if (m->ev_join) cudaEventDestroy(m->ev_join);
 }
 
 int stream_error_status(bsp_mesh* m, cudaStream_t s) {
@@ -393,15 +395,23 @@ int ensure_workspace(bsp_mesh* M, int c_cap, int maxbatch) {
   if ((rc = ensure(&M->d_Gp, &M->cap_Gp, gp)) != BSP_OK) return rc;
   if ((rc = ensure(&M->d_Rsm, &M->cap_Rsm, (size_t)maxbatch * cpad * cpad * sizeof(T))) != BSP_OK)
     return rc;
-  if ((rc = ensure(&M->d_theta, &M->cap_theta, (size_t)maxbatch * cpad * sizeof(T))) != BSP_OK)
+  if ((rc = ensure(&M->d_theta, &M->cap_theta,
+                   (size_t)bsp_mesh::kSide * maxbatch * cpad * sizeof(T))) != BSP_OK)
     return rc;
-  if ((rc = ensure(&M->d_Gp_rr, &M->cap_Gp_rr, gp)) != BSP_OK) return rc;
-  if ((rc = ensure(&M->d_Rsm_rr, &M->cap_Rsm_rr, (size_t)maxbatch * cpad * cpad * sizeof(T))) != BSP_OK)
-    return rc;
-  if (!M->side_stream && cudaStreamCreateWithFlags(&M->side_stream, cudaStreamNonBlocking) != cudaSuccess)
-    return fail(BSP_ERR_CUDA, "stream creation failed");
-  if (!M->ev_fork && (cudaEventCreateWithFlags(&M->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-                      cudaEventCreateWithFlags(&M->ev_join, cudaEventDisableTiming) != cudaSuccess))
+  const size_t gp_slice = (gp + 255) & ~(size_t)255;
+  const size_t rsm_slice = ((size_t)maxbatch * cpad * cpad * sizeof(T) + 255) & ~(size_t)255;
+  if ((rc = ensure(&M->d_Gp_rr, &M->cap_Gp_rr, gp_slice * bsp_mesh::kSide)) != BSP_OK) return rc;
+  if ((rc = ensure(&M->d_Rsm_rr, &M->cap_Rsm_rr, rsm_slice * bsp_mesh::kSide)) != BSP_OK) return rc;
+  M->gp_rr_slice = gp_slice;
+  M->rsm_rr_slice = rsm_slice;
+  for (int i = 0; i < bsp_mesh::kSide; ++i) {
+    if (!M->side_stream[i] &&
+        cudaStreamCreateWithFlags(&M->side_stream[i], cudaStreamNonBlocking) != cudaSuccess)
+      return fail(BSP_ERR_CUDA, "stream creation failed");
+    if (!M->ev_join[i] && cudaEventCreateWithFlags(&M->ev_join[i], cudaEventDisableTiming) != cudaSuccess)
+      return fail(BSP_ERR_CUDA, "event creation failed");
+  }
+  if (!M->ev_fork && cudaEventCreateWithFlags(&M->ev_fork, cudaEventDisableTiming) != cudaSuccess)
     return fail(BSP_ERR_CUDA, "event creation failed");
   if ((M->c_cap != c_cap || g_realloc) && M->graph_exec) {
     cudaGraphExecDestroy(M->graph_exec);
@@ -420,10 +430,14 @@ int fork_rr(bsp_mesh* M, int l, int c, cudaStream_t s, int* launches) {
   DenseArgs da{M->d_waves + M->h_wave_off[l], (int)M->waves[l].size(), M->d_bptr, M->d_cb,
                M->c_cap, c, wmax, M->d_status};
   da.sweeps = &M->d_cgstats->jacobi_sweeps;
+  const int si = l % bsp_mesh::kSide;   // waves round-robin over the side streams
+  cudaStream_t side = M->side_stream[si];
   CU(cudaEventRecord(M->ev_fork, s));
-  CU(cudaStreamWaitEvent(M->side_stream, M->ev_fork, 0));
-  int rc = launch_rayleigh_ritz<T, TA>(da, view<T>(M), (T*)M->d_U, (TA*)M->d_Gp_rr,
-                                       (T*)M->d_Rsm_rr, (T*)M->d_theta, M->side_stream, launches);
+  CU(cudaStreamWaitEvent(side, M->ev_fork, 0));
+  int rc = launch_rayleigh_ritz<T, TA>(
+      da, view<T>(M), (T*)M->d_U, (TA*)((char*)M->d_Gp_rr + si * M->gp_rr_slice),
+      (T*)((char*)M->d_Rsm_rr + si * M->rsm_rr_slice),
+      (T*)M->d_theta + (size_t)si * (M->cap_theta / sizeof(T) / bsp_mesh::kSide), side, launches);
   return rc ? fail(rc, "launch failed (Rayleigh-Ritz)") : BSP_OK;
 }
 
@@ -484,8 +498,10 @@ int enqueue_fixed(bsp_mesh* M, int c, int t_max, cudaStream_t s, int* launches) 
   }
   if (M->opts.rayleigh_ritz && levels > 0) {
     if ((rc = fork_rr<T, TA>(M, levels - 1, c, s, launches))) return rc;
-    CU(cudaEventRecord(M->ev_join, M->side_stream));   // join the side branch
-    CU(cudaStreamWaitEvent(s, M->ev_join, 0));
+    for (int i = 0; i < bsp_mesh::kSide && i < levels; ++i) {   // join the side branches
+      CU(cudaEventRecord(M->ev_join[i], M->side_stream[i]));
+      CU(cudaStreamWaitEvent(s, M->ev_join[i], 0));
+    }
   }
   return BSP_OK;
 }

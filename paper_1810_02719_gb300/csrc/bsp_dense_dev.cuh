@@ -34,6 +34,16 @@ BSP_DEV void ld4(const T* p, T (&v)[4]) {
   }
 }
 
+template <typename T>
+BSP_DEV void st4(T* p, const T* v) {
+  if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+    *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
+  }
+}
+
 // out[i][j] (cpad x cpad, TA) = sum_r S[r][i] * S2[r][j] over the panel's CH rows,
 // in 4x4 register tiles; `upper` computes only tiles with ti <= tj.
 template <typename T, typename TA>

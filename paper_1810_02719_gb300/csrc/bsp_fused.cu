@@ -16,18 +16,25 @@ namespace {
 using namespace dev;
 
 // Scratch next to the panel: the Gram half-sums (cpad^2) and the Cholesky's
-// pivot row (CP + 1); a multiple of 4 keeps the following arrays aligned.
+// double-buffered row (2 (CP + 4)); a multiple of 4 keeps the following
+// arrays aligned.
 __host__ __device__ inline int fused_half_elems(int cpad, int cp) {
-  const int a = cpad * cpad, b = 2 * cp;
+  const int a = cpad * cpad, b = 2 * cp + 8;
   return ((a > b ? a : b) + 3) & ~3;
 }
 
 // Cholesky of the Jacobi-scaled Gram in FP32 by CP threads (CP/32 warps):
-// thread j keeps column j of A in registers (rows 0..CP-1, upper triangle
-// used); step k publishes the pivot and the scaled pivot row through shared
-// memory (two named barriers over the CP threads).  Rows/columns >= c act as
+// thread j keeps column j of the symmetric A in registers.  The step loop is
+// unrolled, so every register index is a constant.  Step k publishes row k
+// (a_kj from thread j) in a double-buffered shared row, one named barrier
+// over the CP threads; then every thread forms r_kj = a_kj / sqrt(a_kk) and
+// applies the symmetric update a_ij -= a_ki a_kj / a_kk (i > k).  Entries
+// below the diagonal of column j turn to rounding-level values once step j
+// has passed; they are never read back (row k's readers only read entries
+// k..CP-1 of threads >= k) and never written out.  Rows/columns >= c act as
 // the identity.  Writes R (upper, stride CP) to Rr and 1/R_jj to rinv.
-// Called by threads 0..CP-1 only.
+// Called by threads 0..CP-1 only; lbuf holds 2 (CP + 4) floats, 16-byte
+// aligned.
 template <typename TG, int CP>
 BSP_DEV void chol_cols(const TG* g, int c, int cpad, const float* dsc, float* Rr, float* rinv,
                        float* lbuf, int* fail) {
@@ -35,29 +42,29 @@ BSP_DEV void chol_cols(const TG* g, int c, int cpad, const float* dsc, float* Rr
   float a[CP];
 #pragma unroll
   for (int i = 0; i < CP; ++i) {
-    float v = 0.f;
-    if (i < c && j < c && i <= j) v = (float)g[i * cpad + j] * dsc[i] * dsc[j];
-    if (i == j && j >= c) v = 1.f;
+    float v = i == j ? 1.f : 0.f;
+    if (i < c && j < c) v = (float)g[min(i, j) * cpad + max(i, j)] * dsc[i] * dsc[j];
     a[i] = v;
   }
   bool bad = false;
 #pragma unroll
   for (int k = 0; k < CP; ++k) {
-    if (j == k) lbuf[CP] = a[k];                       // pivot
+    if (k >= c) continue;   // uniform over the CP threads
+    float* buf = lbuf + (k & 1) * (CP + 4);
+    buf[j] = a[k];
     asm volatile("bar.sync 1, %0;" ::"r"(CP) : "memory");
-    const float piv = lbuf[CP];
+    const float piv = buf[k];
     const bool ok = piv > 0.f && isfinite(piv);
     bad = bad || !ok;
-    const float lj = j >= k ? a[k] * (ok ? rsqrtf(piv) : 1.f) : 0.f;
-    a[k] = lj;
-    lbuf[j] = lj;
-    asm volatile("bar.sync 1, %0;" ::"r"(CP) : "memory");
+    const float rs = ok ? rsqrtf(piv) : 1.f;
+    const float f = a[k] * rs * rs;
+    a[k] = a[k] * rs;
 #pragma unroll
-    for (int i = k + 1; i < CP; ++i) a[i] -= lbuf[i] * lj;
+    for (int i = k + 1; i < CP; ++i) a[i] -= buf[i] * f;
   }
 #pragma unroll
   for (int i = 0; i < CP; ++i) Rr[i * CP + j] = i <= j ? a[i] : 0.f;
-  rinv[j] = 1.f / a[j];
+  rinv[j] = 1.f / Rr[j * CP + j];
   if (bad && j == 0) *fail = 1;
 }
 
@@ -109,12 +116,12 @@ BSP_DEV void chol_block(const TG* g, int c, int cpad, TA* A, TA* dsc, TA* lrow, 
 // (rows x 16 outputs, 8 per thread), then a per-row 16 x 16 triangular solve.
 // All threads; ends with a barrier.
 template <typename T, int CP>
-BSP_DEV void trsm_rows(T* S, int rows, int cpad, int c, const T* Rr, const T* rinv,
+BSP_DEV void trsm_rows(T* S, int rows, int cpad, int ldS, int c, const T* Rr, const T* rinv,
                        const float* dscf, const double* dscd) {
   // scale the columns by D (zero past c)
   for (int r = threadIdx.x >> 5; r < rows; r += blockDim.x >> 5)
     for (int jj = threadIdx.x & 31; jj < cpad; jj += 32)
-      S[r * cpad + jj] = jj < c ? S[r * cpad + jj] * (dscd ? (T)dscd[jj] : (T)dscf[jj]) : T(0);
+      S[r * ldS + jj] = jj < c ? S[r * ldS + jj] * (dscd ? (T)dscd[jj] : (T)dscf[jj]) : T(0);
   __syncthreads();
 #pragma unroll 1
   for (int J = 0; J < CP / 16; ++J) {
@@ -128,20 +135,26 @@ BSP_DEV void trsm_rows(T* S, int rows, int cpad, int c, const T* Rr, const T* ri
 #pragma unroll
         for (int q = 0; q < 8; ++q) acc[q] = 0;
         for (int l = 0; l < j0; ++l) {
-          const T sv = S[r * cpad + l];
+          const T sv = S[r * ldS + l];
 #pragma unroll
           for (int q = 0; q < 8; ++q) acc[q] += sv * Rr[l * CP + j0 + 8 * h + q];
         }
 #pragma unroll
         for (int q = 0; q < 8; ++q)
-          if (j0 + 8 * h + q < cpad) S[r * cpad + j0 + 8 * h + q] -= acc[q];
+          if (j0 + 8 * h + q < cpad) S[r * ldS + j0 + 8 * h + q] -= acc[q];
       }
       __syncthreads();
     }
     for (int r = threadIdx.x; r < rows; r += blockDim.x) {
       T q[16];
+      T* row = S + r * ldS + j0;   // 16-byte aligned: ldS and j0 are multiples of 4
 #pragma unroll
-      for (int jj = 0; jj < 16; ++jj) q[jj] = j0 + jj < cpad ? S[r * cpad + j0 + jj] : T(0);
+      for (int v = 0; v < 4; ++v) {
+        T t4[4] = {T(0), T(0), T(0), T(0)};
+        if (j0 + 4 * v < cpad) ld4(row + 4 * v, t4);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) q[4 * v + e] = t4[e];
+      }
 #pragma unroll
       for (int jj = 0; jj < 16; ++jj) {
         T s0 = q[jj];
@@ -150,8 +163,8 @@ BSP_DEV void trsm_rows(T* S, int rows, int cpad, int c, const T* Rr, const T* ri
         q[jj] = s0 * rinv[j0 + jj];
       }
 #pragma unroll
-      for (int jj = 0; jj < 16; ++jj)
-        if (j0 + jj < cpad) S[r * cpad + j0 + jj] = q[jj];
+      for (int v = 0; v < 4; ++v)
+        if (j0 + 4 * v < cpad) st4(row + 4 * v, q + 4 * v);
     }
     __syncthreads();
   }
@@ -161,13 +174,13 @@ BSP_DEV void trsm_rows(T* S, int rows, int cpad, int c, const T* Rr, const T* ri
 // zero padded: warp per row, 16-byte vectors when aligned.
 template <typename T>
 BSP_DEV void stage_rows(const T* __restrict__ A, int ld, int row0, int nr, int c, int cpad,
-                        int rows, T* S) {
+                        int rows, T* S, int ldS) {
   constexpr int VE = 16 / sizeof(T);
   const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const bool vec = (ld % VE == 0) && (cpad % VE == 0) && (c % VE == 0) &&
                    ((uintptr_t)A % 16 == 0);
   for (int r = threadIdx.x >> 5; r < rows; r += nw) {
-    T* dst = S + r * cpad;
+    T* dst = S + r * ldS;
     if (r >= nr) {
       for (int j = lane; j < cpad; j += 32) dst[j] = T(0);
     } else if (vec) {
@@ -188,7 +201,7 @@ BSP_DEV void stage_rows(const T* __restrict__ A, int ld, int row0, int nr, int c
 // cpad): tiles of 4 x 4, the rows split in two halves so that every thread
 // has work; the halves are added through shared memory scratch `half` (T).
 template <typename T, typename TA>
-BSP_DEV void panel_gram_split(const T* S, int rows, int cpad, T* half, TA* out) {
+BSP_DEV void panel_gram_split(const T* S, int rows, int cpad, int ldS, T* half, TA* out) {
   const int nt = cpad / 4;
   const int nup = nt * (nt + 1) / 2;
   const int items = 2 * nup;
@@ -212,8 +225,8 @@ BSP_DEV void panel_gram_split(const T* S, int rows, int cpad, T* half, TA* out) 
     tiles[q] = (ti * nt + tj) * 2 + h;
     for (int r = h * hr; r < (h + 1) * hr; ++r) {
       T a4[4], b4[4];
-      ld4(S + r * cpad + 4 * ti, a4);
-      ld4(S + r * cpad + 4 * tj, b4);
+      ld4(S + r * ldS + 4 * ti, a4);
+      ld4(S + r * ldS + 4 * tj, b4);
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -266,8 +279,9 @@ __global__ void __launch_bounds__(kDT) k_cholqr2_cluster(DenseArgs a, const T* Y
   const int RP = (nb + P - 1) / P;
   const int row0 = p * RP;
   const int nr = max(0, min(RP, nb - row0));
-  T* S = reinterpret_cast<T*>(smem_raw);                 // rp_max x cpad
-  T* half = S + rp_max * cpad;                           // scratch: Gram halves, pivot row
+  const int ldS = cpad + 4;                              // padded: conflict-free row-parallel access
+  T* S = reinterpret_cast<T*>(smem_raw);                 // rp_max x ldS
+  T* half = S + rp_max * ldS;                            // scratch: Gram halves, pivot row
   T* Rr = half + fused_half_elems(cpad, CP);             // CP x CP
   T* rinv = Rr + CP * CP;                                // CP
   TA* dsc = reinterpret_cast<TA*>(rinv + CP);            // cpad (scaling), then pivot row
@@ -275,12 +289,12 @@ __global__ void __launch_bounds__(kDT) k_cholqr2_cluster(DenseArgs a, const T* Y
   float* dscf = reinterpret_cast<float*>(A + cpad * cpad);
   __shared__ int fail;
   if (threadIdx.x == 0) fail = 0;
-  stage_rows(Y, a.ld, r0 + row0, nr, c, cpad, rp_max, S);
+  stage_rows(Y, a.ld, r0 + row0, nr, c, cpad, rp_max, S, ldS);
   __syncthreads();
   const size_t cc = (size_t)cpad * cpad;
   TA* gf = Gfin + (size_t)slot * cc;
   for (int pass = 0; pass < passes; ++pass) {
-    panel_gram_split<T, TA>(S, rp_max, cpad, half, Gpart + ((size_t)slot * P + p) * cc);
+    panel_gram_split<T, TA>(S, rp_max, cpad, ldS, half, Gpart + ((size_t)slot * P + p) * cc);
     cluster_barrier();
     for (int e = p * blockDim.x + threadIdx.x; e < cpad * cpad; e += P * blockDim.x) {
       const int i = e / cpad, jj = e - i * cpad;
@@ -318,21 +332,20 @@ __global__ void __launch_bounds__(kDT) k_cholqr2_cluster(DenseArgs a, const T* Y
       for (int t = threadIdx.x; t < cpad; t += blockDim.x) { dsc[t] = TA(1); dscf[t] = 1.f; }
       __syncthreads();
     }
-    trsm_rows<T, CP>(S, rp_max, cpad, c, Rr, rinv, dscf,
+    trsm_rows<T, CP>(S, rp_max, cpad, ldS, c, Rr, rinv, dscf,
                      sizeof(T) == 8 ? reinterpret_cast<const double*>(dsc) : nullptr);
     cluster_barrier();  // every CTA has read Gfin before the next pass rewrites it
   }
-  for (int t = threadIdx.x; t < nr * cpad; t += blockDim.x) {
-    const int i = t / cpad, jj = t - i * cpad;
-    if (jj < c) Q[(size_t)(r0 + row0 + i) * a.ld + jj] = S[t];
-  }
+  for (int i = threadIdx.x >> 5; i < nr; i += blockDim.x >> 5)
+    for (int jj = threadIdx.x & 31; jj < c; jj += 32)
+      Q[(size_t)(r0 + row0 + i) * a.ld + jj] = S[i * ldS + jj];
   if (fail && threadIdx.x == 0 && p == 0) atomicOr(a.status, ST_NUMERICAL);
 }
 
 template <typename T, typename TA>
 size_t fused_smem(int rp_max, int cpad) {
   const int cp = chol_cp(cpad);
-  return (size_t)(rp_max * cpad + fused_half_elems(cpad, cp) + cp * cp + cp) * sizeof(T) +
+  return (size_t)(rp_max * (cpad + 4) + fused_half_elems(cpad, cp) + cp * cp + cp) * sizeof(T) +
          (size_t)(2 * cpad + cpad * cpad) * sizeof(TA) + (size_t)cpad * sizeof(float) + 16;
 }
 

@@ -264,12 +264,14 @@ struct bsp_mesh {
   void* d_rho = nullptr;
   void* d_X = nullptr;
   size_t cap_X = 0;
-  // Rayleigh-Ritz side branch: own workspace, stream and fork/join events
+  // Rayleigh-Ritz side branches: kSide streams used round-robin, each with its
+  // own workspace slice and join event
+  static constexpr int kSide = 8;
   void* d_Gp_rr = nullptr;
   void* d_Rsm_rr = nullptr;
-  size_t cap_Gp_rr = 0, cap_Rsm_rr = 0;
-  cudaStream_t side_stream = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  size_t cap_Gp_rr = 0, cap_Rsm_rr = 0, gp_rr_slice = 0, rsm_rr_slice = 0;
+  cudaStream_t side_stream[kSide] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[kSide] = {};
   // graph cache for the fixed-c schedule
   cudaGraphExec_t graph_exec = nullptr;
   int graph_c = -1, graph_t = -1, graph_launches = 0;
