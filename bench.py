@@ -199,24 +199,31 @@ def run_ours(args, rank, world, device):
     peak_f32 = 152 * 128 * 2 * clk * 1e6 / 1e12
     nb = args.tile * args.tile
     k = len(ptr) - 1
-    if dom == "chol":
-        # fused Onorm per block: Gram (n c^2) + Cholesky (c^3/3) + TRSM (n c^2) per pass;
-        # t_max - 1 one-pass and one two-pass launch per block
-        passes = 2 * k + (args.t - 1) * k
-        flops = passes * (2.0 * nb * args.c ** 2 + args.c ** 3 / 3.0)
-        roof = {"kernel": "k_cholqr2_cluster (fused CholeskyQR2, one cluster per block)",
-                "bound": "alu", "unit": "TFLOP/s",
-                "achieved": flops / (kernels[dom]["ms"] * 1e-3) / 1e12, "peak": peak_f32,
-                "peak_source": "derived: 152 SM x 128 FP32 FMA/clk x 2 x median SM clock under load",
-                "algorithmic_flops_per_launch": flops / kernels[dom]["launches"]}
-    else:
-        steps = prof_stats["cg_steps_total"]
-        flops = steps * nb * (2.0 * 7 + 10)
-        roof = {"kernel": "k_cg1 (register-ELL CG, one column per CTA)", "bound": "alu",
-                "unit": "TFLOP/s", "achieved": flops / (kernels[dom]["ms"] * 1e-3) / 1e12,
-                "peak": peak_f32,
-                "peak_source": "derived: 152 SM x 128 FP32 FMA/clk x 2 x median SM clock under load",
-                "algorithmic_flops_per_launch": flops / kernels[dom]["launches"]}
+    c = args.c
+    # algorithmic FP32 flops of every kernel class over the profiled step
+    work = {
+        # fused Onorm: Gram (2 n c^2) + Cholesky (c^3 / 3) + TRSM (n c^2) per pass;
+        # one two-pass launch and t_max - 1 one-pass launches per block
+        "chol": ((2 * k + (args.t - 1) * k) * (3.0 * nb * c ** 2 + c ** 3 / 3.0),
+                 "k_cholqr2_cluster (fused CholeskyQR2, one 8-CTA cluster per block)"),
+        # CG: one SpMV (2 flops per nonzero, ~6.75 per row) + ~10 vector flops per row per step
+        "cg": (prof_stats["cg_steps_total"] * nb * (2.0 * 6.75 + 10),
+               "k_cg1 (register-ELL CG, one column per CTA)"),
+        # cyclic Jacobi: c (c - 1) / 2 rotations per sweep, each 18 c flops (2 rows and
+        # 2 columns of H, 2 columns of the eigenvectors)
+        "jacobi": (prof_stats["jacobi_sweeps"] * 9.0 * c * c * (c - 1),
+                   "k_jacobi (Rayleigh-Ritz c x c eigensolver, side streams)"),
+        # Rayleigh-Ritz: L V (2 nnz c) and V^T (L V) (2 n c^2) per block
+        "rr": (k * (2.0 * 6.75 * nb * c + 2.0 * nb * c ** 2), "k_rr (H = V^T L V, side streams)"),
+        "panel": (k * 2.0 * nb * c ** 2, "k_panel_mul (V <- V Q_H, side streams)"),
+    }
+    flops, kname = work.get(dom, (0.0, dom))
+    roof = {"kernel": kname, "bound": "alu", "unit": "TFLOP/s",
+            "achieved": flops / (kernels[dom]["ms"] * 1e-3) / 1e12, "peak": peak_f32,
+            "peak_source": "derived: 152 SM x 128 FP32 FMA/clk x 2 x median SM clock under load",
+            "algorithmic_flops_per_launch": flops / kernels[dom]["launches"],
+            "critical_path": {kc: kernels[kc]["ms"] for kc in ("init", "cg", "chol", "reduce")
+                              if kc in kernels}}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["avg_launch_s"] = kernels[dom]["ms"] * 1e-3 / kernels[dom]["launches"]
     roof["traffic"] = None
@@ -361,6 +368,21 @@ def run_frames(args, device):
         f()
     t_pbf, t_rbf = timed(pj_bf, args.steps), timed(rc_bf, args.steps)
     t_p32, t_r32 = timed(pj_32, args.steps), timed(rc_32, args.steps)
+
+    def kernel_time(fn, cls):
+        """Average device time of the kernel class per launch: CUDA events
+        around each launch on its stream (the library's profiling hook)."""
+        bsp.bsp_set_profiling(h, 1)
+        bsp.bsp_get_kernel_times(h)
+        before = bsp.bsp_get_kernel_times(h)[cls]
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            fn()
+        after = bsp.bsp_get_kernel_times(h)[cls]
+        bsp.bsp_set_profiling(h, 0)
+        return (after[0] - before[0]) * 1e-3 / max(1, after[1] - before[1])
+
+    k_pbf, k_rbf = kernel_time(pj_bf, "project"), kernel_time(rc_bf, "recon")
     # errors against the FP64 oracle on the first 4 blocks of the chain
     om = O.build_mesh(n, ptr[:5], verts[:ptr[4]], parent[:4], faces=faces)
     Uref = O.oi_track(om, c, args.t, starts, delta=1e-2)
@@ -378,8 +400,12 @@ def run_frames(args, device):
             den += np.sum(ref ** 2)
         errs[name] = float(np.sqrt(num / den))
     peak_hbm, peak_kind = peaks()
-    bytes_pbf = n * cols * 2 + k * c * cols * 4 + n * c * 4
-    bytes_rbf = k * c * cols * 4 + n * c * 4 + n * cols * 4
+    # bytes each kernel must move: its operands as the kernel reads them (X and
+    # the basis in BF16, padded to 16 columns; E in BF16 for the reconstruction)
+    # and its FP32 output
+    np16 = (c + 15) // 16 * 16
+    bytes_pbf = n * cols * 2 + n * np16 * 2 + k * c * cols * 4
+    bytes_rbf = k * c * cols * 2 + n * np16 * 2 + n * cols * 4
     flops = 2.0 * n * c * cols
     bsp.bsp_mesh_destroy(h)
     return {
@@ -388,18 +414,20 @@ def run_frames(args, device):
         "vertex_frames_per_s_projection_bf16": n * F / t_pbf,
         "times_ms": {"track": 1e3 * t_track, "project_bf16_tc": 1e3 * t_pbf,
                      "reconstruct_bf16_tc": 1e3 * t_rbf, "project_f32": 1e3 * t_p32,
-                     "reconstruct_f32": 1e3 * t_r32},
+                     "reconstruct_f32": 1e3 * t_r32,
+                     "note": "API calls (each ends with a stream synchronise and a status read)"},
+        "kernel_ms": {"k_project_tc": 1e3 * k_pbf, "k_recon_tc": 1e3 * k_rbf},
         "rel_err_vs_fp64_oracle_first4blocks": errs,
         "roofline": {"kernel": "k_project_tc (tcgen05, BF16 X, all frames)", "bound": "hbm",
-                     "achieved": bytes_pbf / t_pbf / 1e9, "peak": peak_hbm, "unit": "GB/s",
-                     "peak_source": peak_kind, "frac": bytes_pbf / t_pbf / 1e9 / peak_hbm,
-                     "traffic": None, "algorithmic_bytes": bytes_pbf, "avg_launch_s": t_pbf,
-                     "tensor_tflops": flops / t_pbf / 1e12},
+                     "achieved": bytes_pbf / k_pbf / 1e9, "peak": peak_hbm, "unit": "GB/s",
+                     "peak_source": peak_kind, "frac": bytes_pbf / k_pbf / 1e9 / peak_hbm,
+                     "traffic": None, "algorithmic_bytes": bytes_pbf, "avg_launch_s": k_pbf,
+                     "tensor_tflops": flops / k_pbf / 1e12},
         "roofline_reconstruct": {"kernel": "k_recon_tc", "bound": "hbm",
-                                 "achieved": bytes_rbf / t_rbf / 1e9, "peak": peak_hbm,
-                                 "unit": "GB/s", "frac": bytes_rbf / t_rbf / 1e9 / peak_hbm,
-                                 "algorithmic_bytes": bytes_rbf, "avg_launch_s": t_rbf,
-                                 "tensor_tflops": flops / t_rbf / 1e12},
+                                 "achieved": bytes_rbf / k_rbf / 1e9, "peak": peak_hbm,
+                                 "unit": "GB/s", "frac": bytes_rbf / k_rbf / 1e9 / peak_hbm,
+                                 "algorithmic_bytes": bytes_rbf, "avg_launch_s": k_rbf,
+                                 "tensor_tflops": flops / k_rbf / 1e12},
     }
 
 

@@ -229,8 +229,10 @@ int bsp_reconstruct(bsp_mesh* mesh, const void* E, int32_t cols, void* X_out, vo
  * coordinate matrices (all frames of a dynamic mesh, Sec. 7.3).
  *   E      device float [sum_b c_b x cols]; X_out device float [n x cols].
  * Requires F32 or MIXED precision and c <= 128.  (bsp_project takes the
- * tensor-core path itself when x_dtype is BSP_DT_BF16, cols % 8 == 0 and
- * cols >= 64.)  Errors: BSP_ERR_INVALID_ARG, BSP_ERR_TIMEOUT, BSP_ERR_CUDA.
+ * tensor-core path itself when x_dtype is BSP_DT_BF16, cols % 8 == 0,
+ * cols >= 64 and X is 16-byte aligned.)  Both build a BF16 copy of the bases
+ * (n x pad16(c), kept on the mesh until the next tracking call).
+ * Errors: BSP_ERR_INVALID_ARG, BSP_ERR_TIMEOUT, BSP_ERR_CUDA.
  */
 int bsp_reconstruct_bf16(bsp_mesh* mesh, const float* E, int32_t cols, float* X_out, void* stream);
 

@@ -147,7 +147,7 @@ void release(bsp_mesh* m) {
                   m->d_wt, m->d_diag, m->d_status, m->d_cgstats, m->d_U, m->d_Y, m->d_starts,
                   m->d_Gp, m->d_Rsm, m->d_theta, m->d_action, m->d_round, m->d_forced,
                   m->d_gcol, m->d_rho, m->d_X, m->d_Gp_rr, m->d_Rsm_rr, m->d_ckV, m->d_ckY,
-                  m->d_adj_gp, m->d_adj_thin, m->d_adj_rows};
+                  m->d_adj_gp, m->d_adj_thin, m->d_adj_rows, m->d_Ubf, m->d_Ebf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (m->graph_exec) cudaGraphExecDestroy(m->graph_exec);
@@ -585,6 +585,7 @@ int track_fixed(bsp_mesh* M, int c, int t_max, const void* V0, cudaStream_t s) {
   }
   M->stats.gpu_launches = launches;
   M->tracked = true;
+  M->ubf_valid = false;
   return stream_error_status(M, s);
 }
 
@@ -731,6 +732,7 @@ int track_dynamic(bsp_mesh* M, const void* X, double tol, int c_min, int c_max, 
   }
   M->stats.gpu_launches = launches;
   M->tracked = true;
+  M->ubf_valid = false;
   return stream_error_status(M, s);
 }
 
@@ -807,6 +809,7 @@ int filter_forward(bsp_mesh* M, int c, int t_max, const void* V0, cudaStream_t s
   M->filter_c = c;
   M->filter_t = t_max;
   M->tracked = true;
+  M->ubf_valid = false;
   M->stats.gpu_launches = launches;
   return stream_error_status(M, s);
 }
@@ -1093,6 +1096,21 @@ int bsp_get_basis(const bsp_mesh* M, int32_t b, void* U, int32_t* c) {
   return BSP_OK;
 }
 
+// BF16 copy of the tracked bases (tensor-core operand), built once per tracking call.
+int ensure_basis_bf16(bsp_mesh* M, const ProjArgs& pa, cudaStream_t s, int* launched) {
+  const int np = (pa.cmax + 15) & ~15;
+  const size_t cap0 = M->cap_Ubf;
+  int rc;
+  *launched = 0;
+  if ((rc = ensure(&M->d_Ubf, &M->cap_Ubf, (size_t)M->n * np * 2)) != BSP_OK) return rc;
+  if (M->cap_Ubf != cap0) M->ubf_valid = false;
+  if (M->ubf_valid) return BSP_OK;
+  if ((rc = launch_basis_bf16(pa, (const float*)M->d_U, M->d_Ubf, s)) != BSP_OK) return rc;
+  M->ubf_valid = true;
+  *launched = 1;
+  return BSP_OK;
+}
+
 int bsp_project(bsp_mesh* M, const void* X, int32_t x_dtype, int32_t cols, void* E_out,
                 void* stream) {
   g_err.clear();
@@ -1125,9 +1143,12 @@ int bsp_project(bsp_mesh* M, const void* X, int32_t x_dtype, int32_t cols, void*
   ProjArgs pa{M->d_bptr, M->d_verts, M->d_cb, M->d_ceoff, M->k, M->c_cap, cmax, M->max_nb, cols};
   ProfScope ps(M);
   bool tc = false;
-  if (x_dtype == BSP_DT_BF16 && rb == 4 && cols % 8 == 0 && cols >= 64 && cmax <= 256) {
+  int conv = 0;
+  if (x_dtype == BSP_DT_BF16 && rb == 4 && cols % 8 == 0 && cols >= 64 && cmax <= 256 &&
+      (uintptr_t)dX % 16 == 0) {
     CU(cudaMemsetAsync(M->d_status, 0, sizeof(int), s));
-    rc = launch_project_tc(pa, (const float*)M->d_U, dX, (float*)dE, M->d_status, s);
+    if ((rc = ensure_basis_bf16(M, pa, s, &conv)) != BSP_OK) return fail(rc, "basis conversion failed");
+    rc = launch_project_tc(pa, M->d_Ubf, dX, (float*)dE, M->d_status, s);
     tc = rc == BSP_OK;
   }
   if (!tc) {
@@ -1137,7 +1158,7 @@ int bsp_project(bsp_mesh* M, const void* X, int32_t x_dtype, int32_t cols, void*
   if (rc) return fail(rc, "projection launch failed");
   if (host_out) CU(cudaMemcpyAsync(E_out, dE, (size_t)erows * cols * rb, cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
-  M->stats.gpu_launches = 1;
+  M->stats.gpu_launches = 1 + conv;
   if (tc) {
     int st = 0;
     CU(cudaMemcpy(&st, M->d_status, sizeof(int), cudaMemcpyDeviceToHost));
@@ -1196,13 +1217,21 @@ int bsp_reconstruct_bf16(bsp_mesh* M, const float* E, int32_t cols, float* X_out
   ProjArgs pa{M->d_bptr, M->d_verts, M->d_cb, M->d_ceoff, M->k, M->c_cap, cmax, M->max_nb, cols};
   ProfScope ps(M);
   CU(cudaMemsetAsync(M->d_status, 0, sizeof(int), s));
-  int rc = launch_recon_tc(pa, (const float*)M->d_U, E, X_out, M->d_status, s);
+  int conv = 0;
+  int rc = ensure_basis_bf16(M, pa, s, &conv);
+  if (rc) return fail(rc, "basis conversion failed");
+  int64_t erows = 0;
+  for (int b = 0; b < M->k; ++b) erows += M->h_c[b];
+  const size_t ebytes = (size_t)erows * (((size_t)cols + 7) & ~(size_t)7) * 2;
+  if ((rc = ensure(&M->d_Ebf, &M->cap_Ebf, ebytes > 0 ? ebytes : 16)) != BSP_OK)
+    return fail(rc, "out of device memory");
+  rc = launch_recon_tc(pa, M->d_Ubf, E, erows, M->d_Ebf, X_out, M->d_status, s);
   if (rc) return fail(rc, "reconstruction launch failed");
   CU(cudaStreamSynchronize(s));
   int st = 0;
   CU(cudaMemcpy(&st, M->d_status, sizeof(int), cudaMemcpyDeviceToHost));
   if (st & ST_TIMEOUT) return fail(BSP_ERR_TIMEOUT, "a bounded device wait expired");
-  M->stats.gpu_launches = 1;
+  M->stats.gpu_launches = 2 + conv;
   return BSP_OK;
 }
 

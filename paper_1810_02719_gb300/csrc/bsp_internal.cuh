@@ -182,11 +182,14 @@ int launch_project(const ProjArgs& a, const T* U, const void* X, int x_dtype, T*
                    cudaStream_t s);
 template <typename T>
 int launch_reconstruct(const ProjArgs& a, const T* U, const T* E, T* X, cudaStream_t s);
-// tcgen05 tensor-core versions, BF16 operands, FP32 accumulation (bsp_tc.cu)
-int launch_project_tc(const ProjArgs& a, const float* U, const void* X, float* E, int* status,
+// tcgen05 tensor-core versions, BF16 operands, FP32 accumulation (bsp_tc.cu);
+// Ub is the BF16 copy of the basis written by launch_basis_bf16 (pad16(cmax)
+// columns per row, zero past each block's c).
+int launch_basis_bf16(const ProjArgs& a, const float* U, void* Ub, cudaStream_t s);
+int launch_project_tc(const ProjArgs& a, const void* Ub, const void* X, float* E, int* status,
                       cudaStream_t s);
-int launch_recon_tc(const ProjArgs& a, const float* U, const float* E, float* X, int* status,
-                    cudaStream_t s);
+int launch_recon_tc(const ProjArgs& a, const void* Ub, const float* E, int64_t erows, void* Eb,
+                    float* X, int* status, cudaStream_t s);
 void configure_tc_kernels();
 
 // Start matrices and dynamic-c helpers (bsp_dyn.cu)
@@ -264,6 +267,13 @@ struct bsp_mesh {
   void* d_rho = nullptr;
   void* d_X = nullptr;
   size_t cap_X = 0;
+  // BF16 copy of the tracked bases for the tensor-core projection and
+  // reconstruction; rebuilt on first use after every tracking call
+  void* d_Ubf = nullptr;
+  size_t cap_Ubf = 0;
+  bool ubf_valid = false;
+  void* d_Ebf = nullptr;   // BF16 copy of the coefficients of a reconstruction call
+  size_t cap_Ebf = 0;
   // Rayleigh-Ritz side branches: kSide streams used round-robin, each with its
   // own workspace slice and join event
   static constexpr int kSide = 8;

@@ -12,6 +12,8 @@
 // frees its tensor memory and returns.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "bsp_internal.cuh"
 
 namespace bsp {
@@ -19,8 +21,10 @@ namespace {
 
 constexpr int kTT = 256;         // threads per CTA
 constexpr int kM = 128;          // MMA M (rows of D = TMEM lanes)
-constexpr int kKC = 64;          // K chunk per pipeline stage (4 MMAs of K = 16)
+constexpr int kKC = 32;          // projection K chunk per ring stage (2 MMAs of K = 16)
 constexpr long kSpin = 1L << 26; // bounded mbarrier wait (iterations)
+constexpr int kS = 8;            // projection ring depth
+constexpr int kD = 6;            // chunks in flight ahead of the MMAs (kS - 2)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -90,17 +94,83 @@ __device__ __forceinline__ void tmem_free(uint32_t tmem, int cols) {
   asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cols));
 }
 
+// 16-byte global -> shared copy on the asynchronous copy path; src_bytes = 0
+// writes zeros without reading.
+__device__ __forceinline__ void cp16(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
+               "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N)); }
+
+// Element offsets inside the non-swizzled layouts (core matrix = 8 x 16 bytes):
+//  K-major  (r, k), K extent kc:  core (r/8, k/8) at ((r/8)(kc/8) + k/8) * 64,
+//           row r%8 holds 8 consecutive k;  LBO = 128 B (K), SBO = (kc/8) 128 B (rows).
+//  MN-major (r, k), MN extent R:  core (r/8, k/8) at ((k/8)(R/8) + r/8) * 64,
+//           row k%8 holds 8 consecutive r;  LBO = (R/8) 128 B (K), SBO = 128 B (MN).
+__device__ __forceinline__ int mnmaj(int r, int k, int R) {
+  return ((k >> 3) * (R >> 3) + (r >> 3)) * 64 + (k & 7) * 8 + (r & 7);
+}
+
+// Instruction descriptor with operand majorness: bit 15 (A) / bit 16 (B) set
+// for MN-major.
+__device__ __forceinline__ uint32_t idesc_bf16_major(int M, int N, int a_mn, int b_mn) {
+  return idesc_bf16(M, N) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16);
+}
+
+// Ub[r][j] = bf16(U[r][j]) for j < c_b of the row's block, 0 for c_b <= j < NP:
+// the basis as a tensor-core operand (rows in block order, NP columns).
+__global__ void k_basis_bf16(ProjArgs a, const float* __restrict__ U, __nv_bfloat16* __restrict__ Ub,
+                             int NP) {
+  const int b = blockIdx.y;
+  const int r0 = a.bptr[b], nb = a.bptr[b + 1] - r0, c = a.cb[b];
+  const int g = NP / 8;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nb * g; t += gridDim.x * blockDim.x) {
+    const int r = t / g, j0 = (t - r * g) * 8;
+    const float* src = U + (size_t)(r0 + r) * a.ld + j0;
+    __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = __float2bfloat16(j0 + e < c ? src[e] : 0.f);
+    *reinterpret_cast<uint4*>(Ub + (size_t)(r0 + r) * NP + j0) = *reinterpret_cast<const uint4*>(v);
+  }
+}
+
+// Eb[r][n] = bf16(E[r][n]) for n < cols, 0 for cols <= n < colsP (colsP =
+// cols rounded up to 8, so that every 16-byte piece of an Eb row is aligned).
+__global__ void k_coef_bf16(const float* __restrict__ E, __nv_bfloat16* __restrict__ Eb, int64_t rows,
+                            int cols, int colsP) {
+  const int g = colsP / 8;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < rows * g;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / g;
+    const int n0 = (int)(t - r * g) * 8;
+    __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = __float2bfloat16(n0 + e < cols ? E[r * cols + n0 + e] : 0.f);
+    *reinterpret_cast<uint4*>(Eb + r * colsP + n0) = *reinterpret_cast<const uint4*>(v);
+  }
+}
+
 // E^T tile = X^T U for block b = blockIdx.y and frame-columns [m0, m0 + 128):
-// A[m][k] = X[verts[r0 + k]][m0 + m] (bf16), B[n][k] = U[r0 + k][n] (fp32 -> bf16),
-// K over the block's vertices in chunks of 64 (two pipeline stages).
-__global__ void __launch_bounds__(kTT) k_project_tc(ProjArgs a, const float* __restrict__ U,
+// A[m][k] = X[verts[r0 + k]][m0 + m] and B[n][k] = Ub[r0 + k][n], both
+// MN-major, so every 16-byte piece of a gathered X row (8 frame-columns) and
+// of a basis row (8 basis columns) is one asynchronous copy, no register
+// staging.  K runs over the block's vertices in chunks of 32 through an
+// 8-stage ring with 6 chunks in flight; stage reuse waits on the MMA commit
+// of the chunk that last read it.  Eight consecutive threads fill one core matrix (8 rows x 16 B,
+// contiguous), so the shared-memory writes are conflict-free.
+__global__ void __launch_bounds__(kTT) k_project_tc(ProjArgs a, const __nv_bfloat16* __restrict__ Ub,
                                                     const __nv_bfloat16* __restrict__ X,
                                                     float* __restrict__ E, int NP, int tcols,
                                                     int* status) {
+  constexpr int S = kS;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(smem_raw);     // 2 x kM x kKC
-  __nv_bfloat16* sB = sA + 2 * kM * kKC;                               // 2 x NP x kKC
-  __shared__ __align__(8) uint64_t mbar[2];
+  const int stageA = kM * kKC, stageB = NP * kKC;                     // elements
+  __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(smem_raw);     // S x kM x kKC
+  __nv_bfloat16* sB = sA + S * stageA;                                 // S x NP x kKC
+  int32_t* sv = reinterpret_cast<int32_t*>(sB + S * stageB);           // the block's vertex ids
+  __shared__ __align__(8) uint64_t mbar[kS];
   __shared__ uint32_t tmem_base;
   const int tid = threadIdx.x, warp = tid >> 5;
   const int b = blockIdx.y;
@@ -109,79 +179,80 @@ __global__ void __launch_bounds__(kTT) k_project_tc(ProjArgs a, const float* __r
   const int m0 = blockIdx.x * kM;
   const int cols = a.cols;
   if (warp == 0) tmem_alloc(&tmem_base, tcols);
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
-    asm volatile("fence.mbarrier_init.release.cluster;");
-  }
+  // vertex ids once per CTA: the row gathers below then need no dependent
+  // global load before each copy
+  for (int t = tid; t < nb; t += kTT) sv[t] = a.verts[r0 + t];
+  if (tid < S) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[tid])));
+  if (tid == 0) asm volatile("fence.mbarrier_init.release.cluster;");
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
-  const uint32_t idesc = idesc_bf16(kM, NP);
+  const uint32_t idesc = idesc_bf16_major(kM, NP, 1, 1);
   const int nchunk = (nb + kKC - 1) / kKC;
-  uint32_t phase[2] = {0, 0};
+  const int gB = NP / 8;
+  auto issue = [&](int ch) {
+    const int st = ch % S, k0 = ch * kKC;
+    __nv_bfloat16* tA = sA + st * stageA;
+    __nv_bfloat16* tB = sB + st * stageB;
+    // A: kKC rows x 16 pieces; item -> (k % 8 fastest, piece, k / 8)
+    for (int it = tid; it < kKC * (kM / 8); it += kTT) {
+      const int k = (it & 7) + 8 * (it >> 7), mg = (it >> 3) & 15;
+      const int row = k0 + k;
+      const bool ok = row < nb && m0 + 8 * mg < cols;
+      const __nv_bfloat16* src = ok ? X + (size_t)sv[row] * cols + m0 + 8 * mg : X;
+      cp16(tA + mnmaj(8 * mg, k, kM), src, ok ? 16 : 0);
+    }
+    // B: kKC rows x NP/8 pieces of the BF16 basis
+    for (int it = tid; it < kKC * gB; it += kTT) {
+      const int q = it >> 3, k = (it & 7) + 8 * (q / gB), ng = q % gB;
+      const int row = k0 + k;
+      const bool ok = row < nb;
+      const __nv_bfloat16* src = ok ? Ub + (size_t)(r0 + row) * NP + 8 * ng : Ub;
+      cp16(tB + mnmaj(8 * ng, k, NP), src, ok ? 16 : 0);
+    }
+  };
   bool ok = true;
+  for (int ch = 0; ch < kD; ++ch) {
+    if (ch < nchunk) issue(ch);
+    cp_commit();
+  }
   for (int ch = 0; ch < nchunk; ++ch) {
-    const int s = ch & 1;
-    if (ch >= 2) {  // the MMAs that read this stage two chunks ago must be done
-      if (!mbar_wait(&mbar[s], phase[s])) ok = false;
-      phase[s] ^= 1;
+    const int nxt = ch + kD;
+    if (nxt < nchunk) {
+      // stage nxt % S was last read by the MMAs of chunk ch - 2, issued two
+      // iterations ago, so this wait rarely blocks
+      if (ch >= 2 && !mbar_wait(&mbar[(ch - 2) % S], ((ch - 2) / S) & 1)) ok = false;
+      issue(nxt);
     }
-    __nv_bfloat16* tA = sA + s * kM * kKC;
-    __nv_bfloat16* tB = sB + s * NP * kKC;
-    const int k0 = ch * kKC;
-    // A: 8 consecutive frame-columns of one vertex row per 16-byte load
-    for (int t = tid; t < kKC * (kM / 8); t += kTT) {
-      const int k = t / (kM / 8), mg = (t % (kM / 8)) * 8;
-      const int row = k0 + k;
-      __nv_bfloat16 v[8];
-      if (row < nb && m0 + mg + 8 <= cols) {
-        const uint4 q = *reinterpret_cast<const uint4*>(X + (size_t)a.verts[r0 + row] * cols + m0 + mg);
-        const __nv_bfloat16* qv = reinterpret_cast<const __nv_bfloat16*>(&q);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = qv[j];
-      } else {
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-          v[j] = (row < nb && m0 + mg + j < cols)
-                     ? X[(size_t)a.verts[r0 + row] * cols + m0 + mg + j]
-                     : __float2bfloat16(0.f);
-      }
-#pragma unroll
-      for (int j = 0; j < 8; ++j) tA[kmaj(mg + j, k, kKC)] = v[j];
-    }
-    // B: the basis rows, converted to bf16 (zero past c and past the block)
-    for (int t = tid; t < kKC * NP; t += kTT) {
-      const int k = t / NP, n = t % NP;
-      const int row = k0 + k;
-      const float u = (row < nb && n < c) ? U[(size_t)(r0 + row) * a.ld + n] : 0.f;
-      tB[kmaj(n, k, kKC)] = __float2bfloat16(u);
-    }
+    cp_commit();
+    cp_wait<kD>();  // chunk ch's copies (this thread's) have landed
     asm volatile("fence.proxy.async.shared::cta;");
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;");
+      const int st = ch % S;
+      const uint32_t aBase = smem_u32(sA + st * stageA), bBase = smem_u32(sB + st * stageB);
 #pragma unroll
       for (int q = 0; q < kKC / 16; ++q) {
-        const uint64_t da = smem_desc(smem_u32(tA) + q * 256, 128, 1024);
-        const uint64_t db = smem_desc(smem_u32(tB) + q * 256, 128, 1024);
+        const uint64_t da = smem_desc(aBase + q * 2 * (kM / 8) * 128, (kM / 8) * 128, 128);
+        const uint64_t db = smem_desc(bBase + q * 2 * gB * 128, gB * 128, 128);
         mma_bf16(tmem, da, db, idesc, (ch > 0 || q > 0) ? 1u : 0u);
       }
-      mma_commit(&mbar[s]);
+      mma_commit(&mbar[st]);
     }
   }
-  // drain: the last commit of each stage in use
-  for (int s = 0; s < 2 && s < nchunk; ++s) {
-    if (!mbar_wait(&mbar[s], phase[s])) ok = false;
-  }
+  cp_wait<0>();
+  // the last commit covers every MMA issued before it
+  if (nchunk > 0 && !mbar_wait(&mbar[(nchunk - 1) % S], ((nchunk - 1) / S) & 1)) ok = false;
   asm volatile("tcgen05.fence::after_thread_sync;");
-  if (ok && warp < 4 && nchunk > 0) {
-    const int m = warp * 32 + (tid & 31);
+  if (ok && nchunk > 0) {
+    // warp w reads lanes 32 (w % 4) .. + 31; warps 0-3 and 4-7 split the columns
+    const int m = (warp & 3) * 32 + (tid & 31);
     const size_t eb = (size_t)a.eoff[b];
-    for (int c0 = 0; c0 < NP; c0 += 16) {
+    for (int c0 = (warp >> 2) * 16; c0 < NP; c0 += 32) {
       float v[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
+      tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + c0, v);
 #pragma unroll
       for (int j = 0; j < 16; ++j)
         if (c0 + j < c && m0 + m < cols) E[(eb + c0 + j) * cols + m0 + m] = v[j];
@@ -193,80 +264,125 @@ __global__ void __launch_bounds__(kTT) k_project_tc(ProjArgs a, const float* __r
   if (warp == 0) tmem_free(tmem, tcols);
 }
 
-// X~ tile = U E for block b = blockIdx.z, vertex rows [m0, m0 + 128) and
-// columns [n0, n0 + 128): A[m][k] = U[r0 + m0 + m][k], B[n][k] = E[eoff + k][n0 + n],
-// K = c padded to KP (a multiple of 16) in one stage.
-__global__ void __launch_bounds__(kTT) k_recon_tc(ProjArgs a, const float* __restrict__ U,
-                                                  const float* __restrict__ E,
+// X~ rows [m0, m0 + 128) of block b = blockIdx.y (m0 = 128 blockIdx.x) for
+// all columns: A[m][k] = Ub[r0 + m0 + m][k] (K-major, resident for the whole
+// CTA), B[n][k] = Eb[eoff + k][n0 + n] (MN-major), one 128-column tile after
+// the other.  Both operands arrive by 16-byte asynchronous copies; the B tile
+// of the next column tile is in flight while the current one drains.  The
+// accumulator is double-buffered in tensor memory (2 x 128 columns), so the
+// MMAs of tile j run while tile j - 1 drains: tcgen05.ld -> shared staging
+// (row stride 132 floats, conflict-free) -> full 512-byte row segments to
+// global memory.
+constexpr int kNT = 128;
+constexpr int kOS = kNT + 4;   // staging row stride (floats)
+__global__ void __launch_bounds__(kTT) k_recon_tc(ProjArgs a, const __nv_bfloat16* __restrict__ Ub,
+                                                  const __nv_bfloat16* __restrict__ Eb, int colsP,
                                                   float* __restrict__ X, int KP, int* status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  constexpr int NT = 128;
   __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(smem_raw);  // kM x KP
-  __nv_bfloat16* sB = sA + kM * KP;                                 // NT x KP
-  __shared__ __align__(8) uint64_t mbar;
+  __nv_bfloat16* sB = sA + kM * KP;                                 // 2 x kNT x KP
+  float* out = reinterpret_cast<float*>(sB + 2 * kNT * KP);         // kM x kOS
+  __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_base;
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int b = blockIdx.z;
+  __shared__ int32_t sv[kM];   // the tile's vertex ids
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int b = blockIdx.y;
   const int c = a.cb[b];
   const int r0 = a.bptr[b], nb = a.bptr[b + 1] - r0;
-  const int m0 = blockIdx.y * kM, n0 = blockIdx.x * NT;
+  const int m0 = blockIdx.x * kM;
   const int cols = a.cols;
   if (m0 >= nb) return;  // uniform per CTA, before any tensor-memory use
-  if (warp == 0) tmem_alloc(&tmem_base, NT);
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
-    asm volatile("fence.mbarrier_init.release.cluster;");
-  }
+  if (warp == 0) tmem_alloc(&tmem_base, 2 * kNT);
+  if (tid < kM) sv[tid] = m0 + tid < nb ? a.verts[r0 + m0 + tid] : 0;
+  if (tid < 2) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[tid])));
+  if (tid == 0) asm volatile("fence.mbarrier_init.release.cluster;");
   const size_t eb = (size_t)a.eoff[b];
-  for (int t = tid; t < kM * KP; t += kTT) {
-    const int m = t / KP, k = t % KP;
-    const float u = (m0 + m < nb && k < c) ? U[(size_t)(r0 + m0 + m) * a.ld + k] : 0.f;
-    sA[kmaj(m, k, KP)] = __float2bfloat16(u);
+  const int gA = KP / 8;
+  // A: 128 rows x KP/8 pieces; item -> (row % 8 fastest, piece, row / 8)
+  for (int it = tid; it < kM * gA; it += kTT) {
+    const int q = it >> 3, m = (it & 7) + 8 * (q / gA), kg = q % gA;
+    const bool ok = m0 + m < nb;
+    const __nv_bfloat16* src = ok ? Ub + (size_t)(r0 + m0 + m) * KP + 8 * kg : Ub;
+    cp16(sA + ((m >> 3) * gA + kg) * 64 + (m & 7) * 8, src, ok ? 16 : 0);
   }
-  for (int t = tid; t < KP * NT; t += kTT) {
-    const int k = t / NT, n = t % NT;
-    const float e = (k < c && n0 + n < cols) ? E[(eb + k) * cols + n0 + n] : 0.f;
-    sB[kmaj(n, k, KP)] = __float2bfloat16(e);
-  }
-  asm volatile("fence.proxy.async.shared::cta;");
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  const uint32_t tmem = tmem_base;
-  if (tid == 0) {
-    const uint32_t idesc = idesc_bf16(kM, NT);
-    for (int q = 0; q < KP / 16; ++q) {
-      const uint64_t da = smem_desc(smem_u32(sA) + q * 256, 128, (KP / 8) * 128);
-      const uint64_t db = smem_desc(smem_u32(sB) + q * 256, 128, (KP / 8) * 128);
-      mma_bf16(tmem, da, db, idesc, q > 0 ? 1u : 0u);
+  // B tile j: KP rows x 16 pieces of 8 columns; item -> (k % 8 fastest, piece, k / 8)
+  auto issue_B = [&](int j) {
+    const int n0 = j * kNT;
+    __nv_bfloat16* tB = sB + (j & 1) * kNT * KP;
+    for (int it = tid; it < KP * (kNT / 8); it += kTT) {
+      const int k = (it & 7) + 8 * (it >> 7), ng = (it >> 3) & 15;
+      const int n = n0 + 8 * ng;
+      const bool ok = k < c && n < colsP;
+      const __nv_bfloat16* src = ok ? Eb + (eb + k) * colsP + n : Eb;
+      cp16(tB + mnmaj(8 * ng, k, kNT), src, ok ? 16 : 0);
     }
-    mma_commit(&mbar);
-  }
-  const bool ok = mbar_wait(&mbar, 0);
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  if (ok && warp < 4) {
-    const int m = warp * 32 + (tid & 31);
-    const bool live = m0 + m < nb;
-    float* xo = live ? X + (size_t)a.verts[r0 + m0 + m] * cols : nullptr;
-    for (int c0 = 0; c0 < NT; c0 += 16) {
-      float v[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
-      if (!live) continue;
-      if (n0 + c0 + 16 <= cols && (cols & 3) == 0) {
+  };
+  const int ntiles = (cols + kNT - 1) / kNT;
+  issue_B(0);
+  cp_commit();   // group 0: A and B tile 0
+  const bool vec = (cols & 3) == 0 && ((uintptr_t)X & 15) == 0;
+  bool ok = true;
+  for (int j = 0; j < ntiles; ++j) {
+    // B tile j + 1 goes to the buffer that the MMAs of tile j - 1 read
+    if (j >= 1 && !mbar_wait(&mbar[(j - 1) & 1], ((j - 1) >> 1) & 1)) ok = false;
+    if (j + 1 < ntiles) issue_B(j + 1);
+    cp_commit();
+    cp_wait<1>();  // this thread's copies of tile j (and A) have landed
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t idesc = idesc_bf16_major(kM, kNT, 0, 1);
+      const uint32_t aBase = smem_u32(sA), bBase = smem_u32(sB + (j & 1) * kNT * KP);
+      for (int q = 0; q < KP / 16; ++q) {
+        const uint64_t da = smem_desc(aBase + q * 256, 128, gA * 128);
+        const uint64_t db = smem_desc(bBase + q * 2 * (kNT / 8) * 128, (kNT / 8) * 128, 128);
+        mma_bf16(tmem_base + (uint32_t)((j & 1) * kNT), da, db, idesc, q > 0 ? 1u : 0u);
+      }
+      mma_commit(&mbar[j & 1]);
+    }
+    // drain tile j - 1 (its MMAs were waited for above), then, after the
+    // loop, the last tile
+    const int last = (j == ntiles - 1);
+    for (int jj = (j >= 1 ? j - 1 : j); jj <= j; ++jj) {
+      if (jj == j && !last) break;
+      if (jj == j && !mbar_wait(&mbar[jj & 1], (jj >> 1) & 1)) ok = false;
+      const int n0 = jj * kNT;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      __syncthreads();  // the previous drain's readers are done with `out`
+      const int m = (warp & 3) * 32 + lane;
+      const int cbase = (warp >> 2) * 64;
 #pragma unroll
-        for (int j = 0; j < 16; j += 4)
-          *reinterpret_cast<float4*>(xo + n0 + c0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-      } else {
+      for (int c0 = 0; c0 < 64; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem_base + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((jj & 1) * kNT + cbase + c0), v);
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
-          if (n0 + c0 + j < cols) xo[n0 + c0 + j] = v[j];
+        for (int e = 0; e < 16; e += 4)
+          *reinterpret_cast<float4*>(out + m * kOS + cbase + c0 + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncthreads();
+      const int width = min(kNT, cols - n0);
+      for (int r = warp; r < kM; r += kTT / 32) {
+        if (m0 + r >= nb) break;
+        float* dst = X + (size_t)sv[r] * cols + n0;
+        const float* srow = out + r * kOS;
+        if (ok) {
+          if (vec && width == kNT) {
+            reinterpret_cast<float4*>(dst)[lane] = reinterpret_cast<const float4*>(srow)[lane];
+          } else {
+            for (int e = lane; e < width; e += 32) dst[e] = srow[e];
+          }
+        }
       }
     }
   }
+  cp_wait<0>();
   if (!ok && tid == 0) atomicOr(status, ST_TIMEOUT);
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) tmem_free(tmem, NT);
+  if (warp == 0) tmem_free(tmem_base, 2 * kNT);
 }
 
 inline int pad16(int c) { return (c + 15) & ~15; }
@@ -283,31 +399,52 @@ void configure_tc_kernels() {
   set_max_dynamic_smem(k_recon_tc);
 }
 
-// E = U^T X with X in bf16 on tensor cores; needs cols % 8 == 0 and c <= 256.
-int launch_project_tc(const ProjArgs& a, const float* U, const void* X, float* E, int* status,
+// Ub = bf16 copy of the basis, NP = pad16(cmax) columns, zero past each c_b.
+int launch_basis_bf16(const ProjArgs& a, const float* U, void* Ub, cudaStream_t s) {
+  const int NP = pad16(a.cmax);
+  const int per = a.max_nb * (NP / 8);
+  dim3 grid((per + 255) / 256, a.k);
+  k_basis_bf16<<<grid, 256, 0, s>>>(a, U, (__nv_bfloat16*)Ub, NP);
+  return cudaGetLastError() == cudaSuccess ? BSP_OK : BSP_ERR_CUDA;
+}
+
+// E = U^T X with X in bf16 on tensor cores; Ub from launch_basis_bf16; needs
+// cols % 8 == 0 and c <= 256.
+int launch_project_tc(const ProjArgs& a, const void* Ub, const void* X, float* E, int* status,
                       cudaStream_t s) {
   const int NP = pad16(a.cmax);
   if (a.cols % 8 != 0 || NP > 256) return BSP_ERR_INVALID_ARG;
-  const size_t smem = (size_t)2 * (kM + NP) * kKC * sizeof(__nv_bfloat16);
+  const size_t smem = (size_t)kS * (kM + NP) * kKC * sizeof(__nv_bfloat16) +
+                      (size_t)a.max_nb * sizeof(int32_t);
+  if (smem > 220 * 1024) return BSP_ERR_INVALID_ARG;
   dim3 grid((a.cols + kM - 1) / kM, a.k);
   prof_begin(KC_PROJECT, s);
-  k_project_tc<<<grid, kTT, smem, s>>>(a, U, (const __nv_bfloat16*)X, E, NP, tmem_cols(NP), status);
+  k_project_tc<<<grid, kTT, smem, s>>>(a, (const __nv_bfloat16*)Ub, (const __nv_bfloat16*)X, E, NP,
+                                       tmem_cols(NP), status);
   prof_end(KC_PROJECT, s);
   return cudaGetLastError() == cudaSuccess ? BSP_OK : BSP_ERR_CUDA;
 }
 
-// X = U E with bf16 operands on tensor cores (FP32 accumulation and output); c <= 128.
-int launch_recon_tc(const ProjArgs& a, const float* U, const float* E, float* X, int* status,
-                    cudaStream_t s) {
+// X = U E with bf16 operands on tensor cores (FP32 accumulation and output);
+// Ub from launch_basis_bf16, Eb scratch of erows x pad8(cols) bf16; c <= 128.
+int launch_recon_tc(const ProjArgs& a, const void* Ub, const float* E, int64_t erows, void* Eb,
+                    float* X, int* status, cudaStream_t s) {
   const int KP = pad16(a.cmax);
   if (KP > 128) return BSP_ERR_INVALID_ARG;
-  // at least 60 KB of shared memory per CTA keeps <= 3 CTAs (384 tensor-memory
+  const int colsP = (a.cols + 7) & ~7;
+  const int64_t pieces = erows * (colsP / 8);
+  if (pieces > 0) {
+    const int grid = (int)std::min<int64_t>((pieces + 255) / 256, 152 * 16);
+    k_coef_bf16<<<grid, 256, 0, s>>>(E, (__nv_bfloat16*)Eb, erows, a.cols, colsP);
+  }
+  // at least 80 KB of shared memory per CTA keeps <= 2 CTAs (512 tensor-memory
   // columns) per SM, so tcgen05.alloc never waits for another CTA
-  size_t smem = (size_t)(kM + 128) * KP * sizeof(__nv_bfloat16);
-  if (smem < 60 * 1024) smem = 60 * 1024;
-  dim3 grid((a.cols + 127) / 128, (a.max_nb + kM - 1) / kM, a.k);
+  size_t smem = (size_t)3 * kNT * KP * sizeof(__nv_bfloat16) + (size_t)kM * kOS * sizeof(float);
+  if (smem < 80 * 1024) smem = 80 * 1024;
+  dim3 grid((a.max_nb + kM - 1) / kM, a.k);
   prof_begin(KC_RECON, s);
-  k_recon_tc<<<grid, kTT, smem, s>>>(a, U, E, X, KP, status);
+  k_recon_tc<<<grid, kTT, smem, s>>>(a, (const __nv_bfloat16*)Ub, (const __nv_bfloat16*)Eb, colsP, X,
+                                     KP, status);
   prof_end(KC_RECON, s);
   return cudaGetLastError() == cudaSuccess ? BSP_OK : BSP_ERR_CUDA;
 }

@@ -395,27 +395,24 @@ def _bf16_round(a):
     return t.numpy()
 
 
-@pytest.mark.parametrize("c", [48, 32])
-def test_tensor_core_projection_and_reconstruction(c):
-    """All frames at once (Sec. 7.3): E = U^T X and X~ = U E on tcgen05 with BF16 operands."""
-    N, T, F = 64, 32, 200
-    frames, faces = synth.torus_frames(N, frames=F, seed=3)
+def _check_tensor_core_paths(N, F, ptr, verts, parent, c, seed):
+    frames, faces = synth.torus_frames(N, frames=F, seed=seed)
     xyz = frames[0]
-    ptr, verts = synth.tile_partition(N, T)
-    parent = synth.raster_chain(4)
+    k = len(ptr) - 1
     cols = 3 * F
     X = np.ascontiguousarray(frames.transpose(1, 0, 2).reshape(N * N, cols))
     h = bsp.bsp_mesh_create(xyz, faces, ptr, verts, parent, bsp.make_opts(precision=bsp.BSP_PREC_F32))
     try:
-        starts = synth.gaussian_starts(ptr, parent, c, seed=4).astype(np.float32)
+        starts = synth.gaussian_starts(ptr, parent, c, seed=seed + 1).astype(np.float32)
         bsp.bsp_oi_track(h, c, 2, starts)
         Xb = torch.tensor(X, dtype=torch.float32, device="cuda").to(torch.bfloat16)
-        E = torch.empty(4 * c, cols, dtype=torch.float32, device="cuda")
+        E = torch.empty(k * c, cols, dtype=torch.float32, device="cuda")
         bsp.bsp_project(h, Xb, bsp.BSP_DT_BF16, cols, E)
-        Xo = torch.empty(N * N, cols, dtype=torch.float32, device="cuda")
+        Xo = torch.full((N * N, cols), float("nan"), dtype=torch.float32, device="cuda")
         bsp.bsp_reconstruct_bf16(h, E, cols, Xo)
         torch.cuda.synchronize()
         En, Xon = E.cpu().double().numpy(), Xo.cpu().double().numpy()
+        assert np.isfinite(Xon).all()          # every output row and column written
         Xq = Xb.to(torch.float64).cpu().numpy()
         om = O.build_mesh(N * N, ptr, verts, parent, faces=faces)
         for b, blk in enumerate(om.blocks):
@@ -434,3 +431,21 @@ def test_tensor_core_projection_and_reconstruction(c):
         assert err <= 2e-2, err
     finally:
         bsp.bsp_mesh_destroy(h)
+
+
+@pytest.mark.parametrize("c", [48, 32])
+def test_tensor_core_projection_and_reconstruction(c):
+    """All frames at once (Sec. 7.3): E = U^T X and X~ = U E on tcgen05 with BF16 operands."""
+    N = 64
+    ptr, verts = synth.tile_partition(N, 32)
+    _check_tensor_core_paths(N, 200, ptr, verts, synth.raster_chain(4), c, seed=3)
+
+
+@pytest.mark.parametrize("F,c", [(24, 20), (200, 20), (40, 72)])
+def test_tensor_core_ragged_blocks_and_columns(F, c):
+    """Uneven BFS blocks (rows not a multiple of the 64-row chunk or 128-row
+    tile), c not a multiple of 16, and a last column tile narrower than 128."""
+    N = 48
+    ptr, verts = synth.bfs_partition(N, target_blocks=6, min_size=150, max_size=700, seed=7)
+    ptr, verts, parent = synth.block_forest(ptr, verts, N, roots=2, seed=8)
+    _check_tensor_core_paths(N, F, ptr, verts, parent, c, seed=5)
