@@ -139,6 +139,37 @@ void configure_once() {
   });
 }
 
+// Sort a batch by the size bucket of the batched CG (rows per thread 1, 4, 8,
+// 16; blocks too large last) and return the bucket offsets off[0..4] and the
+// largest block of every bucket.
+void sort_by_bucket(const bsp_mesh* M, std::vector<int32_t>& list, int off[5], int rows[4]) {
+  auto nb = [&](int b) { return M->h_bptr[b + 1] - M->h_bptr[b]; };
+  auto key = [&](int b) {
+    const int q = cg_bucket(nb(b));
+    return q < 0 ? 4 : q;
+  };
+  std::stable_sort(list.begin(), list.end(), [&](int a, int b) { return key(a) < key(b); });
+  off[0] = 0;
+  for (int q = 0; q < 4; ++q) {
+    int cnt = 0, mx = 0;
+    for (int b : list)
+      if (key(b) == q) {
+        ++cnt;
+        mx = std::max(mx, nb(b));
+      }
+    off[q + 1] = off[q] + cnt;
+    rows[q] = mx;
+  }
+}
+
+// The batched one-column-per-CTA CG, launched per size bucket, for batches of
+// several blocks (automatic column choice only; slab widths set by the caller
+// keep the shared-memory slab kernel).
+bool use_buckets(const bsp_mesh* M, int nbatch, int wmax) {
+  return M->opts.cols_per_cta == 0 && nbatch >= 2 &&
+         cg1_fits(wmax, M->max_deg, M->real_bytes, M->d_wt != nullptr);
+}
+
 int pad4(int c) { return (c + 3) & ~3; }
 
 void release(bsp_mesh* m) {
@@ -171,6 +202,8 @@ int stream_error_status(bsp_mesh* m, cudaStream_t s) {
   m->stats.jacobi_sweeps = cs.jacobi_sweeps;
   if (st & ST_NUMERICAL)
     return fail(BSP_ERR_NUMERICAL, "Gram matrix not positive definite or non-finite values");
+  if (st & ST_CG_BREAKDOWN)
+    return fail(BSP_ERR_NUMERICAL, "CG breakdown: (p, A p) <= 0 or a non-finite recurrence");
   if (st & ST_TIMEOUT) return fail(BSP_ERR_TIMEOUT, "a bounded device wait expired");
   if (st & ST_NOT_CONVERGED)
     return fail(BSP_ERR_NOT_CONVERGED,
@@ -250,6 +283,10 @@ int create_common(const double* xyz, int64_t n, const int32_t* tri, int64_t m, i
   }
   M->waves.assign(levels, {});
   for (int b = 0; b < k; ++b) M->waves[M->h_level[b]].push_back(b);
+  M->wave_bucket.assign(levels, {});
+  M->wave_bucket_rows.assign(levels, {});
+  for (int l = 0; l < levels; ++l)
+    sort_by_bucket(M, M->waves[l], M->wave_bucket[l].data(), M->wave_bucket_rows[l].data());
   M->h_wave_off.assign(levels + 1, 0);
   for (int l = 0; l < levels; ++l) {
     M->h_wave_off[l + 1] = M->h_wave_off[l] + (int32_t)M->waves[l].size();
@@ -481,17 +518,25 @@ int enqueue_fixed(bsp_mesh* M, int c, int t_max, cudaStream_t s, int* launches) 
       if ((rc = launch_cholqr2<T, TA>(dn, U, U, (TA*)M->d_Gp, (T*)M->d_Rsm, s, launches)))
         return fail(rc, "launch failed (Onorm of start)");
     }
-    CgArgs ca{batch, nbw, M->d_cb, M->c_cap, M->opts.z, M->opts.delta, M->opts.cg_rtol,
+    // S^z V is applied as z solves with an Onorm after each: the span is that
+    // of R^z V (Onorm keeps the span), and every solve sees a well-conditioned
+    // input (R^z V itself loses rank in FP32 once ((lambda_c + delta)/delta)^z
+    // nears 1/u).
+    CgArgs ca{batch, nbw, M->d_cb, M->c_cap, 1, M->opts.delta, M->opts.cg_rtol,
               M->opts.cg_max_steps, M->d_status, M->d_cgstats, M->max_deg};
     const int cs = pick_cs(M, nbw, c, sizeof(T));
-    for (int t = 0; t < t_max; ++t) {
-      if ((rc = launch_cg<T>(mv, U, Y, ca, cs, wmax, c, s)))
-        return fail(rc, "CG launch failed (block too large for shared memory?)");
+    const bool buckets = use_buckets(M, nbw, wmax);
+    const int sub = t_max * M->opts.z;
+    for (int t = 0; t < sub; ++t) {
+      rc = buckets ? launch_cg_buckets<T>(mv, U, Y, ca, M->wave_bucket[l].data(),
+                                          M->wave_bucket_rows[l].data(), c, s)
+                   : launch_cg<T>(mv, U, Y, ca, cs, wmax, c, s);
+      if (rc) return fail(rc, "CG launch failed (block too large for shared memory?)");
       ++*launches;
       // Intermediate steps only need a well-conditioned basis for the next
       // solve (span(S Q) = span(S Y)): one Cholesky-QR pass; the last step
       // orthonormalises to working precision with CholeskyQR2.
-      const int passes = (t + 1 < t_max) ? 1 : 2;
+      const int passes = (t + 1 < sub) ? 1 : 2;
       if ((rc = launch_cholqr2<T, TA>(da, Y, U, (TA*)M->d_Gp, (T*)M->d_Rsm, s, launches, passes)))
         return fail(rc, "launch failed (Onorm)");
     }
@@ -640,6 +685,8 @@ int track_dynamic(bsp_mesh* M, const void* X, double tol, int c_min, int c_max, 
   int launches = 0;
   for (size_t l = 0; l < M->waves.size(); ++l) {
     std::vector<int32_t> active = M->waves[l];
+    int boff[5], brows[4];
+    sort_by_bucket(M, active, boff, brows);
     for (int b : active) {
       int p = M->h_parent[b];
       int nb = M->h_bptr[b + 1] - M->h_bptr[b];
@@ -677,11 +724,14 @@ int track_dynamic(bsp_mesh* M, const void* X, double tol, int c_min, int c_max, 
       batch_stats(active, &wmax, &cm);
       const int nbw = (int)active.size();
       DenseArgs da{d_list, nbw, M->d_bptr, M->d_cb, c_cap, cm, wmax, M->d_status};
-      CgArgs ca{d_list, nbw, M->d_cb, c_cap, M->opts.z, M->opts.delta, M->opts.cg_rtol,
+      CgArgs ca{d_list, nbw, M->d_cb, c_cap, 1, M->opts.delta, M->opts.cg_rtol,
                 M->opts.cg_max_steps, M->d_status, M->d_cgstats, M->max_deg};
       const int cs = pick_cs(M, nbw, cm, sizeof(T));
-      for (int t = 0; t < t_max; ++t) {
-        if ((rc = launch_cg<T>(mv, U, Y, ca, cs, wmax, cm, s))) return fail(rc, "CG launch failed");
+      const bool buckets = use_buckets(M, nbw, wmax);
+      for (int t = 0; t < t_max * M->opts.z; ++t) {   // z solves per step, Onorm after each
+        rc = buckets ? launch_cg_buckets<T>(mv, U, Y, ca, boff, brows, cm, s)
+                     : launch_cg<T>(mv, U, Y, ca, cs, wmax, cm, s);
+        if (rc) return fail(rc, "CG launch failed");
         ++launches;
         if ((rc = launch_cholqr2<T, TA>(da, Y, U, (TA*)M->d_Gp, (T*)M->d_Rsm, s, &launches)))
           return fail(rc, "launch failed");
@@ -706,6 +756,7 @@ int track_dynamic(bsp_mesh* M, const void* X, double tol, int c_min, int c_max, 
         if (act[b] == 1 && hc[b] < cmaxb) grow.push_back(b);
       }
       if (grow.empty()) break;
+      sort_by_bucket(M, grow, boff, brows);
       if ((rc = upload(grow, d_list))) return rc;
       CU(cudaMemcpyAsync(M->d_round, rounds.data(), sizeof(int32_t) * M->k, cudaMemcpyHostToDevice, s));
       batch_stats(grow, &wmax, &cm);

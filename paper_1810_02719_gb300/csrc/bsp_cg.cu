@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(kThreads) k_cg(MeshView<T> mv, const T* __rest
       atomicAdd(&a.stats->not_converged, 1);
       atomicOr(a.status, ST_NOT_CONVERGED);
     }
-    if (bad) atomicOr(a.status, ST_NUMERICAL);
+    if (bad) atomicOr(a.status, ST_CG_BREAKDOWN);
   }
 }
 
@@ -340,12 +340,16 @@ __global__ void k_spmm_scalar(int64_t n, MeshView<T> mv, const int32_t* __restri
 }
 
 
-// ---- one column per CTA, latency-optimised (the warm-started chain case).
+// ---- one column per CTA, latency-optimised (the warm-started chain, and the
+// batches of dynamic c, whose growth columns start from random vectors).
 // Chronopoulos-Gear CG: one fused reduction of (r, r) and (A r, r) per step and
-// two barriers; each thread keeps its rows' x, r, p, s = A p, w = A r and the
-// rows' ELL pattern (width ELLW) in registers, only r goes through shared
-// memory for the neighbour reads.  Rows: i = threadIdx.x + 256 m, m < MAXR.
-template <typename T, int MAXR, int ELLW>
+// two barriers; each thread keeps its rows' x, r, p, s = A p, w = A r in
+// registers, only r goes through shared memory for the neighbour reads.
+// Rows: i = threadIdx.x + 256 m, m < MAXR.  The rows' pattern (ELL, width
+// ELLW) sits in registers for MAXR <= 4 (blocks up to 1,024 rows) and in
+// shared memory for larger blocks (SMEM_ELL: padded entries point at a zero
+// slot of the shared vector, so every row does ELLW branch-free updates).
+template <typename T, int MAXR, int ELLW, bool SMEM_ELL>
 __global__ void __launch_bounds__(kThreads) k_cg1(MeshView<T> mv, const T* __restrict__ V,
                                                   T* __restrict__ Y, CgArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -355,33 +359,59 @@ __global__ void __launch_bounds__(kThreads) k_cg1(MeshView<T> mv, const T* __res
   if (col >= a.cb[b]) return;
   const int r0 = mv.bptr[b];
   const int nb = mv.bptr[b + 1] - r0;
-  T* rs = reinterpret_cast<T*>(smem_raw);          // nb entries: the vector being multiplied
+  constexpr int CAP = MAXR * kThreads;            // rows this instantiation holds
+  constexpr int RSN = SMEM_ELL ? CAP + 4 : 0;     // shared vector incl. the zero slot
+  T* rs = reinterpret_cast<T*>(smem_raw);
+  // SMEM_ELL layout after rs: diagonal + delta [CAP], weights [CAP][ELLW]
+  // (weighted meshes only), neighbour indices [CAP][ELLW]
+  T* sdd = rs + RSN;
+  T* swt = sdd + (SMEM_ELL ? CAP : 0);
+  uint16_t* snb = reinterpret_cast<uint16_t*>(swt + ((SMEM_ELL && mv.wt) ? (size_t)CAP * ELLW : 0));
   const T delta = (T)a.delta;
   const T rtol2 = (T)(a.rtol * a.rtol);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  // pattern and diagonal of my rows
-  uint16_t nbr[MAXR][ELLW];
-  T wt[MAXR][ELLW];
-  T dd[MAXR];
-  int deg[MAXR];
+  constexpr int RR = SMEM_ELL ? 1 : MAXR;          // rows whose pattern is in registers
+  uint16_t nbr[RR][ELLW];
+  T wt[RR][ELLW];
+  T dd[RR];
+  int deg[RR];
 #pragma unroll
   for (int m = 0; m < MAXR; ++m) {
     const int i = threadIdx.x + kThreads * m;
-    deg[m] = 0;
-    dd[m] = 0;
+    const int q = SMEM_ELL ? 0 : m;
+    int dg = 0;
+    T d0 = 0;
+    uint16_t nl[ELLW];
+    T wl[ELLW];
 #pragma unroll
-    for (int e = 0; e < ELLW; ++e) { nbr[m][e] = 0; wt[m][e] = 0; }
+    for (int e = 0; e < ELLW; ++e) { nl[e] = SMEM_ELL ? (uint16_t)CAP : 0; wl[e] = 0; }
     if (i < nb) {
       const int e0 = mv.rowptr[r0 + i], e1 = mv.rowptr[r0 + i + 1];
-      deg[m] = e1 - e0;
-      dd[m] = mv.diag[r0 + i] + delta;
+      dg = e1 - e0;
+      d0 = mv.diag[r0 + i] + delta;
 #pragma unroll
       for (int e = 0; e < ELLW; ++e)
-        if (e < e1 - e0) {
-          nbr[m][e] = mv.col[e0 + e];
-          wt[m][e] = mv.wt ? mv.wt[e0 + e] : T(1);
+        if (e < dg) {
+          nl[e] = mv.col[e0 + e];
+          wl[e] = mv.wt ? mv.wt[e0 + e] : T(1);
         }
     }
+    if constexpr (SMEM_ELL) {
+      sdd[i] = d0;
+#pragma unroll
+      for (int e = 0; e < ELLW; ++e) {
+        snb[(size_t)i * ELLW + e] = nl[e];
+        if (mv.wt) swt[(size_t)i * ELLW + e] = wl[e];
+      }
+    } else {
+      deg[q] = dg;
+      dd[q] = d0;
+#pragma unroll
+      for (int e = 0; e < ELLW; ++e) { nbr[q][e] = nl[e]; wt[q][e] = wl[e]; }
+    }
+  }
+  if constexpr (SMEM_ELL) {
+    if (threadIdx.x == 0) rs[CAP] = T(0);          // the padded entries' target
   }
   int buf = 0;
   // sum of two per-thread values over the CTA (one barrier, double buffered)
@@ -399,11 +429,37 @@ __global__ void __launch_bounds__(kThreads) k_cg1(MeshView<T> mv, const T* __res
   auto apply = [&](const T (&v)[MAXR], T (&out)[MAXR]) {
 #pragma unroll
     for (int m = 0; m < MAXR; ++m) {
-      T acc = dd[m] * v[m];
+      if constexpr (SMEM_ELL) {
+        const int i = threadIdx.x + kThreads * m;
+        T acc = 0;
+        if (i < nb) {
+          acc = sdd[i] * v[m];
+          uint16_t nl[ELLW];
+          if constexpr (ELLW == 8) {
+            const uint4 q = *reinterpret_cast<const uint4*>(snb + (size_t)i * ELLW);
+            const uint16_t* qp = reinterpret_cast<const uint16_t*>(&q);
 #pragma unroll
-      for (int e = 0; e < ELLW; ++e)
-        if (e < deg[m]) acc -= wt[m][e] * rs[nbr[m][e]];
-      out[m] = acc;
+            for (int e = 0; e < 8; ++e) nl[e] = qp[e];
+          } else {
+#pragma unroll
+            for (int e = 0; e < ELLW; ++e) nl[e] = snb[(size_t)i * ELLW + e];
+          }
+          if (mv.wt) {
+#pragma unroll
+            for (int e = 0; e < ELLW; ++e) acc -= swt[(size_t)i * ELLW + e] * rs[nl[e]];
+          } else {
+#pragma unroll
+            for (int e = 0; e < ELLW; ++e) acc -= rs[nl[e]];
+          }
+        }
+        out[m] = acc;
+      } else {
+        T acc = dd[m] * v[m];
+#pragma unroll
+        for (int e = 0; e < ELLW; ++e)
+          if (e < deg[m]) acc -= wt[m][e] * rs[nbr[m][e]];
+        out[m] = acc;
+      }
     }
   };
   T bvec[MAXR], x[MAXR], r[MAXR], p[MAXR], sv[MAXR], wv[MAXR];
@@ -504,18 +560,45 @@ __global__ void __launch_bounds__(kThreads) k_cg1(MeshView<T> mv, const T* __res
       atomicAdd(&a.stats->not_converged, 1);
       atomicOr(a.status, ST_NOT_CONVERGED);
     }
-    if (bad) atomicOr(a.status, ST_NUMERICAL);
+    if (bad) atomicOr(a.status, ST_CG_BREAKDOWN);
   }
 }
 
-template <typename T, int MAXR, int ELLW>
+// Shared memory of a k_cg1 launch: the shared vector, and for SMEM_ELL the
+// diagonal, the weights (weighted meshes) and the neighbour indices.
+template <typename T, int MAXR, int ELLW, bool SMEM_ELL>
+size_t cg1_smem(int max_nb, bool weighted) {
+  if (!SMEM_ELL) return (size_t)max_nb * sizeof(T);
+  const size_t cap = (size_t)MAXR * kThreads;
+  return (cap + 4 + cap) * sizeof(T) + (weighted ? cap * ELLW * sizeof(T) : 0) +
+         cap * ELLW * sizeof(uint16_t);
+}
+
+template <typename T, int MAXR, int ELLW, bool SMEM_ELL>
 int launch_cg1_t(const MeshView<T>& mv, const T* V, T* Y, const CgArgs& a, int max_nb, int c_max,
                  cudaStream_t s) {
   dim3 grid(c_max, a.nbatch);
-  prof_begin(KC_CG, s);
-  k_cg1<T, MAXR, ELLW><<<grid, kThreads, (size_t)max_nb * sizeof(T), s>>>(mv, V, Y, a);
-  prof_end(KC_CG, s);
+  const size_t smem = cg1_smem<T, MAXR, ELLW, SMEM_ELL>(max_nb, mv.wt != nullptr);
+  if (smem > 220 * 1024) return BSP_ERR_INVALID_ARG;
+  k_cg1<T, MAXR, ELLW, SMEM_ELL><<<grid, kThreads, smem, s>>>(mv, V, Y, a);
   return cudaGetLastError() == cudaSuccess ? BSP_OK : BSP_ERR_CUDA;
+}
+
+// One-column-per-CTA CG for rows up to 4,096 and degrees up to 16: the
+// instantiation by rows per thread (1, 4 in registers; 8, 16 in shared memory).
+template <typename T>
+int launch_cg1_rows(const MeshView<T>& mv, const T* V, T* Y, const CgArgs& a, int max_nb,
+                    int c_max, cudaStream_t s) {
+  const int mr = (max_nb + kThreads - 1) / kThreads;
+  const bool w8 = a.max_deg <= 8;
+  if (mr <= 1) return w8 ? launch_cg1_t<T, 1, 8, false>(mv, V, Y, a, max_nb, c_max, s)
+                         : launch_cg1_t<T, 1, 16, false>(mv, V, Y, a, max_nb, c_max, s);
+  if (mr <= 4) return w8 ? launch_cg1_t<T, 4, 8, false>(mv, V, Y, a, max_nb, c_max, s)
+                         : launch_cg1_t<T, 4, 16, false>(mv, V, Y, a, max_nb, c_max, s);
+  if (mr <= 8) return w8 ? launch_cg1_t<T, 8, 8, true>(mv, V, Y, a, max_nb, c_max, s)
+                         : launch_cg1_t<T, 8, 16, true>(mv, V, Y, a, max_nb, c_max, s);
+  return w8 ? launch_cg1_t<T, 16, 8, true>(mv, V, Y, a, max_nb, c_max, s)
+            : launch_cg1_t<T, 16, 16, true>(mv, V, Y, a, max_nb, c_max, s);
 }
 
 template <typename T, int CS>
@@ -544,6 +627,55 @@ void configure_cg_kernels() {
   set_max_dynamic_smem(k_cg<double, 2>);
   set_max_dynamic_smem(k_cg<double, 4>);
   set_max_dynamic_smem(k_cg<double, 8>);
+  set_max_dynamic_smem(k_cg1<float, 8, 8, true>);
+  set_max_dynamic_smem(k_cg1<float, 8, 16, true>);
+  set_max_dynamic_smem(k_cg1<float, 16, 8, true>);
+  set_max_dynamic_smem(k_cg1<float, 16, 16, true>);
+  set_max_dynamic_smem(k_cg1<double, 8, 8, true>);
+  set_max_dynamic_smem(k_cg1<double, 8, 16, true>);
+  set_max_dynamic_smem(k_cg1<double, 16, 8, true>);
+  set_max_dynamic_smem(k_cg1<double, 16, 16, true>);
+}
+
+// Whether the one-column-per-CTA CG holds a block of max_nb rows (its shared
+// memory within the opt-in limit).
+bool cg1_fits(int max_nb, int max_deg, int real_bytes, bool weighted) {
+  if (max_deg <= 0 || max_deg > 16 || max_nb > 16 * kThreads) return false;
+  const int mr = (max_nb + kThreads - 1) / kThreads;
+  const size_t rows = mr <= 1 ? 1 : mr <= 4 ? 4 : mr <= 8 ? 8 : 16;
+  if (rows <= 4) return true;
+  const size_t cap = rows * kThreads, ellw = max_deg <= 8 ? 8 : 16;
+  const size_t bytes = (2 * cap + 4) * real_bytes + (weighted ? cap * ellw * real_bytes : 0) +
+                       cap * ellw * 2;
+  return bytes <= 220 * 1024;
+}
+
+// Size bucket of a block for the batched one-column-per-CTA CG: rows per
+// thread 1, 4, 8, 16 (buckets 0..3), -1 when the block is too large.
+int cg_bucket(int nb) {
+  return nb <= kThreads ? 0 : nb <= 4 * kThreads ? 1 : nb <= 8 * kThreads ? 2
+                            : nb <= 16 * kThreads ? 3 : -1;
+}
+
+// CG over a batch sorted by size bucket (bucket_off[q] .. bucket_off[q + 1] of
+// a.batch holds bucket q): one launch per non-empty bucket, each sized for
+// its own largest block.
+template <typename T>
+int launch_cg_buckets(const MeshView<T>& mv, const T* V, T* Y, const CgArgs& a,
+                      const int* bucket_off, const int* bucket_rows, int c_max, cudaStream_t s) {
+  if (!(a.max_deg > 0 && a.max_deg <= 16)) return BSP_ERR_INVALID_ARG;
+  prof_begin(KC_CG, s);
+  int rc = BSP_OK;
+  for (int q = 0; q < 4 && rc == BSP_OK; ++q) {
+    const int n = bucket_off[q + 1] - bucket_off[q];
+    if (n <= 0) continue;
+    CgArgs sub = a;
+    sub.batch = a.batch + bucket_off[q];
+    sub.nbatch = n;
+    rc = launch_cg1_rows<T>(mv, V, Y, sub, bucket_rows[q], c_max, s);
+  }
+  prof_end(KC_CG, s);
+  return rc;
 }
 
 template <typename T>
@@ -554,14 +686,12 @@ int cg_smem_bytes(int cs, int max_nb) {
 template <typename T>
 int launch_cg(const MeshView<T>& mv, const T* V, T* Y, const CgArgs& a, int cs, int max_nb,
               int c_max, cudaStream_t s) {
-  // one column per CTA with the pattern in registers when it fits
-  if (cs == 1 && a.max_deg > 0 && a.max_deg <= 16 && max_nb <= 4 * kThreads && !g_disable_cg1) {
-    const int mr = (max_nb + kThreads - 1) / kThreads;
-    if (a.max_deg <= 8)
-      return mr <= 1 ? launch_cg1_t<T, 1, 8>(mv, V, Y, a, max_nb, c_max, s)
-                     : launch_cg1_t<T, 4, 8>(mv, V, Y, a, max_nb, c_max, s);
-    return mr <= 1 ? launch_cg1_t<T, 1, 16>(mv, V, Y, a, max_nb, c_max, s)
-                   : launch_cg1_t<T, 4, 16>(mv, V, Y, a, max_nb, c_max, s);
+  // one column per CTA when the pattern fits its ELL forms
+  if (cs == 1 && cg1_fits(max_nb, a.max_deg, sizeof(T), mv.wt != nullptr) && !g_disable_cg1) {
+    prof_begin(KC_CG, s);
+    const int rc = launch_cg1_rows<T>(mv, V, Y, a, max_nb, c_max, s);
+    prof_end(KC_CG, s);
+    return rc;
   }
   switch (cs) {
     case 1: return launch_cg_cs<T, 1>(mv, V, Y, a, max_nb, c_max, s);
@@ -608,6 +738,10 @@ template int launch_cg<float>(const MeshView<float>&, const float*, float*, cons
                               int, int, cudaStream_t);
 template int launch_cg<double>(const MeshView<double>&, const double*, double*, const CgArgs&,
                                int, int, int, cudaStream_t);
+template int launch_cg_buckets<float>(const MeshView<float>&, const float*, float*,
+                                      const CgArgs&, const int*, const int*, int, cudaStream_t);
+template int launch_cg_buckets<double>(const MeshView<double>&, const double*, double*,
+                                       const CgArgs&, const int*, const int*, int, cudaStream_t);
 template void launch_spmm<float>(int64_t, const MeshView<float>&, const int32_t*, float,
                                  const float*, float*, int, cudaStream_t);
 template void launch_spmm<double>(int64_t, const MeshView<double>&, const int32_t*, double,

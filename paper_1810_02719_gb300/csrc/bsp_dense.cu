@@ -459,7 +459,7 @@ void configure_dense_kernels() {
 }
 
 // One Onorm: G1 = Y^T Y (TA), Cholesky (TA), Q1 = Y R1^-1 fused with G2 = Q1^T Q1
-// (T), Cholesky (T), Q = Q1 R2^-1.  Q may alias Y.
+// (TA), Cholesky (TA), Q = Q1 R2^-1.  Q may alias Y.
 template <typename T, typename TA>
 int launch_cholqr2(const DenseArgs& a, const T* Y, T* Q, TA* Gp, T* Rsm, cudaStream_t s,
                    int* launches, int passes) {
@@ -476,8 +476,6 @@ int launch_cholqr2(const DenseArgs& a, const T* Y, T* Q, TA* Gp, T* Rsm, cudaStr
   }
   // partial-Gram area first, reduced Gram after it (both in the Gp workspace)
   TA* G = Gp + (size_t)a.nbatch * maxch * cpad * cpad;
-  T* Gp2raw = reinterpret_cast<T*>(Gp);  // pass 2 partials in T reuse the same area
-  T* G2 = Gp2raw + (size_t)a.nbatch * maxch * cpad * cpad;
   dim3 gp(maxch, a.nbatch);
   const size_t sm_panel = (size_t)CH * cpad * sizeof(T);
   prof_begin(KC_GRAM, s);
@@ -501,16 +499,17 @@ int launch_cholqr2(const DenseArgs& a, const T* Y, T* Q, TA* Gp, T* Rsm, cudaStr
     if (launches) *launches += 4;
     return cudaGetLastError() == cudaSuccess ? BSP_OK : BSP_ERR_CUDA;
   }
+  // pass 2 accumulates and factorises in TA as well: with MIXED precision an
+  // ill-conditioned Y (z >= 2) leaves Q1 far enough from orthonormal that an
+  // FP32 Cholesky of its Gram can break down
   prof_begin(KC_PANEL, s);
-  k_panel_mul<T, T, true, true><<<gp, kDT, sm_mul, s>>>(a, Y, Q, Rsm, CH, maxch, Gp2raw);
+  k_panel_mul<T, TA, true, true><<<gp, kDT, sm_mul, s>>>(a, Y, Q, Rsm, CH, maxch, Gp);
   prof_end(KC_PANEL, s);
   prof_begin(KC_REDUCE, s);
-  k_reduce<T><<<gr, kDT, 0, s>>>(a, CH, maxch, true, Gp2raw, G2);
+  k_reduce<TA><<<gr, kDT, 0, s>>>(a, CH, maxch, true, Gp, G);
   prof_end(KC_REDUCE, s);
-  const size_t sm_chol_b = (size_t)(chol_a_elems<T, T>(cpad, cpw) + 2 * cpad) * sizeof(T) +
-                           (size_t)cpw * cpw * sizeof(T);
   prof_begin(KC_CHOL, s);
-  k_chol<T, T><<<a.nbatch, kDT, sm_chol_b, s>>>(a, G2, Rsm);
+  k_chol<T, TA><<<a.nbatch, kDT, sm_chol_a, s>>>(a, G, Rsm);
   prof_end(KC_CHOL, s);
   prof_begin(KC_PANEL, s);
   k_panel_mul<T, T, true, false><<<gp, kDT, sm_mul, s>>>(a, Q, Q, Rsm, CH, maxch, (T*)nullptr);

@@ -12,6 +12,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <array>
 #include <vector>
 
 #include "../../include/bsp.h"
@@ -27,6 +28,7 @@ enum : int {
   ST_DUP_VERTEX = 1 << 3,     // assembly saw a vertex in two blocks
   ST_DEGREE = 1 << 4,         // a row's neighbour list overflowed
   ST_TIMEOUT = 1 << 5,        // a bounded device wait expired
+  ST_CG_BREAKDOWN = 1 << 6,   // a CG recurrence lost positivity ((p, A p) <= 0)
 };
 
 struct CgStats {
@@ -141,6 +143,14 @@ extern bool g_disable_cg1;  // force the shared-memory CG kernel (A/B checks)
 template <typename T>
 int launch_cg(const MeshView<T>& mv, const T* V, T* Y, const CgArgs& a, int cs, int max_nb,
               int c_max, cudaStream_t s);
+// Batched one-column-per-CTA CG (bsp_cg.cu): the batch sorted by size bucket
+// (rows per thread 1, 4, 8, 16), bucket_off[0..4] (host) delimiting the
+// buckets and bucket_rows[q] the largest block of bucket q.
+int cg_bucket(int nb);   // -1 when the block is too large (> 4,096 rows)
+bool cg1_fits(int max_nb, int max_deg, int real_bytes, bool weighted);
+template <typename T>
+int launch_cg_buckets(const MeshView<T>& mv, const T* V, T* Y, const CgArgs& a,
+                      const int* bucket_off, const int* bucket_rows, int c_max, cudaStream_t s);
 template <typename T>
 int cg_smem_bytes(int cs, int max_nb);
 void configure_cg_kernels();
@@ -241,6 +251,8 @@ struct bsp_mesh {
   std::vector<std::vector<int32_t>> waves;
   std::vector<int32_t> h_wave_list;      // all waves concatenated
   std::vector<int32_t> h_wave_off;       // [levels+1]
+  std::vector<std::array<int, 5>> wave_bucket;  // CG size-bucket offsets per wave
+  std::vector<std::array<int, 4>> wave_bucket_rows;  // largest block per bucket
   int64_t root_rows = 0;
   // device arrays
   int32_t *d_bptr = nullptr, *d_verts = nullptr, *d_rowptr = nullptr, *d_eoff = nullptr,

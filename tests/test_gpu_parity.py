@@ -225,6 +225,68 @@ def test_uneven_blocks_forest_rowtransfer_z2():
         bsp.bsp_mesh_destroy(h)
 
 
+def _wide_wave_mesh(prec, **kw):
+    """96x96 torus cut into ~20 uneven BFS blocks (150-1,400 rows), all roots:
+    one wave of many blocks, which takes the batched CG in three size buckets
+    (1 and 4 rows per thread in registers, 8 in shared memory)."""
+    N = 96
+    xyz, faces = synth.torus(N, seed=2)
+    ptr, verts = synth.bfs_partition(N, target_blocks=24, min_size=150, max_size=1400, seed=11)
+    k = len(ptr) - 1
+    parent = -np.ones(k, np.int32)
+    h = bsp.bsp_mesh_create(xyz, faces, ptr, verts, parent, bsp.make_opts(precision=prec, **kw))
+    om = O.build_mesh(N * N, ptr, verts, parent, faces=faces)
+    sizes = np.diff(ptr)
+    assert sizes.max() > 512 and sizes.min() <= 512 and k >= 12
+    return h, om, xyz, faces, ptr, verts, parent
+
+
+@pytest.mark.parametrize("prec,z,real", [(bsp.BSP_PREC_MIXED, 2, np.float32),
+                                         (bsp.BSP_PREC_F32, 1, np.float32),
+                                         (bsp.BSP_PREC_F64, 1, np.float64)])
+def test_batched_cg_wide_wave(prec, z, real):
+    """Batched blocks of one wave (one-column-per-CTA CG per size bucket, the
+    pattern in registers up to 1,024 rows and in shared memory above): same
+    bases as the oracle."""
+    kw = dict(z=z)
+    if real == np.float64:
+        kw["cg_rtol"] = 1e-13
+    h, om, xyz, faces, ptr, verts, parent = _wide_wave_mesh(prec, **kw)
+    try:
+        c = 24
+        starts = synth.gaussian_starts(ptr, parent, c, seed=3)
+        bsp.bsp_oi_track(h, c, 2, starts.astype(real))
+        U_ref = O.oi_track(om, c, 2, starts, delta=1e-2, z=z)
+        if real == np.float64:
+            compare_bases(h, om, U_ref, xyz, real, SINE_F64, PROJ_F64)
+        else:
+            compare_bases(h, om, U_ref, xyz, real, SINE_F32, PROJ_F32)
+        assert bsp.bsp_get_stats(h)["not_converged"] == 0
+    finally:
+        bsp.bsp_mesh_destroy(h)
+
+
+def test_batched_cg_dynamic_wide_wave():
+    """Dynamic c over one wide wave of uneven blocks (batched CG in every round)."""
+    h, om, xyz, faces, ptr, verts, parent = _wide_wave_mesh(bsp.BSP_PREC_MIXED)
+    try:
+        k = len(ptr) - 1
+        starts = synth.gaussian_starts(ptr, parent, 16, seed=4)
+        kw = dict(tol=1e-2, c_min=16, c_max=64, c_step=8, t_max=3, delta=1e-2, seed=9)
+        Ur, cr, sens = oracle_perturbation_sines(om, xyz, starts, **kw)
+        cg = np.empty(k, np.int32)
+        assert len(set(cr.tolist())) > 3
+        bsp.bsp_oi_track_dynamic(h, xyz.astype(np.float32), 1e-2, 16, 64, 8, 3, 9,
+                                 starts.astype(np.float32), None, cg)
+        assert np.array_equal(cg, cr), (cg, cr)
+        for b, blk in enumerate(om.blocks):
+            U = bsp.bsp_get_basis(h, b, blk.verts.size, np.float32).astype(np.float64)
+            assert O.max_sine(U, Ur[b]) <= max(SINE_F32, 10 * sens[b])
+            assert O.projector_rel_error(U, Ur[b], xyz[blk.verts]) <= PROJ_F32
+    finally:
+        bsp.bsp_mesh_destroy(h)
+
+
 def test_full_width_reconstructs_and_c1_gives_centroid():
     N = 16
     xyz, faces = synth.grid_heightfield(N, seed=7)
