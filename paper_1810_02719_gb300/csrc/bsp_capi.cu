@@ -136,6 +136,7 @@ void configure_once() {
     configure_dense_kernels();
     configure_adjoint_kernels();
     configure_tc_kernels();
+    configure_spmm_kernels();
   });
 }
 
@@ -178,7 +179,8 @@ void release(bsp_mesh* m) {
                   m->d_wt, m->d_diag, m->d_status, m->d_cgstats, m->d_U, m->d_Y, m->d_starts,
                   m->d_Gp, m->d_Rsm, m->d_theta, m->d_action, m->d_round, m->d_forced,
                   m->d_gcol, m->d_rho, m->d_X, m->d_Gp_rr, m->d_Rsm_rr, m->d_ckV, m->d_ckY,
-                  m->d_adj_gp, m->d_adj_thin, m->d_adj_rows, m->d_Ubf, m->d_Ebf};
+                  m->d_adj_gp, m->d_adj_thin, m->d_adj_rows, m->d_Ubf, m->d_Ebf,
+                  m->d_spmm_chunks};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (m->graph_exec) cudaGraphExecDestroy(m->graph_exec);
@@ -1293,13 +1295,47 @@ int bsp_spmm(bsp_mesh* M, const void* P, void* Y, int32_t c, void* stream) {
   if (!is_device_ptr(P) || !is_device_ptr(Y))
     return fail(BSP_ERR_INVALID_ARG, "bsp_spmm takes device pointers");
   cudaStream_t s = (cudaStream_t)stream;
+  if (!M->d_spmm_chunks) {
+    // chunk table, once per mesh: rows on the host, neighbour ranges on the device
+    std::vector<int32_t> ch = spmm_chunk_rows(M->h_bptr);
+    const int nch = (int)(ch.size() / 4);
+    void* d = nullptr;
+    if (cudaMalloc(&d, sizeof(int32_t) * (ch.empty() ? 4 : ch.size())) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(BSP_ERR_OOM, "device allocation failed");
+    }
+    CU(cudaMemcpy(d, ch.data(), sizeof(int32_t) * ch.size(), cudaMemcpyHostToDevice));
+    launch_spmm_ranges(view<float>(M), M->d_blk_row, (int32_t*)d, nch, 0);
+    CU(cudaMemcpy(ch.data(), d, sizeof(int32_t) * ch.size(), cudaMemcpyDeviceToHost));
+    int span = 0, mnnz = 0;
+    std::vector<int32_t> rp(M->n + 1);
+    CU(cudaMemcpy(rp.data(), M->d_rowptr, sizeof(int32_t) * (M->n + 1), cudaMemcpyDeviceToHost));
+    for (int q = 0; q < nch; ++q) {
+      span = std::max(span, ch[4 * q + 3] - ch[4 * q + 2] + 1);
+      mnnz = std::max(mnnz, rp[ch[4 * q] + ch[4 * q + 1]] - rp[ch[4 * q]]);
+    }
+    M->d_spmm_chunks = (int32_t*)d;
+    M->spmm_nchunks = nch;
+    M->spmm_max_span = span;
+    M->spmm_max_nnz = mnnz;
+  }
   ProfScope ps(M);
-  if (M->real_bytes == 8)
-    launch_spmm<double>(M->n, view<double>(M), M->d_blk_row, M->opts.delta, (const double*)P,
-                        (double*)Y, c, s);
-  else
-    launch_spmm<float>(M->n, view<float>(M), M->d_blk_row, (float)M->opts.delta, (const float*)P,
-                       (float*)Y, c, s);
+  int rc;
+  if (M->real_bytes == 8) {
+    rc = launch_spmm_tiled<double>(view<double>(M), M->d_blk_row, M->d_spmm_chunks, M->spmm_nchunks,
+                                   M->spmm_max_span, M->spmm_max_nnz, M->opts.delta, (const double*)P, (double*)Y,
+                                   c, s);
+    if (rc == BSP_ERR_INVALID_ARG)
+      launch_spmm<double>(M->n, view<double>(M), M->d_blk_row, M->opts.delta, (const double*)P,
+                          (double*)Y, c, s);
+  } else {
+    rc = launch_spmm_tiled<float>(view<float>(M), M->d_blk_row, M->d_spmm_chunks, M->spmm_nchunks,
+                                  M->spmm_max_span, M->spmm_max_nnz, (float)M->opts.delta, (const float*)P,
+                                  (float*)Y, c, s);
+    if (rc == BSP_ERR_INVALID_ARG)
+      launch_spmm<float>(M->n, view<float>(M), M->d_blk_row, (float)M->opts.delta, (const float*)P,
+                         (float*)Y, c, s);
+  }
   CU(cudaGetLastError());
   M->stats.gpu_launches = 1;
   return BSP_OK;

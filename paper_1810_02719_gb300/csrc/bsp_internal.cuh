@@ -202,6 +202,17 @@ int launch_recon_tc(const ProjArgs& a, const void* Ub, const float* E, int64_t e
                     float* X, int* status, cudaStream_t s);
 void configure_tc_kernels();
 
+// Tiled operator product (bsp_spmm.cu): chunks of up to 128 rows inside a
+// block, each with the row range [lo, hi] that its neighbours reach.
+void configure_spmm_kernels();
+std::vector<int32_t> spmm_chunk_rows(const std::vector<int32_t>& bptr);
+void launch_spmm_ranges(const MeshView<float>& mv_any, const int32_t* blk_row, int32_t* chunks,
+                        int nchunks, cudaStream_t s);
+template <typename T>
+int launch_spmm_tiled(const MeshView<T>& mv, const int32_t* blk_row, const int32_t* chunks,
+                      int nchunks, int max_span, int max_nnz, T delta, const T* P, T* Y, int c,
+                      cudaStream_t s);
+
 // Start matrices and dynamic-c helpers (bsp_dyn.cu)
 template <typename T>
 void launch_init_starts(const int32_t* batch, int nbatch, const int32_t* bptr,
@@ -284,6 +295,8 @@ struct bsp_mesh {
   void* d_Ubf = nullptr;
   size_t cap_Ubf = 0;
   bool ubf_valid = false;
+  int32_t* d_spmm_chunks = nullptr;   // tiled operator product: 4 int32 per chunk
+  int spmm_nchunks = 0, spmm_max_span = 0, spmm_max_nnz = 0;
   void* d_Ebf = nullptr;   // BF16 copy of the coefficients of a reconstruction call
   size_t cap_Ebf = 0;
   // Rayleigh-Ritz side branches: kSide streams used round-robin, each with its

@@ -119,7 +119,8 @@ def test_edge_list_graphs_path_cycle():
 # ---------------------------------------------------------------- operator
 
 @pytest.mark.parametrize("prec,c", [(bsp.BSP_PREC_MIXED, 64), (bsp.BSP_PREC_MIXED, 12),
-                                    (bsp.BSP_PREC_F64, 16), (bsp.BSP_PREC_MIXED, 7)])
+                                    (bsp.BSP_PREC_F64, 16), (bsp.BSP_PREC_MIXED, 7),
+                                    (bsp.BSP_PREC_MIXED, 48), (bsp.BSP_PREC_F64, 44)])
 def test_spmm_matches_dense_operator(prec, c):
     h, om, *_ = make_tile_mesh(64, 32, kind="torus", prec=prec)
     real = np.float64 if prec == bsp.BSP_PREC_F64 else np.float32
@@ -138,6 +139,38 @@ def test_spmm_matches_dense_operator(prec, c):
             ref = A @ P[rows].astype(real).astype(np.float64)
             err = np.abs(Y[rows] - ref).max() / np.abs(ref).max()
             assert err <= (1e-12 if real == np.float64 else 2e-6), err
+    finally:
+        bsp.bsp_mesh_destroy(h)
+
+
+@pytest.mark.parametrize("mode,c", [(bsp.BSP_W_COMBINATORIAL, 32), (bsp.BSP_W_INV_SQ_DIST, 48)])
+def test_spmm_uneven_blocks_and_weights(mode, c):
+    """Tiled operator product on uneven BFS blocks (chunks of different sizes and
+    halos, a ragged last chunk per block), with and without edge weights."""
+    N = 72
+    xyz, faces = synth.torus(N, seed=6)
+    ptr, verts = synth.bfs_partition(N, target_blocks=14, min_size=100, max_size=900, seed=2)
+    k = len(ptr) - 1
+    parent = -np.ones(k, np.int32)
+    h = bsp.bsp_mesh_create(xyz, faces, ptr, verts, parent,
+                            bsp.make_opts(precision=bsp.BSP_PREC_MIXED, weight_mode=mode))
+    om = O.build_mesh(N * N, ptr, verts, parent, faces=faces, xyz=xyz,
+                      weight_mode={0: O.WEIGHT_COMBINATORIAL, 2: O.WEIGHT_INV_SQ_DIST}[mode])
+    try:
+        rng = np.random.default_rng(1)
+        P = rng.standard_normal((N * N, c))
+        Pd = torch.tensor(P, dtype=torch.float32, device="cuda")
+        Yd = torch.full_like(Pd, float("nan"))
+        bsp.bsp_spmm(h, Pd, Yd, c)
+        torch.cuda.synchronize()
+        Y = Yd.cpu().double().numpy()
+        assert np.isfinite(Y).all()
+        for b, blk in enumerate(om.blocks):
+            rows = slice(ptr[b], ptr[b + 1])
+            A = O.laplacian(blk) + 1e-2 * np.eye(blk.verts.size)
+            ref = A @ P[rows].astype(np.float32).astype(np.float64)
+            err = np.abs(Y[rows] - ref).max() / np.abs(ref).max()
+            assert err <= 2e-6, err
     finally:
         bsp.bsp_mesh_destroy(h)
 
