@@ -397,12 +397,16 @@ def oi_dynamic_block(L, X, V0, delta, z, t_max, tol, c_min, c_max, c_step, seed,
 
 def oi_track_dynamic(mesh: Mesh, X: np.ndarray, starts: np.ndarray, tol: float = 2e-3,
                      c_min: int = 8, c_max: int = 128, c_step: int = 8, t_max: int = 2,
-                     delta: float = 1e-2, z: int = 1, seed: int = 0, forced_c=None):
+                     delta: float = 1e-2, z: int = 1, seed: int = 0, forced_c=None,
+                     block_ids=None):
     """Dynamic OI over all blocks in topological order (Sec. 5, Alg. 2).
 
     Roots start at width c_min from their rows of ``starts`` (first c_min
     columns); a child starts at its parent's width c_parent (>= c_min) from the
     parent's basis (Alg. 2, second line).  X: n x 3 coordinates.
+    ``block_ids``: the index of every block of ``mesh`` in a larger mesh it was
+    cut from, which keys the counter hash of the growth columns (default: its
+    position here).
     Returns (U list, c array, met array, rho array).
     """
     k = mesh.k
@@ -428,7 +432,8 @@ def oi_track_dynamic(mesh: Mesh, X: np.ndarray, starts: np.ndarray, tol: float =
         fc = -1 if forced_c is None else int(forced_c[b])
         U[b], cs[b], met[b], _, rhos[b] = oi_dynamic_block(
             L, X[blk.verts], V0, delta, z, t_max, tol, c_min,
-            min(c_max, (n_b // c_step) * c_step), c_step, seed, b, fc)
+            min(c_max, (n_b // c_step) * c_step), c_step, seed,
+            b if block_ids is None else int(block_ids[b]), fc)
     return U, cs, met, rhos
 
 

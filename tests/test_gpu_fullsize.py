@@ -1,0 +1,223 @@
+"""Parity at the benchmark's full sizes, in the launch configuration bench.py times.
+
+The oracle computes what it can one block at a time: the whole warm-start
+chain of the 1M-vertex torus (sampled blocks compared), root blocks of the BFS
+forest on their own, the first blocks of the frames and filter workloads.
+Everything else is checked through properties that hold at any size
+(orthonormal bases, the dynamic-c choice is the smallest passing width, the
+projection equals its definition on the returned basis).
+"""
+import numpy as np
+import pytest
+
+from oracle import bsp_oracle as O
+from paper_1810_02719_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1810_02719_gb300 import bsp  # noqa: E402
+from paper_1810_02719_gb300.filter import block_low_pass  # noqa: E402
+
+SINE_F32, PROJ_F32 = 1e-4, 1e-5
+# FP32 orthonormality after CholeskyQR2 and the Rayleigh-Ritz rotation: the
+# loss grows like n u (u = 2^-24, n up to ~3,000 rows); observed ~1e-5
+ORTH_F32 = 1e-4
+
+
+def _orthonormality(U):
+    return float(np.abs(U.T @ U - np.eye(U.shape[1])).max())
+
+
+def _oracle_dynamic_with_sensitivity(mesh, X, starts, **kw):
+    """The oracle's Algorithm 2, and how far its projector moves when every solve
+    is perturbed by 1e-6 (relative): unconverged directions of a few OI steps
+    from a random start respond strongly, and only that much agreement can be
+    asked of an FP32 solve."""
+    U0, c0, *_ = O.oi_track_dynamic(mesh, X, starts, **kw)
+    orig = O.apply_S
+    rng = np.random.default_rng(0)
+
+    def noisy(L, V, delta, z):
+        Y = orig(L, V, delta, z)
+        return Y + 1e-6 * np.linalg.norm(Y, axis=0) * rng.standard_normal(Y.shape) / np.sqrt(Y.shape[0])
+
+    O.apply_S = noisy
+    try:
+        U1, c1, *_ = O.oi_track_dynamic(mesh, X, starts, **kw)
+    finally:
+        O.apply_S = orig
+    return U0, c0, c1, U1
+
+
+def test_chain_1m_torus_c64():
+    """1024^2 torus, 1,024 chained 32x32 blocks, c = 64, 2 OI steps, RR, FP32, CUDA graph."""
+    N, T, c, t = 1024, 32, 64, 2
+    xyz, faces = synth.torus(N, seed=0)
+    ptr, verts = synth.tile_partition(N, T)
+    k = len(ptr) - 1
+    parent = synth.raster_chain(k)
+    starts = synth.gaussian_starts(ptr, parent, c, seed=0)
+    h = bsp.bsp_mesh_create(xyz, faces, ptr, verts, parent, bsp.make_opts(precision=bsp.BSP_PREC_F32))
+    try:
+        bsp.bsp_oi_track(h, c, t, torch.tensor(starts, dtype=torch.float32, device="cuda"))
+        X = torch.tensor(xyz, dtype=torch.float32, device="cuda")
+        E = torch.empty(k * c, 3, dtype=torch.float32, device="cuda")
+        Xo = torch.empty_like(X)
+        bsp.bsp_project(h, X, bsp.BSP_DT_F32, 3, E)
+        bsp.bsp_reconstruct(h, E, 3, Xo)
+        torch.cuda.synchronize()
+        Xon = Xo.cpu().double().numpy()
+        om = O.build_mesh(N * N, ptr, verts, parent, faces=faces)
+        U_ref = O.oi_track(om, c, t, starts, delta=1e-2)
+        for b in range(k):
+            U = bsp.bsp_get_basis(h, b, 1024).astype(np.float64)
+            assert _orthonormality(U) <= ORTH_F32, b
+            if b in (0, 1, 2, 255, 511, 767, 1022, 1023):
+                rows = om.blocks[b].verts
+                assert O.max_sine(U, U_ref[b]) <= SINE_F32, b
+                assert O.projector_rel_error(U, U_ref[b], xyz[rows]) <= PROJ_F32, b
+                ref = U_ref[b] @ (U_ref[b].T @ xyz[rows])
+                assert np.linalg.norm(Xon[rows] - ref) / np.linalg.norm(ref) <= PROJ_F32, b
+    finally:
+        bsp.bsp_mesh_destroy(h)
+
+
+def test_batched_bfs_dynamic_c():
+    """1024^2 torus, ~2,000 BFS blocks of 300-3,000 v, 32-root forest, dynamic c 8..128
+    to relative error 2e-3, MIXED precision (the batched configuration)."""
+    N, tol = 1024, 2e-3
+    xyz, faces = synth.torus(N, seed=0)
+    ptr, verts = synth.bfs_partition(N, target_blocks=6000, min_size=300, max_size=3000, seed=0)
+    ptr, verts, parent = synth.block_forest(ptr, verts, N, roots=32, seed=1)
+    k = len(ptr) - 1
+    starts = synth.gaussian_starts(ptr, parent, 8, seed=0)
+    h = bsp.bsp_mesh_create(xyz, faces, ptr, verts, parent, bsp.make_opts(precision=bsp.BSP_PREC_MIXED))
+    try:
+        cb = np.empty(k, np.int32)
+        X = torch.tensor(xyz, dtype=torch.float32, device="cuda")
+        bsp.bsp_oi_track_dynamic(h, X, tol, 8, 128, 8, 2, 7,
+                                 torch.tensor(starts, dtype=torch.float32, device="cuda"), None, cb)
+        assert np.all(cb % 8 == 0) and cb.min() >= 8 and cb.max() <= 128
+        for b in range(k):
+            rows = verts[ptr[b]:ptr[b + 1]]
+            U = bsp.bsp_get_basis(h, b, rows.size).astype(np.float64)
+            assert _orthonormality(U) <= ORTH_F32, b
+            # the chosen width is the smallest multiple of 8 whose Ritz prefix meets
+            # the target (the decision is taken on the same prefix in FP64)
+            Xb = xyz[rows]
+            rho = O.residual_ratios(U, Xb, 8)       # widths 8, 16, ..., c_b
+            j = cb[b] // 8 - 1
+            if cb[b] < 128:
+                assert rho[j] <= tol * (1 + 1e-5), (b, rho[j])
+            if cb[b] > 8:
+                assert rho[j - 1] > tol * (1 - 1e-5), (b, rho[j - 1])
+        # root blocks on their own against the oracle's Algorithm 2
+        roots = [b for b in range(k) if parent[b] < 0][:4]
+        off = {}
+        o = 0
+        for b in range(k):
+            if parent[b] < 0:
+                off[b] = o
+                o += ptr[b + 1] - ptr[b]
+        for b in roots:
+            rows = verts[ptr[b]:ptr[b + 1]]
+            nb = rows.size
+            om = O.build_mesh(N * N, np.array([0, nb]), rows, np.array([-1]), faces=faces)
+            Ur, cr, cr1, Ur1 = _oracle_dynamic_with_sensitivity(
+                om, xyz, starts[off[b]:off[b] + nb], tol=tol, c_min=8, c_max=128, c_step=8,
+                t_max=2, delta=1e-2, seed=7, block_ids=[b])
+            U = bsp.bsp_get_basis(h, b, nb).astype(np.float64)
+            assert cb[b] == cr[0], (b, cb[b], cr[0])
+            sens = O.projector_rel_error(Ur1[0], Ur[0], xyz[rows]) if cr1[0] == cr[0] else 0.0
+            assert O.projector_rel_error(U, Ur[0], xyz[rows]) <= max(PROJ_F32, 10 * sens), b
+    finally:
+        bsp.bsp_mesh_destroy(h)
+
+
+def test_frames_512_torus_200_frames_tensor_cores():
+    """512^2 torus x 200 frames, 256 blocks, c = 48: tcgen05 projection and reconstruction
+    of all 600 columns at once."""
+    N, T, F, c = 512, 32, 200, 48
+    frames, faces = synth.torus_frames(N, frames=F, seed=0)
+    ptr, verts = synth.tile_partition(N, T)
+    k = len(ptr) - 1
+    parent = synth.raster_chain(k)
+    n, cols = N * N, 3 * F
+    starts = synth.gaussian_starts(ptr, parent, c, seed=0)
+    h = bsp.bsp_mesh_create(frames[0], faces, ptr, verts, parent,
+                            bsp.make_opts(precision=bsp.BSP_PREC_F32))
+    try:
+        bsp.bsp_oi_track(h, c, 2, torch.tensor(starts, dtype=torch.float32, device="cuda"))
+        X64 = frames.transpose(1, 0, 2).reshape(n, cols)
+        Xb = torch.tensor(X64, dtype=torch.float32, device="cuda").to(torch.bfloat16)
+        E = torch.empty(k * c, cols, dtype=torch.float32, device="cuda")
+        Xo = torch.full((n, cols), float("nan"), dtype=torch.float32, device="cuda")
+        bsp.bsp_project(h, Xb, bsp.BSP_DT_BF16, cols, E)
+        bsp.bsp_reconstruct_bf16(h, E, cols, Xo)
+        torch.cuda.synchronize()
+        Xon = Xo.cpu().double().numpy()
+        assert np.isfinite(Xon).all()
+        En = E.cpu().double().numpy()
+        Xq = Xb.to(torch.float64).cpu().numpy()
+        for b in (0, 77, 128, 255):
+            rows = verts[ptr[b]:ptr[b + 1]]
+            U = bsp.bsp_get_basis(h, b, rows.size).astype(np.float64)
+            Uq = torch.tensor(U, dtype=torch.float32).to(torch.bfloat16).double().numpy()
+            Eref = Uq.T @ Xq[rows]
+            assert np.abs(En[b * c:(b + 1) * c] - Eref).max() <= 1e-5 * np.abs(Eref).max(), b
+            Eq = torch.tensor(En[b * c:(b + 1) * c], dtype=torch.float32).to(torch.bfloat16)
+            Xref = Uq @ Eq.double().numpy()
+            assert np.abs(Xon[rows] - Xref).max() <= 1e-5 * np.abs(Xref).max(), b
+        # the first 4 blocks of the chain against the FP64 oracle end to end
+        nb4 = int(ptr[4])
+        om = O.build_mesh(n, ptr[:5], verts[:nb4], parent[:4], faces=faces)
+        U_ref = O.oi_track(om, c, 2, starts, delta=1e-2)
+        num = den = 0.0
+        for b, blk in enumerate(om.blocks):
+            ref = U_ref[b] @ (U_ref[b].T @ X64[blk.verts])
+            num += np.sum((Xon[blk.verts] - ref) ** 2)
+            den += np.sum(ref ** 2)
+        assert np.sqrt(num / den) <= 2e-2
+    finally:
+        bsp.bsp_mesh_destroy(h)
+
+
+def test_filter_512_noisy_torus_gradients():
+    """Differentiable filter at full size (262,144 v, 256 blocks, c = 32, 4 steps, FP32):
+    gradients of the first 4 blocks against the FP64 oracle's autograd."""
+    N, T, c, t = 512, 32, 32, 4
+    clean, noisy, faces = synth.noisy_torus(N, seed=0)
+    ptr, verts = synth.tile_partition(N, T)
+    k = len(ptr) - 1
+    parent = synth.raster_chain(k)
+    n = N * N
+    starts = synth.gaussian_starts(ptr, parent, c, seed=1)
+    h = bsp.bsp_mesh_create(clean, faces, ptr, verts, parent,
+                            bsp.make_opts(precision=bsp.BSP_PREC_F32, weight_mode=bsp.BSP_W_EDGE))
+    try:
+        E = bsp.bsp_get_stats(h)["intra_edges"]
+        rng = np.random.default_rng(3)
+        w0 = 1.0 + 0.25 * rng.random(E)
+        x = torch.tensor(noisy, dtype=torch.float32, device="cuda", requires_grad=True)
+        w = torch.tensor(w0, dtype=torch.float32, device="cuda", requires_grad=True)
+        y = block_low_pass(x, w, h, c, t, torch.tensor(starts, dtype=torch.float32, device="cuda"))
+        loss = ((y - torch.tensor(clean, dtype=torch.float32, device="cuda")) ** 2).sum()
+        loss.backward()
+        gx = x.grad.cpu().double().numpy()
+        gw = w.grad.cpu().double().numpy()
+        assert np.isfinite(gx).all() and np.isfinite(gw).all()
+        nb4 = int(ptr[4])
+        om = O.build_mesh(n, ptr[:5], verts[:nb4], parent[:4], faces=faces, weight_mode=O.WEIGHT_EDGE)
+        E4 = sum(b.edges.shape[0] for b in om.blocks)
+        _, gx_ref, gw_ref, xh_ref = O.filter_loss_grads(om, noisy, clean, w0[:E4], c, t, starts)
+        rows = verts[:nb4]
+        yn = y.detach().cpu().double().numpy()
+        assert np.linalg.norm(yn[rows] - xh_ref[rows]) / np.linalg.norm(xh_ref[rows]) <= 1e-5
+        assert np.linalg.norm(gx[rows] - gx_ref[rows]) / np.linalg.norm(gx_ref[rows]) <= 2e-3
+        assert np.linalg.norm(gw[:E4] - gw_ref) / np.linalg.norm(gw_ref) <= 2e-3
+    finally:
+        bsp.bsp_mesh_destroy(h)
