@@ -262,7 +262,8 @@ def run_ours(args, rank, world, device):
     nnz = prof_stats["nnz"]
     alg_bytes = n * args.c * 4 * 2 + nnz * 2 + (n + 1) * 4 + n * 4 + n * 4
     achieved = alg_bytes / t_spmm / 1e9
-    spmm_roof = {"kernel": "k_spmm_vec (Y = (L + delta I) P, all blocks)", "bound": "hbm",
+    spmm_roof = {"kernel": "k_spmm_tile (Y = (L + delta I) P, all blocks, 64-row chunks staged "
+                           "in shared memory)", "bound": "hbm",
                  "achieved": achieved, "peak": peak_hbm, "peak_source": peak_kind, "unit": "GB/s",
                  "frac": achieved / peak_hbm, "traffic": None, "algorithmic_bytes": alg_bytes,
                  "avg_launch_s": t_spmm}
@@ -605,15 +606,18 @@ def run_frames(args, device):
                      "note": "API calls (each ends with a stream synchronise and a status read)"},
         "kernel_ms": {"k_project_tc": 1e3 * k_pbf, "k_recon_tc": 1e3 * k_rbf},
         "rel_err_vs_fp64_oracle_first4blocks": errs,
+        # traffic: dram__bytes_read.sum + dram__bytes_write.sum of one launch of the
+        # unchanged kernels (profiles/ncu_full_project_recon_tc_frames512x200_c48.md)
         "roofline": {"kernel": "k_project_tc (tcgen05, BF16 X, all frames)", "bound": "hbm",
                      "achieved": bytes_pbf / k_pbf / 1e9, "peak": peak_hbm, "unit": "GB/s",
                      "peak_source": peak_kind, "frac": bytes_pbf / k_pbf / 1e9 / peak_hbm,
-                     "traffic": None, "algorithmic_bytes": bytes_pbf, "avg_launch_s": k_pbf,
+                     "traffic": 364.9e6, "algorithmic_bytes": bytes_pbf, "avg_launch_s": k_pbf,
                      "tensor_tflops": flops / k_pbf / 1e12},
         "roofline_reconstruct": {"kernel": "k_recon_tc", "bound": "hbm",
                                  "achieved": bytes_rbf / k_rbf / 1e9, "peak": peak_hbm,
                                  "unit": "GB/s", "frac": bytes_rbf / k_rbf / 1e9 / peak_hbm,
                                  "algorithmic_bytes": bytes_rbf, "avg_launch_s": k_rbf,
+                                 "traffic": 612.4e6,
                                  "tensor_tflops": flops / k_rbf / 1e12},
     }
 
