@@ -504,6 +504,51 @@ def run_filter(args, device):
     }
 
 
+def run_spmm(args, device):
+    """The operator product Y = (L + delta I) P on its own (the sparse x
+    tall-skinny product inside every solve): the 1024x1024 torus, 1,024 blocks
+    of 32x32, for c = 64 (the chain's width), 48 and 32; CUDA events around
+    every launch, a 512 MB write between launches flushes L2."""
+    import torch
+    from paper_1810_02719_gb300 import bsp
+    xyz, faces, ptr, verts, parent, _ = workload(args)
+    n = xyz.shape[0]
+    h = bsp.bsp_mesh_create(xyz, faces, ptr, verts, parent, bsp.make_opts(precision=bsp.BSP_PREC_F32))
+    nnz = bsp.bsp_get_stats(h)["nnz"]
+    stream = torch.cuda.current_stream(device)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
+    peak, kind = peaks()
+    out = {}
+    for c in (args.c, 48, 32):
+        P = torch.randn(n, c, device=device)
+        Y = torch.empty_like(P)
+        for _ in range(args.warmup):
+            bsp.bsp_spmm(h, P, Y, c, stream)
+        ts = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            bsp.bsp_spmm(h, P, Y, c, stream)
+            a1.record(stream)
+            a1.synchronize()
+            ts.append(a0.elapsed_time(a1) / 1e3)
+        t = statistics.mean(ts)
+        b = n * c * 4 * 2 + nnz * 2 + (n + 1) * 4 + n * 4 + n * 4
+        out[f"c{c}"] = {"us": 1e6 * t, "algorithmic_bytes": b, "GB/s": b / t / 1e9,
+                        "frac": b / t / 1e9 / peak}
+    bsp.bsp_mesh_destroy(h)
+    first = out[f"c{args.c}"]
+    return {"value": n / (first["us"] * 1e-6) / 1e6, "unit": "Mvertices/s",
+            "ms_per_step": first["us"] * 1e-3,
+            "roofline": {"kernel": "k_spmm_tile", "bound": "hbm", "achieved": first["GB/s"],
+                         "peak": peak, "peak_source": kind, "unit": "GB/s", "frac": first["frac"],
+                         "traffic": None, "algorithmic_bytes": first["algorithmic_bytes"],
+                         "avg_launch_s": first["us"] * 1e-6},
+            "by_width": out}
+
+
 def run_frames(args, device):
     """Dynamic mesh: 512x512 torus (262,144 v), 200 frames, 256 blocks of 32x32, c=48.
 
@@ -637,11 +682,13 @@ def main():
     ap.add_argument("--eig-blocks", type=int, default=64,
                     help="blocks timed for the per-block dense eigensolver baseline")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--config", default="chain", choices=["chain", "frames", "batched", "filter"],
+    ap.add_argument("--config", default="chain",
+                    choices=["chain", "frames", "batched", "filter", "spmm"],
                     help="chain: 1M-vertex torus, 1,024 chained blocks (default); "
                          "frames: 262K-vertex torus, 200 frames projected at once; "
                          "batched: 1M-vertex torus, ~2,000 uneven BFS blocks, dynamic c; "
-                         "filter: 262K-vertex noisy torus, differentiable low-pass forward+backward")
+                         "filter: 262K-vertex noisy torus, differentiable low-pass forward+backward; "
+                         "spmm: the operator product alone on the 1M-vertex torus")
     ap.add_argument("--roots", type=int, default=32, help="roots of the BFS warm-start forest")
     args = ap.parse_args()
 
@@ -695,6 +742,19 @@ def main():
                     "config": {"workload": "torus 512x512 (262144 v) x 200 frames, 256 blocks "
                                            "of 32x32, c=48, 2 OI steps on frame 0, project + "
                                            "reconstruct all frames", "l2": "flushed"}}
+            line.update(res)
+            print(json.dumps(line))
+        return
+    if args.config == "spmm":
+        res = run_spmm(args, device)
+        if rank == 0:
+            line = {"metric": METRIC, "impl": "ours", "n_gpus": world, "steps": args.steps,
+                    "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+                    "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                    "config": {"workload": f"operator product (L + delta I) P, torus "
+                                           f"{args.grid}x{args.grid}, blocks of {args.tile}x"
+                                           f"{args.tile}, c={args.c} (also 48, 32)",
+                               "l2": "flushed between timed launches (512 MB write)"}}
             line.update(res)
             print(json.dumps(line))
         return

@@ -528,19 +528,35 @@ int enqueue_fixed(bsp_mesh* M, int c, int t_max, cudaStream_t s, int* launches) 
               M->opts.cg_max_steps, M->d_status, M->d_cgstats, M->max_deg};
     const int cs = pick_cs(M, nbw, c, sizeof(T));
     const bool buckets = use_buckets(M, nbw, wmax);
+    // Onorm placement.  Only the span matters between steps (span(S Q) =
+    // span(S Y) for Q = Onorm(Y)), so Onorm is there to keep the next solve's
+    // input well conditioned.  A random (root) or row-transferred start needs
+    // it after every solve; a warm start from a same-size parent is close to
+    // the block's eigenbasis, which S maps to nearly orthogonal columns, so
+    // two solves can share one Onorm (S^2 V0 stays far inside what
+    // CholeskyQR2 handles).  Intermediate Onorms take one Cholesky-QR pass,
+    // the last one the full CholeskyQR2.
     const int sub = t_max * M->opts.z;
+    const bool warm = need.empty();
+    T* cur = U;
+    T* out = Y;
     for (int t = 0; t < sub; ++t) {
-      rc = buckets ? launch_cg_buckets<T>(mv, U, Y, ca, M->wave_bucket[l].data(),
+      rc = buckets ? launch_cg_buckets<T>(mv, cur, out, ca, M->wave_bucket[l].data(),
                                           M->wave_bucket_rows[l].data(), c, s)
-                   : launch_cg<T>(mv, U, Y, ca, cs, wmax, c, s);
+                   : launch_cg<T>(mv, cur, out, ca, cs, wmax, c, s);
       if (rc) return fail(rc, "CG launch failed (block too large for shared memory?)");
       ++*launches;
-      // Intermediate steps only need a well-conditioned basis for the next
-      // solve (span(S Q) = span(S Y)): one Cholesky-QR pass; the last step
-      // orthonormalises to working precision with CholeskyQR2.
-      const int passes = (t + 1 < sub) ? 1 : 2;
-      if ((rc = launch_cholqr2<T, TA>(da, Y, U, (TA*)M->d_Gp, (T*)M->d_Rsm, s, launches, passes)))
+      const bool last = t + 1 == sub;
+      if (warm && !last && (t % 2) == 0) {   // next solve reads this one's output
+        cur = out;
+        out = (out == Y) ? U : Y;
+        continue;
+      }
+      const int passes = last ? 2 : 1;
+      if ((rc = launch_cholqr2<T, TA>(da, out, U, (TA*)M->d_Gp, (T*)M->d_Rsm, s, launches, passes)))
         return fail(rc, "launch failed (Onorm)");
+      cur = U;
+      out = Y;
     }
   }
   if (M->opts.rayleigh_ritz && levels > 0) {
