@@ -533,30 +533,25 @@ int enqueue_fixed(bsp_mesh* M, int c, int t_max, cudaStream_t s, int* launches) 
     // input well conditioned.  A random (root) or row-transferred start needs
     // it after every solve; a warm start from a same-size parent is close to
     // the block's eigenbasis, which S maps to nearly orthogonal columns, so
-    // two solves can share one Onorm (S^2 V0 stays far inside what
-    // CholeskyQR2 handles).  Intermediate Onorms take one Cholesky-QR pass,
-    // the last one the full CholeskyQR2.
+    // two solves share one Onorm (S^2 V0 stays far inside what CholeskyQR2
+    // handles).  Solves between two Onorms run in one CG launch (every column
+    // goes straight on to its next solve).  Intermediate Onorms take one
+    // Cholesky-QR pass, the last one the full CholeskyQR2.
     const int sub = t_max * M->opts.z;
     const bool warm = need.empty();
-    T* cur = U;
-    T* out = Y;
-    for (int t = 0; t < sub; ++t) {
-      rc = buckets ? launch_cg_buckets<T>(mv, cur, out, ca, M->wave_bucket[l].data(),
+    for (int t = 0; t < sub;) {
+      const int g = (warm && t + 1 < sub) ? 2 : 1;   // solves before the next Onorm
+      CgArgs cg = ca;
+      cg.z = g;
+      rc = buckets ? launch_cg_buckets<T>(mv, U, Y, cg, M->wave_bucket[l].data(),
                                           M->wave_bucket_rows[l].data(), c, s)
-                   : launch_cg<T>(mv, cur, out, ca, cs, wmax, c, s);
+                   : launch_cg<T>(mv, U, Y, cg, cs, wmax, c, s);
       if (rc) return fail(rc, "CG launch failed (block too large for shared memory?)");
       ++*launches;
-      const bool last = t + 1 == sub;
-      if (warm && !last && (t % 2) == 0) {   // next solve reads this one's output
-        cur = out;
-        out = (out == Y) ? U : Y;
-        continue;
-      }
-      const int passes = last ? 2 : 1;
-      if ((rc = launch_cholqr2<T, TA>(da, out, U, (TA*)M->d_Gp, (T*)M->d_Rsm, s, launches, passes)))
+      t += g;
+      const int passes = t == sub ? 2 : 1;
+      if ((rc = launch_cholqr2<T, TA>(da, Y, U, (TA*)M->d_Gp, (T*)M->d_Rsm, s, launches, passes)))
         return fail(rc, "launch failed (Onorm)");
-      cur = U;
-      out = Y;
     }
   }
   if (M->opts.rayleigh_ritz && levels > 0) {
