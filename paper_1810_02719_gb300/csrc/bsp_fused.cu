@@ -16,28 +16,86 @@ namespace {
 using namespace dev;
 
 // Scratch next to the panel: the Gram half-sums (cpad^2) and the Cholesky's
-// double-buffered row (2 (CP + 4)); a multiple of 4 keeps the following
-// arrays aligned.
+// double-buffered block rows (8 (CP + 4)); a multiple of 4 keeps the
+// following arrays aligned.
 __host__ __device__ inline int fused_half_elems(int cpad, int cp) {
-  const int a = cpad * cpad, b = 2 * cp + 8;
+  const int a = cpad * cpad, b = 8 * (cp + 4);
   return ((a > b ? a : b) + 3) & ~3;
 }
 
-// Cholesky of the Jacobi-scaled Gram in FP32 by CP threads (CP/32 warps):
-// thread j keeps column j of the symmetric A in registers.  The step loop is
-// unrolled, so every register index is a constant.  Step k publishes row k
-// (a_kj from thread j) in a double-buffered shared row, one named barrier
-// over the CP threads; then every thread forms r_kj = a_kj / sqrt(a_kk) and
-// applies the symmetric update a_ij -= a_ki a_kj / a_kk (i > k).  Entries
-// below the diagonal of column j turn to rounding-level values once step j
-// has passed; they are never read back (row k's readers only read entries
-// k..CP-1 of threads >= k) and never written out.  Rows/columns >= c act as
-// the identity.  Writes R (upper, stride CP) to Rr and 1/R_jj to rinv.
-// Called by threads 0..CP-1 only; lbuf holds 2 (CP + 4) floats, 16-byte
-// aligned.
+// One block step of chol_cols (rows KB..KB+3).  A template recursion over
+// KB keeps every register index a compile-time constant (an unrolled loop
+// of this size is not unrolled fully, and the column would go to local memory).
+template <int CP, int KB>
+BSP_DEV void chol_step(float (&a)[CP], int c, int j, float* lbuf, bool& bad) {
+  constexpr int B = 4;
+  constexpr int LD = CP + 4;
+  if (KB < c) {   // uniform over the CP threads
+    float* buf = lbuf + ((KB / B) & 1) * (B * LD);
+#pragma unroll
+    for (int q = 0; q < B; ++q) buf[q * LD + j] = a[KB + q];
+    asm volatile("bar.sync 1, %0;" ::"r"(CP) : "memory");
+    float r4[B][B], inv[B];
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+      float sq = buf[q * LD + KB + q];
+#pragma unroll
+      for (int p = 0; p < q; ++p) sq -= r4[p][q] * r4[p][q];
+      const bool ok = sq > 0.f && isfinite(sq);
+      bad = bad || !ok;
+      inv[q] = ok ? rsqrtf(sq) : 1.f;
+      r4[q][q] = ok ? sq * inv[q] : 1.f;
+#pragma unroll
+      for (int r = q + 1; r < B; ++r) {
+        float t = buf[q * LD + KB + r];
+#pragma unroll
+        for (int p = 0; p < q; ++p) t -= r4[p][q] * r4[p][r];
+        r4[q][r] = t * inv[q];
+      }
+    }
+    float l[B], w[B];
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+      float t = a[KB + q];
+#pragma unroll
+      for (int p = 0; p < q; ++p) t -= r4[p][q] * l[p];
+      l[q] = t * inv[q];
+    }
+#pragma unroll
+    for (int q = B - 1; q >= 0; --q) {
+      float t = l[q];
+#pragma unroll
+      for (int p = q + 1; p < B; ++p) t -= r4[q][p] * w[p];
+      w[q] = t * inv[q];
+    }
+#pragma unroll
+    for (int q = 0; q < B; ++q) a[KB + q] = l[q];
+#pragma unroll
+    for (int i = KB + B; i < CP; ++i) {
+      float t = a[i];
+#pragma unroll
+      for (int q = 0; q < B; ++q) t -= buf[q * LD + i] * w[q];
+      a[i] = t;
+    }
+  }
+  if constexpr (KB + 4 < CP) chol_step<CP, KB + 4>(a, c, j, lbuf, bad);
+}
+// Cholesky of the Jacobi-scaled Gram in FP32 by CP threads (CP/32 warps),
+// blocked by 4: thread j keeps column j of the symmetric A in registers.
+// Block step kb publishes rows kb..kb+3 (a_{kb+q, j} from thread j) in a
+// double-buffered shared area, one named barrier over the CP threads; then
+// every thread factorises the 4 x 4 pivot block D = R4^T R4 itself, forms its
+// entries of R's rows kb..kb+3, l = R4^-T p_j (p_j its published values), and
+// applies the Schur update a_ij -= p_i^T D^-1 p_j = sum_q p_i[q] w_j[q] with
+// w_j = D^-1 p_j (i >= kb + 4).  Entries below the diagonal of column j are
+// never read back or written out.  Rows/columns >= c act as the identity.
+// Writes R (upper, stride CP) to Rr and 1/R_jj to rinv.  Called by threads
+// 0..CP-1 only; lbuf holds 8 (CP + 4) floats.
 template <typename TG, int CP>
 BSP_DEV void chol_cols(const TG* g, int c, int cpad, const float* dsc, float* Rr, float* rinv,
                        float* lbuf, int* fail) {
+  constexpr int B = 4;
+  constexpr int LD = CP + 4;
   const int j = threadIdx.x;
   float a[CP];
 #pragma unroll
@@ -47,26 +105,13 @@ BSP_DEV void chol_cols(const TG* g, int c, int cpad, const float* dsc, float* Rr
     a[i] = v;
   }
   bool bad = false;
-#pragma unroll
-  for (int k = 0; k < CP; ++k) {
-    if (k >= c) continue;   // uniform over the CP threads
-    float* buf = lbuf + (k & 1) * (CP + 4);
-    buf[j] = a[k];
-    asm volatile("bar.sync 1, %0;" ::"r"(CP) : "memory");
-    const float piv = buf[k];
-    const bool ok = piv > 0.f && isfinite(piv);
-    bad = bad || !ok;
-    const float rs = ok ? rsqrtf(piv) : 1.f;
-    const float f = a[k] * rs * rs;
-    a[k] = a[k] * rs;
-#pragma unroll
-    for (int i = k + 1; i < CP; ++i) a[i] -= buf[i] * f;
-  }
+  chol_step<CP, 0>(a, c, j, lbuf, bad);
 #pragma unroll
   for (int i = 0; i < CP; ++i) Rr[i * CP + j] = i <= j ? a[i] : 0.f;
   rinv[j] = 1.f / Rr[j * CP + j];
   if (bad && j == 0) *fail = 1;
 }
+
 
 // Block-level Cholesky (any TA), for the FP64-accumulated pass: the balanced
 // factorization of chol_inverse without the inverse; writes R (T, stride CP,
@@ -170,29 +215,36 @@ BSP_DEV void trsm_rows(T* S, int rows, int cpad, int ldS, int c, const T* Rr, co
   }
 }
 
-// Stage rows [row0, row0 + nr) x [0, c) of A (stride ld) into S [rows x cpad],
-// zero padded: warp per row, 16-byte vectors when aligned.
+// Stage rows [row0, row0 + nr) x [0, c) of A (stride ld) into S [rows x cpad]
+// (row stride ldS), zero padded.  Aligned rows go by 16-byte asynchronous
+// copies, all in flight at once (consecutive threads take consecutive pieces
+// of a row: coalesced); the caller's barrier follows the final wait.
 template <typename T>
 BSP_DEV void stage_rows(const T* __restrict__ A, int ld, int row0, int nr, int c, int cpad,
                         int rows, T* S, int ldS) {
   constexpr int VE = 16 / sizeof(T);
-  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const bool vec = (ld % VE == 0) && (cpad % VE == 0) && (c % VE == 0) &&
                    ((uintptr_t)A % 16 == 0);
-  for (int r = threadIdx.x >> 5; r < rows; r += nw) {
-    T* dst = S + r * ldS;
-    if (r >= nr) {
-      for (int j = lane; j < cpad; j += 32) dst[j] = T(0);
-    } else if (vec) {
-      const float4* src = reinterpret_cast<const float4*>(A + (size_t)(row0 + r) * ld);
-      float4* d4 = reinterpret_cast<float4*>(dst);
-      for (int v = lane; v < cpad / VE; v += 32) {
-        float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-        d4[v] = v < c / VE ? src[v] : z;
+  if (vec) {
+    const int per = cpad / VE;
+    for (int t = threadIdx.x; t < rows * per; t += blockDim.x) {
+      const int r = t / per, v = t - r * per;
+      T* dst = S + r * ldS + v * VE;
+      if (r < nr && v * VE < c) {
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                         (uint32_t)__cvta_generic_to_shared(dst)),
+                     "l"(A + (size_t)(row0 + r) * ld + v * VE));
+      } else {
+        *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
       }
-    } else {
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+  } else {
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int r = threadIdx.x >> 5; r < rows; r += nw) {
+      T* dst = S + r * ldS;
       const T* src = A + (size_t)(row0 + r) * ld;
-      for (int j = lane; j < cpad; j += 32) dst[j] = j < c ? src[j] : T(0);
+      for (int j = lane; j < cpad; j += 32) dst[j] = (r < nr && j < c) ? src[j] : T(0);
     }
   }
 }
