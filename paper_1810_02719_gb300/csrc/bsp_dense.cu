@@ -80,7 +80,7 @@ BSP_DEV void chol_inverse(const TG* g, int c, int cpad, TA* A, TA* d, T* Rr, T* 
       *fail = 1;
       v = TA(1);
     }
-    d[t] = TA(1) / sqrt(v);
+    d[t] = rsqrt_newton(v);
   }
   __syncthreads();
   for (int i = threadIdx.x >> 5; i < c; i += blockDim.x >> 5)
@@ -96,7 +96,7 @@ BSP_DEV void chol_inverse(const TG* g, int c, int cpad, TA* A, TA* d, T* Rr, T* 
         *fail = 1;
         piv = TA(1);
       }
-      const TA inv = TA(1) / sqrt(piv);
+      const TA inv = rsqrt_newton(piv);
       for (int jj = k + tx; jj < c; jj += 16) {
         const TA lj = A[k * cpad + jj] * inv;
         lrow[jj] = lj;
@@ -180,9 +180,10 @@ BSP_DEV void chol_inverse_any(const TG* g, int c, int cpad, TA* A, TA* d, T* Rr,
   else chol_inverse<T, TA, TG, 128>(g, c, cpad, A, d, Rr, M, fail);
 }
 
-// Cholesky + inverse for each block of the batch (one CTA per block).
-template <typename T, typename TA>
-__global__ void __launch_bounds__(kDT) k_chol(DenseArgs a, const TA* __restrict__ G,
+// Cholesky + inverse for each block of the batch (one CTA per block): the
+// Gram in TG, the factorization in TA.
+template <typename T, typename TA, typename TG = TA>
+__global__ void __launch_bounds__(kDT) k_chol(DenseArgs a, const TG* __restrict__ G,
                                               T* __restrict__ Mout) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int b = a.batch[blockIdx.x];
@@ -194,7 +195,7 @@ __global__ void __launch_bounds__(kDT) k_chol(DenseArgs a, const TA* __restrict_
   __shared__ int fail;
   if (threadIdx.x == 0) fail = 0;
   __syncthreads();
-  chol_inverse_any<T, TA, TA>(G + (size_t)blockIdx.x * cpad * cpad, c, cpad, A, d, Rr,
+  chol_inverse_any<T, TA, TG>(G + (size_t)blockIdx.x * cpad * cpad, c, cpad, A, d, Rr,
                               Mout + (size_t)blockIdx.x * cpad * cpad, &fail);
   if (fail && threadIdx.x == 0) atomicOr(a.status, ST_NUMERICAL);
 }
@@ -433,6 +434,7 @@ template <typename T, typename TA>
 void configure_one() {
   set_max_dynamic_smem(k_gram<T, TA>);
   set_max_dynamic_smem(k_chol<T, TA>);
+  set_max_dynamic_smem(k_chol<T, T, TA>);
   set_max_dynamic_smem(k_panel_mul<T, TA, true, true>);
   set_max_dynamic_smem(k_panel_mul<T, TA, true, false>);
   set_max_dynamic_smem(k_panel_mul<T, TA, false, false>);
@@ -499,17 +501,18 @@ int launch_cholqr2(const DenseArgs& a, const T* Y, T* Q, TA* Gp, T* Rsm, cudaStr
     if (launches) *launches += 4;
     return cudaGetLastError() == cudaSuccess ? BSP_OK : BSP_ERR_CUDA;
   }
-  // pass 2 accumulates and factorises in TA as well: with MIXED precision an
-  // ill-conditioned Y (z >= 2) leaves Q1 far enough from orthonormal that an
-  // FP32 Cholesky of its Gram can break down
+  // pass 2: the Gram of Q1 accumulates in TA; it is I + O(kappa u), so its
+  // Cholesky runs in T
   prof_begin(KC_PANEL, s);
   k_panel_mul<T, TA, true, true><<<gp, kDT, sm_mul, s>>>(a, Y, Q, Rsm, CH, maxch, Gp);
   prof_end(KC_PANEL, s);
   prof_begin(KC_REDUCE, s);
   k_reduce<TA><<<gr, kDT, 0, s>>>(a, CH, maxch, true, Gp, G);
   prof_end(KC_REDUCE, s);
+  const size_t sm_chol_b = (size_t)(chol_a_elems<T, T>(cpad, cpw) + 2 * cpad) * sizeof(T) +
+                           (size_t)cpw * cpw * sizeof(T);
   prof_begin(KC_CHOL, s);
-  k_chol<T, TA><<<a.nbatch, kDT, sm_chol_a, s>>>(a, G, Rsm);
+  k_chol<T, T, TA><<<a.nbatch, kDT, sm_chol_b, s>>>(a, G, Rsm);
   prof_end(KC_CHOL, s);
   prof_begin(KC_PANEL, s);
   k_panel_mul<T, T, true, false><<<gp, kDT, sm_mul, s>>>(a, Q, Q, Rsm, CH, maxch, (T*)nullptr);

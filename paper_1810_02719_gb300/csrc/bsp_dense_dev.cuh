@@ -44,6 +44,22 @@ BSP_DEV void st4(T* p, const T* v) {
   }
 }
 
+// 1/sqrt(x) for x > 0 without a divide or a square root: an FP32 seed from
+// rsqrtf refined by Newton-Raphson steps y <- y (3 - x y^2) / 2 (two steps
+// take the ~2^-23 seed error below 2^-52 for FP64).  Used on the Cholesky's
+// dependent chain, where the FP64 divide and square root cost most.
+template <typename TA>
+BSP_DEV TA rsqrt_newton(TA x) {
+  if constexpr (sizeof(TA) == 4) {
+    return rsqrtf(x);
+  } else {
+    TA y = (TA)rsqrtf((float)x);
+    y = y * (TA(1.5) - TA(0.5) * x * y * y);
+    y = y * (TA(1.5) - TA(0.5) * x * y * y);
+    return y;
+  }
+}
+
 // out[i][j] (cpad x cpad, TA) = sum_r S[r][i] * S2[r][j] over the panel's CH rows,
 // in 4x4 register tiles; `upper` computes only tiles with ti <= tj.
 template <typename T, typename TA>

@@ -132,7 +132,7 @@ BSP_DEV void chol_block(const TG* g, int c, int cpad, TA* A, TA* dsc, TA* lrow, 
         *fail = 1;
         piv = TA(1);
       }
-      const TA inv = TA(1) / sqrt(piv);
+      const TA inv = rsqrt_newton(piv);
       for (int jj = k + tx; jj < c; jj += 16) {
         const TA lj = A[k * cpad + jj] * inv;
         lrow[jj] = lj;
@@ -314,9 +314,10 @@ BSP_DEV void panel_gram_split(const T* S, int rows, int cpad, int ldS, T* half, 
 // [p RP, (p+1) RP) of Y in shared memory for both passes; partial Grams go
 // through L2 (Gpart), a distributed fixed-order reduction forms G (Gfin), and
 // every CTA factorizes G itself (identical inputs, identical results), so the
-// only inter-CTA steps are cluster barriers.  Every pass accumulates in TA and,
-// when TA is double, factorizes in FP64 (block-level); otherwise the Cholesky
-// runs in registers (FP32).  Q = Y R^-1 by row-wise forward substitution.
+// only inter-CTA steps are cluster barriers.  Every pass accumulates in TA;
+// when TA is double the first pass factorizes in FP64 (block-level); the
+// second pass's Gram is I + O(kappa u), whose Cholesky runs in registers in
+// FP32 like every pass of the FP32 mode.  Q = Y R^-1 by row-wise forward substitution.
 template <typename T, typename TA, int CP>
 __global__ void __launch_bounds__(kDT) k_cholqr2_cluster(DenseArgs a, const T* Y, T* Q, int P,
                                                          int rp_max, TA* Gpart, TA* Gfin,
@@ -370,7 +371,7 @@ __global__ void __launch_bounds__(kDT) k_cholqr2_cluster(DenseArgs a, const T* Y
     if constexpr (sizeof(T) == 8) {
       chol_block<T, TA, TA, CP>(gf, c, cpad, A, dsc, dsc + cpad, Rr, rinv, &fail);
     } else {
-      if (sizeof(TA) == 8) {   // MIXED: every pass factorises in FP64
+      if (sizeof(TA) == 8 && pass == 0) {   // MIXED: the first pass factorises in FP64
         chol_block<T, TA, TA, CP>(gf, c, cpad, A, dsc, dsc + cpad, Rr, rinv, &fail);
       } else {
         if (threadIdx.x < CP)
