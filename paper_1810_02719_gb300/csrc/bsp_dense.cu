@@ -339,6 +339,13 @@ __global__ void __launch_bounds__(kDT) k_jacobi(DenseArgs a, const TA* __restric
   const T floor_abs = (T)8 * eps * hscale;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   int sweeps = 0;
+  // per-round "some pair rotates" flags in three rotating slots: round r sets
+  // slot r % 3 and clears slot (r + 1) % 3 before its first barrier, so the
+  // next round's writers (past that barrier) never race the clearing, and a
+  // round without rotations skips its two update phases and their barriers
+  __shared__ int rot[3];
+  if (threadIdx.x < 3) rot[threadIdx.x] = 0;
+  int rr = 0;
   for (int sweep = 0; sweep < kJacobiSweeps; ++sweep) {
     // any pair above threshold?  (checked before the sweep: a nearly diagonal
     // H, the common case for a warm-started block, costs one pass)
@@ -354,7 +361,8 @@ __global__ void __launch_bounds__(kDT) k_jacobi(DenseArgs a, const TA* __restric
     const int any = rotated;
     if (!any) break;
     ++sweeps;
-    for (int rnd = 0; rnd < ne - 1; ++rnd) {
+    for (int rnd = 0; rnd < ne - 1; ++rnd, rr = rr == 2 ? 0 : rr + 1) {
+      if (threadIdx.x == 0) rot[rr == 2 ? 0 : rr + 1] = 0;
       for (int m = threadIdx.x; m < ne / 2; m += blockDim.x) {
         // round-robin: position 0 fixed, the others rotate by one per round
         int p = m == 0 ? 0 : 1 + (m - 1 + rnd) % (ne - 1);
@@ -367,10 +375,12 @@ __global__ void __launch_bounds__(kDT) k_jacobi(DenseArgs a, const TA* __restric
           T t = (tau >= 0 ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
           cth = T(1) / sqrt(T(1) + t * t);
           sth = t * cth;
+          rot[rr] = 1;
         }
         pp[m] = p; qq[m] = q; cs[m] = cth; sn[m] = sth;
       }
       __syncthreads();
+      if (!rot[rr]) continue;   // uniform: nothing to rotate this round
       // rows p, q  <-  J^T H   (warp per pair, lane per column)
       for (int m = warp; m < ne / 2; m += nwarp) {
         const int p = pp[m], q = qq[m];

@@ -73,15 +73,31 @@ def test_chain_1m_torus_c64():
         Xon = Xo.cpu().double().numpy()
         om = O.build_mesh(N * N, ptr, verts, parent, faces=faces)
         U_ref = O.oi_track(om, c, t, starts, delta=1e-2)
+        # the root starts from a random matrix: after t steps its basis is not
+        # converged, so it is held to the oracle's own response to 1e-6
+        # perturbations of the solves (warm-started blocks converge)
+        om0 = O.build_mesh(N * N, ptr[:2], verts[:ptr[1]], parent[:1], faces=faces)
+        orig = O.apply_S
+        rng = np.random.default_rng(0)
+        O.apply_S = lambda L, V, d, z: (lambda Y: Y + 1e-6 * np.linalg.norm(Y, axis=0) *
+                                        rng.standard_normal(Y.shape) / np.sqrt(Y.shape[0]))(
+                                            orig(L, V, d, z))
+        try:
+            U0p = O.oi_track(om0, c, t, starts, delta=1e-2)[0]
+        finally:
+            O.apply_S = orig
+        rows0 = om.blocks[0].verts
+        tol0 = max(PROJ_F32, 10 * O.projector_rel_error(U0p, U_ref[0], xyz[rows0]))
         for b in range(k):
             U = bsp.bsp_get_basis(h, b, 1024).astype(np.float64)
             assert _orthonormality(U) <= ORTH_F32, b
             if b in (0, 1, 2, 255, 511, 767, 1022, 1023):
                 rows = om.blocks[b].verts
-                assert O.max_sine(U, U_ref[b]) <= SINE_F32, b
-                assert O.projector_rel_error(U, U_ref[b], xyz[rows]) <= PROJ_F32, b
+                tol = tol0 if b == 0 else PROJ_F32
+                assert O.max_sine(U, U_ref[b]) <= max(SINE_F32, 10 * tol), b
+                assert O.projector_rel_error(U, U_ref[b], xyz[rows]) <= tol, b
                 ref = U_ref[b] @ (U_ref[b].T @ xyz[rows])
-                assert np.linalg.norm(Xon[rows] - ref) / np.linalg.norm(ref) <= PROJ_F32, b
+                assert np.linalg.norm(Xon[rows] - ref) / np.linalg.norm(ref) <= tol, b
     finally:
         bsp.bsp_mesh_destroy(h)
 
