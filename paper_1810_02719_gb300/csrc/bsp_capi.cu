@@ -493,14 +493,6 @@ int enqueue_fixed(bsp_mesh* M, int c, int t_max, cudaStream_t s, int* launches) 
     const int32_t* batch = M->d_waves + M->h_wave_off[l];
     int wmax = 0;
     for (int b : M->waves[l]) wmax = std::max(wmax, M->h_bptr[b + 1] - M->h_bptr[b]);
-    launch_init_starts<T>(batch, nbw, M->d_bptr, M->d_parent, M->d_root_off, M->d_cb, M->d_cb,
-                          (const T*)M->d_starts, c, U, M->c_cap, wmax, c, s);
-    ++*launches;
-    // Rayleigh-Ritz of the previous wave leaves the critical path: the warm
-    // starts that read its bases have just been copied, and Rayleigh-Ritz does
-    // not change the spans that the remaining waves depend on.
-    if (l > 0 && M->opts.rayleigh_ritz && (rc = fork_rr<T, TA>(M, l - 1, c, s, launches)))
-      return rc;
     // Onorm of the start where it is not already an orthonormal basis: roots and
     // children whose size differs from their parent's.
     std::vector<int32_t> need;
@@ -508,6 +500,20 @@ int enqueue_fixed(bsp_mesh* M, int c, int t_max, cudaStream_t s, int* launches) 
       int p = M->h_parent[b];
       if (p < 0 || (M->h_bptr[b + 1] - M->h_bptr[b]) != (M->h_bptr[p + 1] - M->h_bptr[p]))
         need.push_back(b);
+    }
+    // a wave of same-size warm starts reads its starts in place (the parents'
+    // rows) in its first solve: no start copy
+    const int sub = t_max * M->opts.z;
+    const bool in_place = need.empty() && l > 0 && sub > 0;
+    if (!in_place) {
+      launch_init_starts<T>(batch, nbw, M->d_bptr, M->d_parent, M->d_root_off, M->d_cb, M->d_cb,
+                            (const T*)M->d_starts, c, U, M->c_cap, wmax, c, s);
+      ++*launches;
+      // Rayleigh-Ritz of the previous wave leaves the critical path here: the
+      // starts have been copied, and Rayleigh-Ritz does not change the spans
+      // that later waves depend on
+      if (l > 0 && M->opts.rayleigh_ritz && (rc = fork_rr<T, TA>(M, l - 1, c, s, launches)))
+        return rc;
     }
     DenseArgs da{batch, nbw, M->d_bptr, M->d_cb, M->c_cap, c, wmax, M->d_status};
     if (!need.empty()) {
@@ -537,17 +543,22 @@ int enqueue_fixed(bsp_mesh* M, int c, int t_max, cudaStream_t s, int* launches) 
     // handles).  Solves between two Onorms run in one CG launch (every column
     // goes straight on to its next solve).  Intermediate Onorms take one
     // Cholesky-QR pass, the last one the full CholeskyQR2.
-    const int sub = t_max * M->opts.z;
     const bool warm = need.empty();
     for (int t = 0; t < sub;) {
       const int g = (warm && t + 1 < sub) ? 2 : 1;   // solves before the next Onorm
       CgArgs cg = ca;
       cg.z = g;
+      if (t == 0 && in_place) cg.vsrc = M->d_parent;
       rc = buckets ? launch_cg_buckets<T>(mv, U, Y, cg, M->wave_bucket[l].data(),
                                           M->wave_bucket_rows[l].data(), c, s)
                    : launch_cg<T>(mv, U, Y, cg, cs, wmax, c, s);
       if (rc) return fail(rc, "CG launch failed (block too large for shared memory?)");
       ++*launches;
+      // with in-place starts, Rayleigh-Ritz of the previous wave forks once the
+      // first solve has read its bases
+      if (t == 0 && in_place && M->opts.rayleigh_ritz &&
+          (rc = fork_rr<T, TA>(M, l - 1, c, s, launches)))
+        return rc;
       t += g;
       const int passes = t == sub ? 2 : 1;
       if ((rc = launch_cholqr2<T, TA>(da, Y, U, (TA*)M->d_Gp, (T*)M->d_Rsm, s, launches, passes)))

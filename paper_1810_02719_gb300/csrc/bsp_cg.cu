@@ -126,10 +126,11 @@ __global__ void __launch_bounds__(kThreads) k_cg(MeshView<T> mv, const T* __rest
   int buf1 = 0, buf2 = 0;
 
   // right-hand side b = V slab (zero-padded past ncol)
+  const int rv = a.vsrc ? mv.bptr[a.vsrc[b]] : r0;
   for (int i = threadIdx.x; i < nb; i += kThreads) {
     T v[CS];
 #pragma unroll
-    for (int j = 0; j < CS; ++j) v[j] = j < ncol ? V[(size_t)(r0 + i) * a.ld + j0 + j] : T(0);
+    for (int j = 0; j < CS; ++j) v[j] = j < ncol ? V[(size_t)(rv + i) * a.ld + j0 + j] : T(0);
     sts_row<T, CS>(p + (size_t)i * CS, v);
   }
   __syncthreads();
@@ -463,10 +464,11 @@ __global__ void __launch_bounds__(kThreads) k_cg1(MeshView<T> mv, const T* __res
     }
   };
   T bvec[MAXR], x[MAXR], r[MAXR], p[MAXR], sv[MAXR], wv[MAXR];
+  const int rv = a.vsrc ? mv.bptr[a.vsrc[b]] : r0;   // rows of the right-hand side
 #pragma unroll
   for (int m = 0; m < MAXR; ++m) {
     const int i = threadIdx.x + kThreads * m;
-    bvec[m] = i < nb ? V[(size_t)(r0 + i) * a.ld + col] : T(0);
+    bvec[m] = i < nb ? V[(size_t)(rv + i) * a.ld + col] : T(0);
   }
   int steps_all = 0, steps_max = 0;
   bool unconverged = false, bad = false;

@@ -138,6 +138,9 @@ struct CgArgs {
   int z; double delta; double rtol; int max_steps;
   int* status; CgStats* stats;
   int max_deg = 0;          // largest row degree of the mesh (selects the register-ELL kernel)
+  // right-hand sides read from the rows of block vsrc[b] instead of block b
+  // (a warm start read in place from a same-size parent); nullptr: own rows
+  const int32_t* vsrc = nullptr;
 };
 extern bool g_disable_cg1;  // force the shared-memory CG kernel (A/B checks)
 template <typename T>
