@@ -137,6 +137,7 @@ void configure_once() {
     configure_adjoint_kernels();
     configure_tc_kernels();
     configure_spmm_kernels();
+    configure_dyn_kernels();
   });
 }
 

@@ -83,10 +83,18 @@ __global__ void __launch_bounds__(kT) k_dyn_decide(const int32_t* batch, const i
   __shared__ T Es[kMaxC][3];
   __shared__ TA red[kT / 32];
   __shared__ TA res[kMaxChk];
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  T* Xs = reinterpret_cast<T*>(dyn_smem);   // the block's coordinates, local order [nb x 3]
   const int b = batch[blockIdx.x];
   const int c = cb[b];
   const int r0 = bptr[b], nb = bptr[b + 1] - r0;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  // gather the block's coordinates once (all rows in flight together)
+  for (int t = threadIdx.x; t < nb * 3; t += kT) {
+    const int i = t / 3, k = t - i * 3;
+    Xs[t] = X[(size_t)verts[r0 + i] * 3 + k];
+  }
+  __syncthreads();
   // E = U^T X: lanes own columns j = lane + 32 q, warps split the rows
   for (int q = 0; q * 32 < c; ++q) {
     const int j = q * 32 + lane;
@@ -95,7 +103,7 @@ __global__ void __launch_bounds__(kT) k_dyn_decide(const int32_t* batch, const i
     int cnt = 0;
     for (int i = w; i < nb; i += kT / 32) {
       const T u = j < c ? U[(size_t)(r0 + i) * ld + j] : T(0);
-      const T* x = X + (size_t)verts[r0 + i] * 3;
+      const T* x = Xs + i * 3;
       f0 += u * x[0];
       f1 += u * x[1];
       f2 += u * x[2];
@@ -120,35 +128,38 @@ __global__ void __launch_bounds__(kT) k_dyn_decide(const int32_t* batch, const i
   }
   // residual norms at every checkpoint width; ||X||^2
   const int nchk = c / c_step;
-  T acc[kMaxChk];
-#pragma unroll
-  for (int q = 0; q < kMaxChk; ++q) acc[q] = 0;
+  __shared__ T accs[kMaxChk][kT];
   T xx = 0;
+  // c is a multiple of c_step = 8: one checkpoint per 8-column segment.  The
+  // segments' partial sums are independent (no long dependent chain); every
+  // thread keeps its checkpoint sums in its own column of accs (shared).
+  for (int q = 0; q < nchk; ++q) accs[q][threadIdx.x] = 0;
   for (int i = threadIdx.x; i < nb; i += kT) {
-    const T* x = X + (size_t)verts[r0 + i] * 3;
+    const T* x = Xs + i * 3;
     const T x0 = x[0], x1 = x[1], x2 = x[2];
     xx += x0 * x0 + x1 * x1 + x2 * x2;
     T h0 = 0, h1 = 0, h2 = 0;
     const T* u = U + (size_t)(r0 + i) * ld;
-    int q = 0;
-    for (int l = 0; l < c; ++l) {
-      const T ul = u[l];
-      h0 += ul * Es[l][0];
-      h1 += ul * Es[l][1];
-      h2 += ul * Es[l][2];
-      if ((l + 1) % c_step == 0) {
-        const T d0 = x0 - h0, d1 = x1 - h1, d2 = x2 - h2;
+    for (int q = 0; q < nchk; ++q) {
+      T s0 = 0, s1 = 0, s2 = 0;
 #pragma unroll
-        for (int qq = 0; qq < kMaxChk; ++qq)
-          if (qq == q) acc[qq] += d0 * d0 + d1 * d1 + d2 * d2;
-        ++q;
+      for (int e = 0; e < 8; ++e) {
+        const T ul = u[q * 8 + e];
+        s0 += ul * Es[q * 8 + e][0];
+        s1 += ul * Es[q * 8 + e][1];
+        s2 += ul * Es[q * 8 + e][2];
       }
+      h0 += s0;
+      h1 += s1;
+      h2 += s2;
+      const T d0 = x0 - h0, d1 = x1 - h1, d2 = x2 - h2;
+      accs[q][threadIdx.x] += d0 * d0 + d1 * d1 + d2 * d2;
     }
     gcol[(size_t)(r0 + i)] = (x0 - h0) + (x1 - h1) + (x2 - h2);
   }
   const TA xnorm2 = block_reduce<T, TA>((TA)xx, red);
   for (int q = 0; q < nchk; ++q) {
-    TA v = block_reduce<T, TA>((TA)acc[q], red);
+    TA v = block_reduce<T, TA>((TA)accs[q][threadIdx.x], red);
     if (threadIdx.x == 0) res[q] = v;
   }
   __syncthreads();
@@ -238,13 +249,18 @@ __global__ void __launch_bounds__(kT) k_dyn_grow(const int32_t* batch, const int
     }
     __syncthreads();
   }
-  // G -= U[:, :c] Cm
+  // G -= U[:, :c] Cm (c a multiple of 8; four independent partial sums)
   for (int t = threadIdx.x; t < nb * c_step; t += kT) {
     const int i = t / c_step, g = t - i * c_step;
     T* row = U + (size_t)(r0 + i) * ld;
-    T s = row[c + g];
-    for (int l = 0; l < c; ++l) s -= row[l] * Cm[l][g];
-    row[c + g] = s;
+    T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+    for (int l = 0; l < c; l += 4) {
+      s0 += row[l] * Cm[l][g];
+      s1 += row[l + 1] * Cm[l + 1][g];
+      s2 += row[l + 2] * Cm[l + 2][g];
+      s3 += row[l + 3] * Cm[l + 3][g];
+    }
+    row[c + g] -= (s0 + s1) + (s2 + s3);
   }
   if (threadIdx.x == 0) cb[b] = c + c_step;
 }
@@ -270,11 +286,19 @@ int launch_dyn_decide(const int32_t* batch, int nbatch, const int32_t* bptr, con
                       const int32_t* forced, double tol, int c_step, int c_max, T* gcol,
                       TA* rho_out, int max_nb, cudaStream_t s) {
   if (c_step < 8 || c_max > kMaxC) return BSP_ERR_INVALID_ARG;
+  const size_t smem = (size_t)max_nb * 3 * sizeof(T);
+  if (smem > 160 * 1024) return BSP_ERR_INVALID_ARG;
   prof_begin(KC_DYN, s);
-  k_dyn_decide<T, TA><<<nbatch, kT, 0, s>>>(batch, bptr, verts, X, U, ld, cb, action, forced, tol,
-                                            c_step, c_max, gcol, rho_out);
+  k_dyn_decide<T, TA><<<nbatch, kT, smem, s>>>(batch, bptr, verts, X, U, ld, cb, action, forced,
+                                               tol, c_step, c_max, gcol, rho_out);
   prof_end(KC_DYN, s);
   return cudaGetLastError() == cudaSuccess ? BSP_OK : BSP_ERR_CUDA;
+}
+
+void configure_dyn_kernels() {
+  set_max_dynamic_smem(k_dyn_decide<float, float>);
+  set_max_dynamic_smem(k_dyn_decide<float, double>);
+  set_max_dynamic_smem(k_dyn_decide<double, double>);
 }
 
 template <typename T, typename TA>

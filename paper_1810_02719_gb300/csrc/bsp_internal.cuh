@@ -208,6 +208,7 @@ void configure_tc_kernels();
 // Tiled operator product (bsp_spmm.cu): chunks of up to 128 rows inside a
 // block, each with the row range [lo, hi] that its neighbours reach.
 void configure_spmm_kernels();
+void configure_dyn_kernels();
 std::vector<int32_t> spmm_chunk_rows(const std::vector<int32_t>& bptr);
 void launch_spmm_ranges(const MeshView<float>& mv_any, const int32_t* blk_row, int32_t* chunks,
                         int nchunks, cudaStream_t s);
