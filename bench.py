@@ -155,6 +155,12 @@ def run_ours(args, rank, world, device):
         bsp.bsp_reconstruct(h, E, 3, Xo, stream)
         return launches + 2
 
+    # untimed: the CG layout picked by the library's autotuner on this mesh
+    tuned = None
+    if args.cs == 0:
+        chosen, tt = bsp.bsp_autotune(h, args.c, args.t, V0, reps=2, stream=stream)
+        tuned = {"cols_per_cta": chosen, "candidates_ms": tt}
+
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -310,7 +316,7 @@ def run_ours(args, rank, world, device):
                 "h2d_bytes_per_step": int(V0h.nbytes + Xh.nbytes),
                 "d2h_bytes_per_step": int(Eh.nbytes + Xoh.nbytes)},
         "roofline": roof, "spmm_roofline": spmm_roof, "kernels": kernels,
-        "eig_baseline": eig, "clocks_summary": clk_summary,
+        "eig_baseline": eig, "clocks_summary": clk_summary, "autotune": tuned,
         "stats": {"cg_steps_total": st["cg_steps_total"], "cg_steps_max": st["cg_steps_max"]},
     }
 
@@ -383,6 +389,11 @@ def run_batched(args, device):
         bsp.bsp_reconstruct(h, E, 3, Xo, stream)
         return launches + 2
 
+    # untimed: the CG layout picked by the library's autotuner (fixed-c tracking
+    # at c = 32, the typical chosen width, on this mesh)
+    V32 = torch.tensor(synth.gaussian_starts(ptr, parent, 32, seed=0), dtype=torch.float32,
+                       device=device)
+    chosen, tt = bsp.bsp_autotune(h, 32, args.t, V32, reps=1, stream=stream)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -428,6 +439,7 @@ def run_batched(args, device):
         "kernels": {kk: {"ms": round(v[0], 3), "launches": v[1]} for kk, v in kt.items() if v[1]},
         "stats": {"cg_steps_total": st["cg_steps_total"], "cg_steps_max": st["cg_steps_max"],
                   "not_converged": st["not_converged"]},
+        "autotune": {"cols_per_cta": chosen, "candidates_ms_fixed_c32": tt},
     }
 
 
@@ -815,7 +827,8 @@ def main():
             "data": "synthetic", "config": config_dict(args), "clocks": res["clocks"],
             "e2e": res["e2e"], "gpu_launches": res["launches"], "roofline": res["roofline"],
             "spmm_roofline": res["spmm_roofline"], "eig_baseline": res["eig_baseline"],
-            "kernels": res["kernels"], "cpu_baseline": cpu, "stats": res["stats"]}
+            "kernels": res["kernels"], "cpu_baseline": cpu, "stats": res["stats"],
+            "autotune": res["autotune"]}
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

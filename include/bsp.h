@@ -304,6 +304,23 @@ int bsp_get_kernel_times(const bsp_mesh* mesh, double* ms_out, int32_t* launches
                          int32_t n_classes);
 
 /*
+ * Autotuner for the tile shape of the solves (no counterpart in the paper):
+ * times fixed-c tracking of this mesh (bsp_oi_track with c, t_max and the
+ * given root starts, reps timed runs after one warm-up, median) for each
+ * candidate CG layout -- one column per CTA in size buckets (0) and column
+ * slabs of 2, 4 and 8 columns per CTA -- and keeps the fastest in the mesh's
+ * options for later tracking calls (fixed and dynamic c).
+ *   times_ms  host double [4] or NULL: median ms per candidate, in the order
+ *             0, 2, 4, 8 (a candidate whose shared memory does not fit the
+ *             mesh's largest block reports -1).
+ *   chosen    host int32 or NULL: the kept columns-per-CTA value.
+ * The tracked bases afterwards are those of the last run.  Errors: as
+ * bsp_oi_track.
+ */
+int bsp_autotune(bsp_mesh* mesh, int32_t c, int32_t t_max, const void* V0_roots, int32_t reps,
+                 double* times_ms, int32_t* chosen, void* stream);
+
+/*
  * Allocation-free orthonormalisation of one block (no counterpart in the
  * paper: an interface for callers that may not allocate device memory).
  * Q = Onorm(Y) by CholeskyQR2 in FP32 (the same fused kernel that Onorm uses

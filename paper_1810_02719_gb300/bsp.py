@@ -84,6 +84,7 @@ def _load():
         "bsp_filter_forward": (C.c_int, [P, I32, I32, P, P, P, P]),
         "bsp_filter_backward": (C.c_int, [P, P, P, P, P, P]),
         "bsp_reconstruct_bf16": (C.c_int, [P, P, I32, P, P]),
+        "bsp_autotune": (C.c_int, [P, I32, I32, P, I32, P, C.POINTER(I32), P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -103,7 +104,8 @@ def exported_symbols():
             "bsp_oi_track", "bsp_oi_track_dynamic", "bsp_get_block_c", "bsp_get_basis",
             "bsp_project", "bsp_reconstruct", "bsp_spmm", "bsp_last_error",
             "bsp_set_profiling", "bsp_get_kernel_times", "bsp_onorm_noalloc",
-            "bsp_filter_forward", "bsp_filter_backward", "bsp_reconstruct_bf16"]
+            "bsp_filter_forward", "bsp_filter_backward", "bsp_reconstruct_bf16",
+            "bsp_autotune"]
 
 
 def _check(code):
@@ -227,6 +229,16 @@ def bsp_set_edge_weights(mesh, w):
 
 def bsp_oi_track(mesh, c, t_max, V0_roots, stream=None):
     _check(_lib.bsp_oi_track(mesh, c, t_max, _ptr(V0_roots), _stream_ptr(stream)))
+
+
+def bsp_autotune(mesh, c, t_max, V0_roots, reps=3, stream=None):
+    """Time the CG layouts (columns per CTA 0, 2, 4, 8) on fixed-c tracking of this
+    mesh and keep the fastest; returns (chosen, {candidate: median ms or -1})."""
+    times = np.zeros(4, np.float64)
+    chosen = C.c_int32()
+    _check(_lib.bsp_autotune(mesh, c, t_max, _ptr(V0_roots), reps, _ptr(times), C.byref(chosen),
+                             _stream_ptr(stream)))
+    return chosen.value, dict(zip((0, 2, 4, 8), times.tolist()))
 
 
 def bsp_oi_track_dynamic(mesh, X, rel_tol, c_min, c_max, c_step, t_max, seed, V0_roots,

@@ -624,7 +624,8 @@ int track_fixed(bsp_mesh* M, int c, int t_max, const void* V0, cudaStream_t s) {
   int launches = 0;
   if ((rc = stage_onorm_lists(M)) != BSP_OK) return rc;
   if (M->opts.use_graph && !M->profiling) {
-    if (!M->graph_exec || M->graph_c != c || M->graph_t != t_max) {
+    if (!M->graph_exec || M->graph_c != c || M->graph_t != t_max ||
+        M->graph_cs != M->opts.cols_per_cta) {
       if (M->graph_exec) {
         cudaGraphExecDestroy(M->graph_exec);
         M->graph_exec = nullptr;
@@ -645,6 +646,7 @@ int track_fixed(bsp_mesh* M, int c, int t_max, const void* V0, cudaStream_t s) {
       if (ie != cudaSuccess) return fail(BSP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
       M->graph_c = c;
       M->graph_t = t_max;
+      M->graph_cs = M->opts.cols_per_cta;
       M->graph_launches = launches;
     }
     CU(cudaGraphLaunch(M->graph_exec, s));
@@ -1126,6 +1128,60 @@ int bsp_oi_track(bsp_mesh* M, int32_t c, int32_t t_max, const void* V0, void* st
     case BSP_PREC_F32: return track_fixed<float, float>(M, c, t_max, V0, s);
     default: return track_fixed<float, double>(M, c, t_max, V0, s);
   }
+}
+
+int bsp_autotune(bsp_mesh* M, int32_t c, int32_t t_max, const void* V0, int32_t reps,
+                 double* times_ms, int32_t* chosen, void* stream) {
+  g_err.clear();
+  if (!M) return fail(BSP_ERR_INVALID_ARG, "mesh is NULL");
+  if (reps < 1) return fail(BSP_ERR_INVALID_ARG, "reps must be >= 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int cand[4] = {0, 2, 4, 8};
+  const int keep = M->opts.cols_per_cta;
+  double best = -1.0;
+  int best_cs = keep;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  int rc = BSP_OK;
+  for (int q = 0; q < 4; ++q) {
+    M->opts.cols_per_cta = cand[q];
+    double ms_med = -1.0;
+    rc = bsp_oi_track(M, c, t_max, V0, stream);   // warm-up (captures the schedule)
+    if (rc == BSP_OK) {
+      std::vector<double> ts;
+      for (int r = 0; r < reps && rc == BSP_OK; ++r) {
+        cudaEventRecord(e0, s);
+        rc = bsp_oi_track(M, c, t_max, V0, stream);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ts.push_back(ms);
+      }
+      if (rc == BSP_OK) {
+        std::sort(ts.begin(), ts.end());
+        ms_med = ts[ts.size() / 2];
+      }
+    }
+    if (rc == BSP_ERR_INVALID_ARG && cand[q] != 0) {
+      rc = BSP_OK;   // this slab does not fit the mesh's blocks: not a candidate
+      cudaGetLastError();
+    }
+    if (rc != BSP_OK) break;
+    if (times_ms) times_ms[q] = ms_med;
+    if (ms_med >= 0 && (best < 0 || ms_med < best)) {
+      best = ms_med;
+      best_cs = cand[q];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  M->opts.cols_per_cta = rc == BSP_OK ? best_cs : keep;
+  if (chosen) *chosen = M->opts.cols_per_cta;
+  if (rc != BSP_OK) return rc;
+  g_err.clear();
+  return BSP_OK;
 }
 
 int bsp_oi_track_dynamic(bsp_mesh* M, const void* X, double rel_tol, int32_t c_min,

@@ -313,7 +313,7 @@ struct bsp_mesh {
   cudaEvent_t ev_fork = nullptr, ev_join[kSide] = {};
   // graph cache for the fixed-c schedule
   cudaGraphExec_t graph_exec = nullptr;
-  int graph_c = -1, graph_t = -1, graph_launches = 0;
+  int graph_c = -1, graph_t = -1, graph_launches = 0, graph_cs = -1;
   cudaStream_t graph_stream = nullptr;
   bsp_stats stats{};
   // low-pass filter checkpoints (last bsp_filter_forward)

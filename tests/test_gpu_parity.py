@@ -320,6 +320,23 @@ def test_batched_cg_dynamic_wide_wave():
         bsp.bsp_mesh_destroy(h)
 
 
+def test_autotune_keeps_a_candidate_and_parity():
+    """The autotuner times the CG layouts on the mesh and keeps the fastest; the
+    kept layout then tracks to the oracle's bases (fixed and dynamic c)."""
+    h, om, xyz, faces, ptr, verts, parent = _wide_wave_mesh(bsp.BSP_PREC_MIXED)
+    try:
+        c = 24
+        starts = synth.gaussian_starts(ptr, parent, c, seed=3)
+        chosen, times = bsp.bsp_autotune(h, c, 2, starts.astype(np.float32), reps=2)
+        assert chosen in (0, 2, 4, 8) and times[0] > 0 and times[chosen] > 0
+        assert all(t == -1 or t >= times[chosen] for t in times.values())
+        bsp.bsp_oi_track(h, c, 2, starts.astype(np.float32))
+        U_ref = O.oi_track(om, c, 2, starts, delta=1e-2)
+        compare_bases(h, om, U_ref, xyz, np.float32, SINE_F32, PROJ_F32)
+    finally:
+        bsp.bsp_mesh_destroy(h)
+
+
 def test_full_width_reconstructs_and_c1_gives_centroid():
     N = 16
     xyz, faces = synth.grid_heightfield(N, seed=7)
