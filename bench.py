@@ -422,6 +422,36 @@ def run_batched(args, device):
     errs = np.array([np.linalg.norm(Xon[verts[ptr[b]:ptr[b + 1]]] - xyz[verts[ptr[b]:ptr[b + 1]]]) /
                      np.linalg.norm(xyz[verts[ptr[b]:ptr[b + 1]]]) for b in range(k)])
     bsp.bsp_mesh_destroy(h)
+    # the same blocks and quality target, one block per launch: the blocks
+    # chained in index order (each warm-starts from the previous one), FP32
+    plain = None
+    if args.plain_baseline:
+        chain = np.arange(-1, k - 1, dtype=np.int32)
+        h1 = bsp.bsp_mesh_create(xyz, faces, ptr, verts, chain,
+                                 bsp.make_opts(precision=bsp.BSP_PREC_F32, cols_per_cta=1))
+        V1 = torch.tensor(synth.gaussian_starts(ptr, chain, 8, seed=0), dtype=torch.float32,
+                          device=device)
+        c1 = torch.empty(k, dtype=torch.int32, device=device)
+        flush.fill_(1.0)
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        bsp.bsp_oi_track_dynamic(h1, X, 2e-3, 8, 128, 8, args.t, 7, V1, None, c1, stream)
+        bsp.bsp_project(h1, X, bsp.BSP_DT_F32, 3, E, stream)
+        bsp.bsp_reconstruct(h1, E, 3, Xo, stream)
+        p1.record(stream)
+        p1.synchronize()
+        tp = p0.elapsed_time(p1) / 1e3
+        cp = c1.cpu().numpy()
+        Xp = Xo.cpu().double().numpy()
+        ep = np.array([np.linalg.norm(Xp[verts[ptr[b]:ptr[b + 1]]] - xyz[verts[ptr[b]:ptr[b + 1]]]) /
+                       np.linalg.norm(xyz[verts[ptr[b]:ptr[b + 1]]]) for b in range(k)])
+        plain = {"value": n / tp / 1e6, "unit": "Mvertices/s", "ms_per_step": 1e3 * tp,
+                 "how": "same blocks chained in index order (one block per launch), FP32, "
+                        "same dynamic-c target; one timed step",
+                 "c_mean": float(cp.mean()), "rel_err_max": float(ep.max()),
+                 "blocks_above_2e-3": int((ep > 2e-3 * (1 + 1e-6)).sum())}
+        bsp.bsp_mesh_destroy(h1)
     levels = np.zeros(k, int)
     for b in range(k):
         levels[b] = 0 if parent[b] < 0 else levels[parent[b]] + 1
@@ -440,6 +470,7 @@ def run_batched(args, device):
         "stats": {"cg_steps_total": st["cg_steps_total"], "cg_steps_max": st["cg_steps_max"],
                   "not_converged": st["not_converged"]},
         "autotune": {"cols_per_cta": chosen, "candidates_ms_fixed_c32": tt},
+        "plain_one_block_per_launch": plain,
     }
 
 
@@ -709,6 +740,8 @@ def main():
                          "filter: 262K-vertex noisy torus, differentiable low-pass forward+backward; "
                          "spmm: the operator product alone on the 1M-vertex torus")
     ap.add_argument("--roots", type=int, default=32, help="roots of the BFS warm-start forest")
+    ap.add_argument("--plain-baseline", type=int, default=1,
+                    help="batched: also time the same blocks one block per launch")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
