@@ -701,12 +701,12 @@ def run_frames(args, device):
                      "note": "API calls (each ends with a stream synchronise and a status read)"},
         "kernel_ms": {"k_project_tc": 1e3 * k_pbf, "k_recon_tc": 1e3 * k_rbf},
         "rel_err_vs_fp64_oracle_first4blocks": errs,
-        # traffic: dram__bytes_read.sum + dram__bytes_write.sum of one launch of the
-        # unchanged kernels (profiles/ncu_full_project_recon_tc_frames512x200_c48.md)
+        # traffic: dram__bytes_read.sum + dram__bytes_write.sum of one launch
+        # (profiles/ncu_full_project_recon_tc_frames512x200_c48.md)
         "roofline": {"kernel": "k_project_tc (tcgen05, BF16 X, all frames)", "bound": "hbm",
                      "achieved": bytes_pbf / k_pbf / 1e9, "peak": peak_hbm, "unit": "GB/s",
                      "peak_source": peak_kind, "frac": bytes_pbf / k_pbf / 1e9 / peak_hbm,
-                     "traffic": 364.9e6, "algorithmic_bytes": bytes_pbf, "avg_launch_s": k_pbf,
+                     "traffic": None, "algorithmic_bytes": bytes_pbf, "avg_launch_s": k_pbf,
                      "tensor_tflops": flops / k_pbf / 1e12},
         "roofline_reconstruct": {"kernel": "k_recon_tc", "bound": "hbm",
                                  "achieved": bytes_rbf / k_rbf / 1e9, "peak": peak_hbm,

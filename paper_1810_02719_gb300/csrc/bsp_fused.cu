@@ -275,6 +275,7 @@ BSP_DEV void panel_gram_split(const T* S, int rows, int cpad, int ldS, T* half, 
     while (u >= nt - ti) { u -= nt - ti; ++ti; }
     const int tj = ti + u;
     tiles[q] = (ti * nt + tj) * 2 + h;
+#pragma unroll 4
     for (int r = h * hr; r < (h + 1) * hr; ++r) {
       T a4[4], b4[4];
       ld4(S + r * ldS + 4 * ti, a4);

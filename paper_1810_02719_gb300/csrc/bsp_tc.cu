@@ -23,8 +23,8 @@ constexpr int kTT = 256;         // threads per CTA
 constexpr int kM = 128;          // MMA M (rows of D = TMEM lanes)
 constexpr int kKC = 32;          // projection K chunk per ring stage (2 MMAs of K = 16)
 constexpr long kSpin = 1L << 26; // bounded mbarrier wait (iterations)
-constexpr int kS = 8;            // projection ring depth
-constexpr int kD = 6;            // chunks in flight ahead of the MMAs (kS - 2)
+constexpr int kS = 6;            // projection ring depth
+constexpr int kD = 4;            // chunks in flight ahead of the MMAs (kS - 2)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -156,9 +156,9 @@ __global__ void k_coef_bf16(const float* __restrict__ E, __nv_bfloat16* __restri
 // A[m][k] = X[verts[r0 + k]][m0 + m] and B[n][k] = Ub[r0 + k][n], both
 // MN-major, so every 16-byte piece of a gathered X row (8 frame-columns) and
 // of a basis row (8 basis columns) is one asynchronous copy, no register
-// staging.  K runs over the block's vertices in chunks of 32 through an
-// 8-stage ring with 6 chunks in flight; stage reuse waits on the MMA commit
-// of the chunk that last read it.  Eight consecutive threads fill one core matrix (8 rows x 16 B,
+// staging.  K runs over the block's vertices in chunks of 32 through a
+// 6-stage ring with 4 chunks in flight (3 CTAs per SM); stage reuse waits on
+// the MMA commit of the chunk that last read it.  Eight consecutive threads fill one core matrix (8 rows x 16 B,
 // contiguous), so the shared-memory writes are conflict-free.
 __global__ void __launch_bounds__(kTT) k_project_tc(ProjArgs a, const __nv_bfloat16* __restrict__ Ub,
                                                     const __nv_bfloat16* __restrict__ X,
