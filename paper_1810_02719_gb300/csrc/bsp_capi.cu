@@ -179,18 +179,14 @@ void release(bsp_mesh* m) {
                   m->d_root_off, m->d_waves, m->d_cb, m->d_cpar, m->d_ceoff, m->d_col,
                   m->d_wt, m->d_diag, m->d_status, m->d_cgstats, m->d_U, m->d_Y, m->d_starts,
                   m->d_Gp, m->d_Rsm, m->d_theta, m->d_action, m->d_round, m->d_forced,
-                  m->d_gcol, m->d_rho, m->d_X, m->d_Gp_rr, m->d_Rsm_rr, m->d_ckV, m->d_ckY,
+                  m->d_gcol, m->d_rho, m->d_X, m->d_Gp_rr, m->d_Rsm_rr, m->d_theta_rr,
+                  m->d_ckV, m->d_ckY,
                   m->d_adj_gp, m->d_adj_thin, m->d_adj_rows, m->d_Ubf, m->d_Ebf,
                   m->d_spmm_chunks};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (m->graph_exec) cudaGraphExecDestroy(m->graph_exec);
   if (m->graph_stream) cudaStreamDestroy(m->graph_stream);
-  for (int i = 0; i < bsp_mesh::kSide; ++i) {
-    if (m->side_stream[i]) cudaStreamDestroy(m->side_stream[i]);
-    if (m->ev_join[i]) cudaEventDestroy(m->ev_join[i]);
-  }
-  if (m->ev_fork) cudaEventDestroy(m->ev_fork);
 }
 
 int stream_error_status(bsp_mesh* m, cudaStream_t s) {
@@ -435,24 +431,8 @@ int ensure_workspace(bsp_mesh* M, int c_cap, int maxbatch) {
   if ((rc = ensure(&M->d_Gp, &M->cap_Gp, gp)) != BSP_OK) return rc;
   if ((rc = ensure(&M->d_Rsm, &M->cap_Rsm, (size_t)maxbatch * cpad * cpad * sizeof(T))) != BSP_OK)
     return rc;
-  if ((rc = ensure(&M->d_theta, &M->cap_theta,
-                   (size_t)bsp_mesh::kSide * maxbatch * cpad * sizeof(T))) != BSP_OK)
+  if ((rc = ensure(&M->d_theta, &M->cap_theta, (size_t)maxbatch * cpad * sizeof(T))) != BSP_OK)
     return rc;
-  const size_t gp_slice = (gp + 255) & ~(size_t)255;
-  const size_t rsm_slice = ((size_t)maxbatch * cpad * cpad * sizeof(T) + 255) & ~(size_t)255;
-  if ((rc = ensure(&M->d_Gp_rr, &M->cap_Gp_rr, gp_slice * bsp_mesh::kSide)) != BSP_OK) return rc;
-  if ((rc = ensure(&M->d_Rsm_rr, &M->cap_Rsm_rr, rsm_slice * bsp_mesh::kSide)) != BSP_OK) return rc;
-  M->gp_rr_slice = gp_slice;
-  M->rsm_rr_slice = rsm_slice;
-  for (int i = 0; i < bsp_mesh::kSide; ++i) {
-    if (!M->side_stream[i] &&
-        cudaStreamCreateWithFlags(&M->side_stream[i], cudaStreamNonBlocking) != cudaSuccess)
-      return fail(BSP_ERR_CUDA, "stream creation failed");
-    if (!M->ev_join[i] && cudaEventCreateWithFlags(&M->ev_join[i], cudaEventDisableTiming) != cudaSuccess)
-      return fail(BSP_ERR_CUDA, "event creation failed");
-  }
-  if (!M->ev_fork && cudaEventCreateWithFlags(&M->ev_fork, cudaEventDisableTiming) != cudaSuccess)
-    return fail(BSP_ERR_CUDA, "event creation failed");
   if ((M->c_cap != c_cap || g_realloc) && M->graph_exec) {
     cudaGraphExecDestroy(M->graph_exec);
     M->graph_exec = nullptr;
@@ -461,24 +441,45 @@ int ensure_workspace(bsp_mesh* M, int c_cap, int maxbatch) {
   return BSP_OK;
 }
 
-// Rayleigh-Ritz of wave l on the side stream, ordered after everything
-// already enqueued on s.
+// Rayleigh-Ritz of the fixed-c schedule runs after the last wave over all
+// blocks: consecutive blocks of the wave order are grouped so that a group's
+// partial Grams stay within kRRBytes (a larger block forms a group alone).
+constexpr size_t kRRBytes = (size_t)512 << 20;
+
 template <typename T, typename TA>
-int fork_rr(bsp_mesh* M, int l, int c, cudaStream_t s, int* launches) {
-  int wmax = 0;
-  for (int b : M->waves[l]) wmax = std::max(wmax, M->h_bptr[b + 1] - M->h_bptr[b]);
-  DenseArgs da{M->d_waves + M->h_wave_off[l], (int)M->waves[l].size(), M->d_bptr, M->d_cb,
-               M->c_cap, c, wmax, M->d_status};
-  da.sweeps = &M->d_cgstats->jacobi_sweeps;
-  const int si = l % bsp_mesh::kSide;   // waves round-robin over the side streams
-  cudaStream_t side = M->side_stream[si];
-  CU(cudaEventRecord(M->ev_fork, s));
-  CU(cudaStreamWaitEvent(side, M->ev_fork, 0));
-  int rc = launch_rayleigh_ritz<T, TA>(
-      da, view<T>(M), (T*)M->d_U, (TA*)((char*)M->d_Gp_rr + si * M->gp_rr_slice),
-      (T*)((char*)M->d_Rsm_rr + si * M->rsm_rr_slice),
-      (T*)M->d_theta + (size_t)si * (M->cap_theta / sizeof(T) / bsp_mesh::kSide), side, launches);
-  return rc ? fail(rc, "launch failed (Rayleigh-Ritz)") : BSP_OK;
+int ensure_rr_groups(bsp_mesh* M, int c) {
+  const int cpad = pad4(c);
+  const int CH = dense_chunk_rows(cpad, (int)sizeof(T));
+  const size_t mat = (size_t)cpad * cpad * sizeof(TA);
+  M->rr_group.assign(1, 0);
+  M->rr_wmax.clear();
+  size_t gp = 0;
+  int nmax = 0, wmax = 0;
+  for (int q = 0; q < M->k; ++q) {
+    const int b = M->h_wave_list[q];
+    const int w = std::max(wmax, M->h_bptr[b + 1] - M->h_bptr[b]);
+    const int n = q - M->rr_group.back() + 1;
+    const size_t bytes = (size_t)n * ((w + CH - 1) / CH + 1) * mat;
+    if (n > 1 && bytes > kRRBytes) {   // close the group before block q
+      M->rr_wmax.push_back(wmax);
+      M->rr_group.push_back(q);
+      wmax = M->h_bptr[b + 1] - M->h_bptr[b];
+      gp = std::max(gp, (size_t)((wmax + CH - 1) / CH + 1) * mat);
+      nmax = std::max(nmax, 1);
+      continue;
+    }
+    wmax = w;
+    gp = std::max(gp, bytes);
+    nmax = std::max(nmax, n);
+  }
+  M->rr_wmax.push_back(wmax);
+  M->rr_group.push_back(M->k);
+  int rc;
+  if ((rc = ensure(&M->d_Gp_rr, &M->cap_Gp_rr, gp)) != BSP_OK ||
+      (rc = ensure(&M->d_Rsm_rr, &M->cap_Rsm_rr, (size_t)nmax * cpad * cpad * sizeof(T))) != BSP_OK ||
+      (rc = ensure(&M->d_theta_rr, &M->cap_theta_rr, (size_t)nmax * cpad * sizeof(T))) != BSP_OK)
+    return rc;
+  return BSP_OK;
 }
 
 // Enqueue the fixed-c schedule on stream s; returns a status, counts launches.
@@ -510,11 +511,6 @@ int enqueue_fixed(bsp_mesh* M, int c, int t_max, cudaStream_t s, int* launches) 
       launch_init_starts<T>(batch, nbw, M->d_bptr, M->d_parent, M->d_root_off, M->d_cb, M->d_cb,
                             (const T*)M->d_starts, c, U, M->c_cap, wmax, c, s);
       ++*launches;
-      // Rayleigh-Ritz of the previous wave leaves the critical path here: the
-      // starts have been copied, and Rayleigh-Ritz does not change the spans
-      // that later waves depend on
-      if (l > 0 && M->opts.rayleigh_ritz && (rc = fork_rr<T, TA>(M, l - 1, c, s, launches)))
-        return rc;
     }
     DenseArgs da{batch, nbw, M->d_bptr, M->d_cb, M->c_cap, c, wmax, M->d_status};
     if (!need.empty()) {
@@ -555,22 +551,24 @@ int enqueue_fixed(bsp_mesh* M, int c, int t_max, cudaStream_t s, int* launches) 
                    : launch_cg<T>(mv, U, Y, cg, cs, wmax, c, s);
       if (rc) return fail(rc, "CG launch failed (block too large for shared memory?)");
       ++*launches;
-      // with in-place starts, Rayleigh-Ritz of the previous wave forks once the
-      // first solve has read its bases
-      if (t == 0 && in_place && M->opts.rayleigh_ritz &&
-          (rc = fork_rr<T, TA>(M, l - 1, c, s, launches)))
-        return rc;
       t += g;
       const int passes = t == sub ? 2 : 1;
       if ((rc = launch_cholqr2<T, TA>(da, Y, U, (TA*)M->d_Gp, (T*)M->d_Rsm, s, launches, passes)))
         return fail(rc, "launch failed (Onorm)");
     }
   }
-  if (M->opts.rayleigh_ritz && levels > 0) {
-    if ((rc = fork_rr<T, TA>(M, levels - 1, c, s, launches))) return rc;
-    for (int i = 0; i < bsp_mesh::kSide && i < levels; ++i) {   // join the side branches
-      CU(cudaEventRecord(M->ev_join[i], M->side_stream[i]));
-      CU(cudaStreamWaitEvent(s, M->ev_join[i], 0));
+  // Rayleigh-Ritz does not change the spans the chain depends on, and no
+  // later wave reads its rotation: it runs once after the last wave, batched
+  // over the groups of ensure_rr_groups().
+  if (M->opts.rayleigh_ritz) {
+    for (size_t g = 0; g + 1 < M->rr_group.size(); ++g) {
+      const int g0 = M->rr_group[g], nbg = M->rr_group[g + 1] - g0;
+      DenseArgs da{M->d_waves + g0, nbg, M->d_bptr, M->d_cb, M->c_cap, c, M->rr_wmax[g],
+                   M->d_status};
+      da.sweeps = &M->d_cgstats->jacobi_sweeps;
+      rc = launch_rayleigh_ritz<T, TA>(da, view<T>(M), U, (TA*)M->d_Gp_rr, (T*)M->d_Rsm_rr,
+                                       (T*)M->d_theta_rr, s, launches);
+      if (rc) return fail(rc, "launch failed (Rayleigh-Ritz)");
     }
   }
   return BSP_OK;
@@ -607,6 +605,7 @@ int track_fixed(bsp_mesh* M, int c, int t_max, const void* V0, cudaStream_t s) {
   g_realloc = false;
   if ((rc = ensure(&M->d_starts, &M->cap_starts, (size_t)M->root_rows * c * sizeof(T))) != BSP_OK)
     return rc;
+  if (M->opts.rayleigh_ritz && (rc = ensure_rr_groups<T, TA>(M, c)) != BSP_OK) return rc;
   if (g_realloc && M->graph_exec) {
     cudaGraphExecDestroy(M->graph_exec);
     M->graph_exec = nullptr;

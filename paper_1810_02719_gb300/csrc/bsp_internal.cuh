@@ -303,14 +303,13 @@ struct bsp_mesh {
   int spmm_nchunks = 0, spmm_max_span = 0, spmm_max_nnz = 0;
   void* d_Ebf = nullptr;   // BF16 copy of the coefficients of a reconstruction call
   size_t cap_Ebf = 0;
-  // Rayleigh-Ritz side branches: kSide streams used round-robin, each with its
-  // own workspace slice and join event
-  static constexpr int kSide = 8;
+  // Rayleigh-Ritz of the fixed-c schedule: block groups (offsets into the
+  // wave order, largest block of each) and their workspace
+  std::vector<int32_t> rr_group, rr_wmax;
   void* d_Gp_rr = nullptr;
   void* d_Rsm_rr = nullptr;
-  size_t cap_Gp_rr = 0, cap_Rsm_rr = 0, gp_rr_slice = 0, rsm_rr_slice = 0;
-  cudaStream_t side_stream[kSide] = {};
-  cudaEvent_t ev_fork = nullptr, ev_join[kSide] = {};
+  void* d_theta_rr = nullptr;
+  size_t cap_Gp_rr = 0, cap_Rsm_rr = 0, cap_theta_rr = 0;
   // graph cache for the fixed-c schedule
   cudaGraphExec_t graph_exec = nullptr;
   int graph_c = -1, graph_t = -1, graph_launches = 0, graph_cs = -1;
