@@ -298,6 +298,106 @@ def reconstruct(mesh: Mesh, U: List[np.ndarray], E: List[np.ndarray], m: int) ->
 
 
 # ---------------------------------------------------------------------------
+# Sec. 7.1: compression (uniform quantisation of the coefficients, bits per
+# vertex, NMSVE)
+# ---------------------------------------------------------------------------
+
+def quantize(E: List[np.ndarray], bits: int):
+    """Uniform scalar quantisation of every block's coefficients to ``bits`` bits (Sec. 7.1).
+
+    The paper gives the bit count (q_c = 12) but not the range.  Reading: each
+    column of each block E[b] (c_b x cols) is coded over its own range
+    [lo, hi] = [min, max], kept as side information; with q = 2^bits - 1,
+    s = q / (hi - lo) and code = clip(rint((e - lo) s), 0, q), rint rounding
+    half to even; s = 0 when hi == lo or when s is not finite.  The codes are
+    integers decided by floating point, so the arithmetic runs in the
+    coefficients' own dtype (float32 for float32 E), one rounding per
+    operation, as the kernel does.
+
+    Returns (codes, ranges): codes[b] uint16 (c_b x cols); ranges[b] (cols x 2).
+    """
+    codes, ranges = [], []
+    for Eb in E:
+        Eb = np.asarray(Eb)
+        t = Eb.dtype.type
+        qmax = t((1 << bits) - 1)
+        lo = Eb.min(axis=0)
+        hi = Eb.max(axis=0)
+        with np.errstate(divide="ignore", over="ignore", invalid="ignore"):
+            s = np.where(hi > lo, qmax / (hi - lo), t(0)).astype(Eb.dtype)
+        s = np.where(np.isfinite(s), s, t(0)).astype(Eb.dtype)
+        q = np.rint((Eb - lo) * s)
+        q = np.clip(q, t(0), qmax)
+        codes.append(q.astype(np.uint16))
+        ranges.append(np.stack([lo, hi], axis=1))
+    return codes, ranges
+
+
+def dequantize(codes: List[np.ndarray], ranges: List[np.ndarray], bits: int,
+               dtype=np.float32) -> List[np.ndarray]:
+    """Decoder of ``quantize`` (Sec. 7.1): e~ = lo + code (hi - lo) / q, in ``dtype``."""
+    out = []
+    t = np.dtype(dtype).type
+    qmax = t((1 << bits) - 1)
+    for Cb, Rb in zip(codes, ranges):
+        lo = Rb[:, 0].astype(dtype)
+        hi = Rb[:, 1].astype(dtype)
+        step = (hi - lo) / qmax
+        out.append(lo + Cb.astype(dtype) * step)
+    return out
+
+
+def bits_per_vertex(c_blocks, n: int, bits: int) -> float:
+    """Coefficient bits per vertex, 3 q_c c k / n_d of Sec. 7.1 with per-block c_b.
+
+    Counts the coded xyz coefficients only (no connectivity, no ranges), as
+    the paper does.
+    """
+    return 3.0 * bits * float(np.sum(c_blocks)) / n
+
+
+def geometric_laplacian(X: np.ndarray, faces: np.ndarray) -> np.ndarray:
+    """GL(v_i) = v_i - sum_j v_j / d_ij / sum_j 1 / d_ij over mesh neighbours (Sec. 7.1, NMSVE).
+
+    Neighbours come from the edges of all faces; d_ij is the edge length in
+    the geometry X itself.  Readings: a neighbour at distance 0 gets no
+    weight; a vertex with no weighted neighbour keeps GL = v_i.
+    """
+    X = np.asarray(X, dtype=np.float64)
+    n = X.shape[0]
+    E = undirected_edges(faces=faces)
+    num = np.zeros((n, 3))
+    den = np.zeros(n)
+    for a, b in E:
+        d = float(np.linalg.norm(X[a] - X[b]))
+        if d > 0.0:
+            num[a] += X[b] / d
+            den[a] += 1.0 / d
+            num[b] += X[a] / d
+            den[b] += 1.0 / d
+    GL = X.copy()
+    has = den > 0
+    GL[has] = X[has] - num[has] / den[has, None]
+    return GL
+
+
+def nmsve(X: np.ndarray, X_rec: np.ndarray, faces: np.ndarray):
+    """Normalised mean square visual error of Sec. 7.1.
+
+    (||v - v~|| + ||GL(v) - GL(v~)||) / (2 n) with v, v~ the 3n stacked
+    coordinates, norms as printed (unsquared), value linear (the paper's dB
+    label comes without a conversion).  Returns (nmsve, ||v - v~||,
+    ||GL(v) - GL(v~)||).
+    """
+    X = np.asarray(X, dtype=np.float64)
+    Xr = np.asarray(X_rec, dtype=np.float64)
+    n = X.shape[0]
+    a = float(np.linalg.norm(X - Xr))
+    g = float(np.linalg.norm(geometric_laplacian(X, faces) - geometric_laplacian(Xr, faces)))
+    return (a + g) / (2.0 * n), a, g
+
+
+# ---------------------------------------------------------------------------
 # Sec. 5: dynamic OI (reading: relative Frobenius residual, growth by c_step)
 # ---------------------------------------------------------------------------
 
