@@ -344,6 +344,68 @@ int bsp_autotune(bsp_mesh* mesh, int32_t c, int32_t t_max, const void* V0_roots,
  */
 int bsp_onorm_noalloc(const float* Y, float* Q, int32_t n, int32_t c, void* stream);
 
+/*
+ * Compression codec of the spectral coefficients (Sec. 7.1): every block's
+ * coefficients are coded with `bits` bits per value by a uniform scalar
+ * quantiser.  The paper fixes the bit count (q_c = 12) but not the range;
+ * here each (block, column) pair has its own range [lo, hi] = [min, max] of
+ * that column over the block's c_b coefficient rows, returned as side
+ * information:
+ *     s = (2^bits - 1) / (hi - lo),   code = clamp(rint((e - lo) s), 0, 2^bits - 1)
+ * with rint rounding half to even, every operation rounded on its own in the
+ * coefficients' precision (real), s = 0 (all codes 0) when hi = lo or when s
+ * overflows.  Codes for NaN coefficients are unspecified.
+ *   E       host or device real [sum_b c_b x cols], blocks concatenated in
+ *           order (the layout of bsp_project's output for the tracked c_b).
+ *   bits    1 .. 16.
+ *   codes   host or device uint16 [sum_b c_b x cols].
+ *   range   host or device real [k x cols x 2]: (lo, hi) of block b, column j
+ *           at index 2 (b cols + j).
+ * Errors: BSP_ERR_INVALID_ARG (no tracking call yet, bad cols or bits),
+ * BSP_ERR_OOM, BSP_ERR_CUDA.
+ */
+int bsp_quantize(bsp_mesh* mesh, const void* E, int32_t cols, int32_t bits, uint16_t* codes,
+                 void* range, void* stream);
+
+/*
+ * Inverse of bsp_quantize (the decoder of Sec. 7.1):
+ *     e~ = lo + code (hi - lo) / (2^bits - 1)
+ * each operation rounded on its own in real precision.
+ *   codes, range   as written by bsp_quantize (host or device).
+ *   E_out          host or device real [sum_b c_b x cols].
+ */
+int bsp_dequantize(bsp_mesh* mesh, const uint16_t* codes, const void* range, int32_t cols,
+                   int32_t bits, void* E_out, void* stream);
+
+/*
+ * Bits per vertex of the coefficient stream for xyz coordinates (Sec. 7.1):
+ * bpv = 3 bits (sum_b c_b) / n, the paper's 3 q_c c k / n with the tracked
+ * c_b of every block; like the paper, it leaves out the connectivity and the
+ * quantiser ranges (side information of 2 k reals per coordinate).
+ */
+int bsp_bits_per_vertex(const bsp_mesh* mesh, int32_t bits, double* bpv);
+
+/*
+ * Normalised mean square visual error between a mesh and its reconstruction
+ * (Sec. 7.1, the NMSVE formula; mesh-wide, independent of any partition):
+ *     out[0] = (out[1] + out[2]) / (2 n)
+ *     out[1] = ||v - v~||            over all 3 n coordinates
+ *     out[2] = ||GL(v) - GL(v~)||    GL(v)_i = v_i - sum_j v_j / d_ij / sum_j 1 / d_ij
+ * with j over the distinct mesh neighbours of vertex i (edges of all faces)
+ * and d_ij the edge length in the geometry GL is applied to; neighbours at
+ * distance 0 get no weight, and a vertex without weighted neighbours has
+ * GL(v)_i = v_i.  The paper prints the norms unsquared and the result in dB
+ * without a conversion; the value here is the formula as printed, linear.
+ * Accumulated in FP64 on the device.
+ *   X, X_rec   host or device [n x 3] of `dtype` (BSP_DT_F32 or BSP_DT_F64).
+ *   faces      host or device int32 [m x 3], vertex ids in [0, n).
+ *   out        host double [3].
+ * Errors: BSP_ERR_INVALID_ARG (face index out of range, bad sizes or dtype),
+ * BSP_ERR_OOM, BSP_ERR_CUDA.  Allocates its own scratch and synchronises.
+ */
+int bsp_nmsve(const void* X, const void* X_rec, int32_t dtype, int64_t n, const int32_t* faces,
+              int64_t m, double* out, void* stream);
+
 /* Thread-local message describing the last failure on this thread ("" if none). */
 const char* bsp_last_error(void);
 

@@ -85,6 +85,10 @@ def _load():
         "bsp_filter_backward": (C.c_int, [P, P, P, P, P, P]),
         "bsp_reconstruct_bf16": (C.c_int, [P, P, I32, P, P]),
         "bsp_autotune": (C.c_int, [P, I32, I32, P, I32, P, C.POINTER(I32), P]),
+        "bsp_quantize": (C.c_int, [P, P, I32, I32, P, P, P]),
+        "bsp_dequantize": (C.c_int, [P, P, P, I32, I32, P, P]),
+        "bsp_bits_per_vertex": (C.c_int, [P, I32, C.POINTER(D)]),
+        "bsp_nmsve": (C.c_int, [P, P, I32, I64, P, I64, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -105,7 +109,8 @@ def exported_symbols():
             "bsp_project", "bsp_reconstruct", "bsp_spmm", "bsp_last_error",
             "bsp_set_profiling", "bsp_get_kernel_times", "bsp_onorm_noalloc",
             "bsp_filter_forward", "bsp_filter_backward", "bsp_reconstruct_bf16",
-            "bsp_autotune"]
+            "bsp_autotune", "bsp_quantize", "bsp_dequantize", "bsp_bits_per_vertex",
+            "bsp_nmsve"]
 
 
 def _check(code):
@@ -273,6 +278,32 @@ def bsp_reconstruct(mesh, E, cols, X_out, stream=None):
 
 def bsp_reconstruct_bf16(mesh, E, cols, X_out, stream=None):
     _check(_lib.bsp_reconstruct_bf16(mesh, _ptr(E), cols, _ptr(X_out), _stream_ptr(stream)))
+
+
+def bsp_quantize(mesh, E, cols, bits, codes, rng, stream=None):
+    """codes (uint16 [sum c_b x cols]) and ranges (real [k x cols x 2]) of E."""
+    _check(_lib.bsp_quantize(mesh, _ptr(E), cols, bits, _ptr(codes), _ptr(rng),
+                             _stream_ptr(stream)))
+
+
+def bsp_dequantize(mesh, codes, rng, cols, bits, E_out, stream=None):
+    _check(_lib.bsp_dequantize(mesh, _ptr(codes), _ptr(rng), cols, bits, _ptr(E_out),
+                               _stream_ptr(stream)))
+
+
+def bsp_bits_per_vertex(mesh, bits) -> float:
+    out = C.c_double()
+    _check(_lib.bsp_bits_per_vertex(mesh, bits, C.byref(out)))
+    return out.value
+
+
+def bsp_nmsve(X, X_rec, dtype, n, faces, m, stream=None):
+    """(NMSVE, ||v - v~||, ||GL(v) - GL(v~)||) of two n x 3 coordinate arrays."""
+    out = np.zeros(3, np.float64)
+    faces = _i32(faces)
+    _check(_lib.bsp_nmsve(_ptr(X), _ptr(X_rec), dtype, n, _ptr(faces), m, _ptr(out),
+                          _stream_ptr(stream)))
+    return float(out[0]), float(out[1]), float(out[2])
 
 
 def bsp_spmm(mesh, P, Y, c, stream=None):

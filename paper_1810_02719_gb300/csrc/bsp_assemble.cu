@@ -97,6 +97,8 @@ __global__ void k_scan_add(int32_t* out, const long long* tsum, int64_t n, const
   }
 }
 
+}  // namespace
+
 // out[0..n] = exclusive scan of in[0..n-1]; out[n] = total.  Returns the total on the host.
 int exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int* d_status, cudaStream_t s,
                    long long* h_total) {
@@ -113,6 +115,8 @@ int exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int* d_status, cu
   cudaFree(tmp);
   return e == cudaSuccess ? BSP_OK : BSP_ERR_CUDA;
 }
+
+namespace {
 
 __global__ void k_rows(int32_t k, const int32_t* bptr, int32_t* blk_row) {
   int b = blockIdx.x;

@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -1476,6 +1477,175 @@ int bsp_get_kernel_times(const bsp_mesh* M, double* ms_out, int32_t* launches_ou
     if (ms_out) ms_out[c] = M->prof_ms[c];
     if (launches_out) launches_out[c] = M->prof_n[c];
   }
+  return BSP_OK;
+}
+
+int bsp_quantize(bsp_mesh* M, const void* E, int32_t cols, int32_t bits, uint16_t* codes,
+                 void* range, void* stream) {
+  g_err.clear();
+  if (!M || !E || !codes || !range) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
+  if (!M->tracked) return fail(BSP_ERR_INVALID_ARG, "no tracking call yet");
+  if (cols < 1) return fail(BSP_ERR_INVALID_ARG, "cols must be >= 1");
+  if (bits < 1 || bits > 16) return fail(BSP_ERR_INVALID_ARG, "bits must be in [1, 16]");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int rb = M->real_bytes;
+  int64_t erows = 0;
+  for (int b = 0; b < M->k; ++b) erows += M->h_c[b];
+  const size_t ne = (size_t)erows * cols, nr = (size_t)M->k * cols * 2;
+  int rc;
+  const void* dE = E;
+  if (!is_device_ptr(E)) {
+    void* t;
+    if ((rc = scratch(0, ne * rb, &t))) return rc;
+    CU(cudaMemcpyAsync(t, E, ne * rb, cudaMemcpyHostToDevice, s));
+    dE = t;
+  }
+  void* dC = codes;
+  const bool host_codes = !is_device_ptr(codes);
+  if (host_codes && (rc = scratch(1, ne * sizeof(uint16_t), &dC))) return rc;
+  void* dR = range;
+  const bool host_range = !is_device_ptr(range);
+  if (host_range && (rc = scratch(2, nr * rb, &dR))) return rc;
+  rc = rb == 8 ? launch_quantize<double>(M->d_ceoff, M->k, (const double*)dE, cols, bits,
+                                         (uint16_t*)dC, (double*)dR, s)
+               : launch_quantize<float>(M->d_ceoff, M->k, (const float*)dE, cols, bits,
+                                        (uint16_t*)dC, (float*)dR, s);
+  if (rc) return fail(rc, "quantiser launch failed");
+  if (host_codes) CU(cudaMemcpyAsync(codes, dC, ne * sizeof(uint16_t), cudaMemcpyDeviceToHost, s));
+  if (host_range) CU(cudaMemcpyAsync(range, dR, nr * rb, cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  M->stats.gpu_launches = 1;
+  return BSP_OK;
+}
+
+int bsp_dequantize(bsp_mesh* M, const uint16_t* codes, const void* range, int32_t cols,
+                   int32_t bits, void* E_out, void* stream) {
+  g_err.clear();
+  if (!M || !codes || !range || !E_out) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
+  if (!M->tracked) return fail(BSP_ERR_INVALID_ARG, "no tracking call yet");
+  if (cols < 1) return fail(BSP_ERR_INVALID_ARG, "cols must be >= 1");
+  if (bits < 1 || bits > 16) return fail(BSP_ERR_INVALID_ARG, "bits must be in [1, 16]");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int rb = M->real_bytes;
+  int64_t erows = 0;
+  for (int b = 0; b < M->k; ++b) erows += M->h_c[b];
+  const size_t ne = (size_t)erows * cols, nr = (size_t)M->k * cols * 2;
+  int rc;
+  const void* dC = codes;
+  if (!is_device_ptr(codes)) {
+    void* t;
+    if ((rc = scratch(0, ne * sizeof(uint16_t), &t))) return rc;
+    CU(cudaMemcpyAsync(t, codes, ne * sizeof(uint16_t), cudaMemcpyHostToDevice, s));
+    dC = t;
+  }
+  const void* dR = range;
+  if (!is_device_ptr(range)) {
+    void* t;
+    if ((rc = scratch(2, nr * rb, &t))) return rc;
+    CU(cudaMemcpyAsync(t, range, nr * rb, cudaMemcpyHostToDevice, s));
+    dR = t;
+  }
+  void* dE = E_out;
+  const bool host_out = !is_device_ptr(E_out);
+  if (host_out && (rc = scratch(1, ne * rb, &dE))) return rc;
+  rc = rb == 8 ? launch_dequantize<double>(M->d_ceoff, M->k, (const uint16_t*)dC,
+                                           (const double*)dR, cols, bits, (double*)dE, s)
+               : launch_dequantize<float>(M->d_ceoff, M->k, (const uint16_t*)dC,
+                                          (const float*)dR, cols, bits, (float*)dE, s);
+  if (rc) return fail(rc, "dequantiser launch failed");
+  if (host_out) CU(cudaMemcpyAsync(E_out, dE, ne * rb, cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  M->stats.gpu_launches = 1;
+  return BSP_OK;
+}
+
+int bsp_bits_per_vertex(const bsp_mesh* M, int32_t bits, double* bpv) {
+  g_err.clear();
+  if (!M || !bpv) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
+  if (!M->tracked) return fail(BSP_ERR_INVALID_ARG, "no tracking call yet");
+  if (bits < 1 || bits > 16) return fail(BSP_ERR_INVALID_ARG, "bits must be in [1, 16]");
+  int64_t csum = 0;
+  for (int b = 0; b < M->k; ++b) csum += M->h_c[b];
+  *bpv = 3.0 * bits * (double)csum / (double)M->n;
+  return BSP_OK;
+}
+
+int bsp_nmsve(const void* X, const void* X_rec, int32_t dtype, int64_t n, const int32_t* faces,
+              int64_t m, double* out, void* stream) {
+  g_err.clear();
+  if (!X || !X_rec || !out || (m > 0 && !faces)) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
+  if (n < 1 || n >= INT32_MAX || m < 0 || m > INT32_MAX / 2)
+    return fail(BSP_ERR_INVALID_ARG, "n or m out of range");
+  if (dtype != BSP_DT_F32 && dtype != BSP_DT_F64)
+    return fail(BSP_ERR_INVALID_ARG, "dtype must be BSP_DT_F32 or BSP_DT_F64");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t xb = dtype == BSP_DT_F64 ? 8 : 4;
+  struct Bufs {
+    std::vector<void*> p;
+    ~Bufs() {
+      for (void* q : p) cudaFree(q);
+    }
+    void* get(size_t bytes) {
+      void* q = nullptr;
+      if (cudaMalloc(&q, bytes ? bytes : 16) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+      }
+      p.push_back(q);
+      return q;
+    }
+  } bufs;
+  const void* dX = X;
+  const void* dXr = X_rec;
+  const int32_t* dF = faces;
+  if (!is_device_ptr(X)) {
+    void* t = bufs.get((size_t)n * 3 * xb);
+    if (!t) return fail(BSP_ERR_OOM, "device allocation failed");
+    CU(cudaMemcpyAsync(t, X, (size_t)n * 3 * xb, cudaMemcpyHostToDevice, s));
+    dX = t;
+  }
+  if (!is_device_ptr(X_rec)) {
+    void* t = bufs.get((size_t)n * 3 * xb);
+    if (!t) return fail(BSP_ERR_OOM, "device allocation failed");
+    CU(cudaMemcpyAsync(t, X_rec, (size_t)n * 3 * xb, cudaMemcpyHostToDevice, s));
+    dXr = t;
+  }
+  if (m > 0 && !is_device_ptr(faces)) {
+    void* t = bufs.get((size_t)m * 3 * sizeof(int32_t));
+    if (!t) return fail(BSP_ERR_OOM, "device allocation failed");
+    CU(cudaMemcpyAsync(t, faces, (size_t)m * 3 * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    dF = (const int32_t*)t;
+  }
+  // [status, pad] [acc0, acc1] then cnt, off, cur: n + 1 ints each
+  char* w = (char*)bufs.get(32 + 3 * (size_t)(n + 1) * sizeof(int32_t));
+  if (!w) return fail(BSP_ERR_OOM, "device allocation failed");
+  int* d_status = (int*)w;
+  double* d_acc = (double*)(w + 16);
+  int32_t* cnt = (int32_t*)(w + 32);
+  int32_t* off = cnt + (n + 1);
+  int32_t* cur = off + (n + 1);
+  CU(cudaMemsetAsync(w, 0, 32 + 3 * (size_t)(n + 1) * sizeof(int32_t), s));
+  if (m > 0) launch_nm_count(m, dF, n, cnt, d_status, s);
+  long long total = 0;
+  int rc = exclusive_scan(cnt, off, n, d_status, s, &total);
+  if (rc) return fail(rc, "scan failed");
+  int st = 0;
+  CU(cudaMemcpy(&st, d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st & ST_BAD_INDEX) return fail(BSP_ERR_INVALID_ARG, "face vertex index out of range");
+  if (st) return fail(BSP_ERR_INVALID_ARG, "too many neighbour entries");
+  int32_t* nbr = (int32_t*)bufs.get((size_t)(total > 0 ? total : 1) * sizeof(int32_t));
+  if (!nbr) return fail(BSP_ERR_OOM, "device allocation failed");
+  if (m > 0) launch_nm_fill(m, dF, n, off, cur, nbr, s);
+  rc = dtype == BSP_DT_F64
+           ? launch_nm_err<double>(n, off, nbr, (const double*)dX, (const double*)dXr, d_acc, s)
+           : launch_nm_err<float>(n, off, nbr, (const float*)dX, (const float*)dXr, d_acc, s);
+  if (rc) return fail(rc, "NMSVE launch failed");
+  double acc[2];
+  CU(cudaMemcpyAsync(acc, d_acc, sizeof(acc), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  out[1] = std::sqrt(acc[0]);
+  out[2] = std::sqrt(acc[1]);
+  out[0] = (out[1] + out[2]) / (2.0 * (double)n);
   return BSP_OK;
 }
 

@@ -113,6 +113,10 @@ struct AssemblyOut {
 int assemble_pattern(int64_t n, const int32_t* d_tri, int64_t m, int arity,
                      const int32_t* d_bptr, const int32_t* d_verts, int32_t k,
                      AssemblyOut* out, int* d_status, cudaStream_t s, std::string* err);
+// out[0..n] = exclusive scan of in[0..n-1], out[n] = total (also returned on
+// the host); synchronises s.
+int exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int* d_status, cudaStream_t s,
+                   long long* h_total);
 template <typename T>
 void launch_weights(int64_t n, const int32_t* bptr, const int32_t* blk_row, const int32_t* verts,
                     const int32_t* rowptr, const uint16_t* col, const double* xyz, int mode,
@@ -216,6 +220,22 @@ template <typename T>
 int launch_spmm_tiled(const MeshView<T>& mv, const int32_t* blk_row, const int32_t* chunks,
                       int nchunks, int max_span, int max_nnz, T delta, const T* P, T* Y, int c,
                       cudaStream_t s);
+
+// Coefficient quantiser and NMSVE (bsp_codec.cu).  ceoff: [k + 1] row offsets
+// of the blocks' coefficients; range: [k x cols x 2] (lo, hi).
+template <typename T>
+int launch_quantize(const int32_t* ceoff, int k, const T* E, int cols, int bits, uint16_t* codes,
+                    T* range, cudaStream_t s);
+template <typename T>
+int launch_dequantize(const int32_t* ceoff, int k, const uint16_t* codes, const T* range, int cols,
+                      int bits, T* E, cudaStream_t s);
+void launch_nm_count(int64_t m, const int32_t* faces, int64_t n, int32_t* cnt, int* status,
+                     cudaStream_t s);
+void launch_nm_fill(int64_t m, const int32_t* faces, int64_t n, const int32_t* off, int32_t* cur,
+                    int32_t* nbr, cudaStream_t s);
+template <typename T>
+int launch_nm_err(int64_t n, const int32_t* off, const int32_t* nbr, const T* X, const T* Xr,
+                  double* acc, cudaStream_t s);
 
 // Start matrices and dynamic-c helpers (bsp_dyn.cu)
 template <typename T>
