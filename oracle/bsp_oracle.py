@@ -25,9 +25,13 @@ or a documented choice here):
   * Rayleigh-Ritz (optional, not in the paper): H = V^T L V, ascending Ritz order.
   * dynamic c: relative Frobenius residual, growth by c_step columns
     [e/||e||, counter-hash columns], see ``oi_track_dynamic``.
+  * codec (Sec. 7.1): a uniform quantiser per block and coefficient column
+    over [min, max]; NMSVE as printed (unsquared norms, linear value), GL with
+    each geometry's own edge lengths, see ``quantize`` and ``nmsve``.
 
 Parity status: every function here is pinned by tests in
-``tests/test_oracle_pins.py`` against closed forms, invariants or brute force.
+``tests/test_oracle_pins.py`` and ``tests/test_oracle_codec_pins.py`` against
+closed forms, invariants, hand-worked examples or brute force.
 """
 from __future__ import annotations
 
