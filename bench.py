@@ -279,8 +279,8 @@ def run_ours(args, rank, world, device):
                  "traffic": 516.4e6, "algorithmic_bytes": alg_bytes,
                  "avg_launch_s": t_spmm}
 
-    # compression codec of Sec. 7.1 on this workload (outside the timed step):
-    # 12-bit coefficients, bits per vertex, NMSVE of the decoded mesh
+    # compression codec of Sec. 7.1 on this workload (outside the timed step),
+    # evaluated as Sec. 8 does: 12-bit coefficients, bits per vertex, NMSVE
     codes = torch.empty(E.shape, dtype=torch.int16, device=device)
     rngq = torch.empty((k, 3, 2), dtype=torch.float32, device=device)
     Eq = torch.empty_like(E)

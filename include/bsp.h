@@ -345,7 +345,8 @@ int bsp_autotune(bsp_mesh* mesh, int32_t c, int32_t t_max, const void* V0_roots,
 int bsp_onorm_noalloc(const float* Y, float* Q, int32_t n, int32_t c, void* stream);
 
 /*
- * Compression codec of the spectral coefficients (Sec. 7.1): every block's
+ * Compression codec of the spectral coefficients (Sec. 7.1; quantisation and
+ * bit count as Sec. 8 evaluates it): every block's
  * coefficients are coded with `bits` bits per value by a uniform scalar
  * quantiser.  The paper fixes the bit count (q_c = 12) but not the range;
  * here each (block, column) pair has its own range [lo, hi] = [min, max] of
@@ -378,7 +379,7 @@ int bsp_dequantize(bsp_mesh* mesh, const uint16_t* codes, const void* range, int
                    int32_t bits, void* E_out, void* stream);
 
 /*
- * Bits per vertex of the coefficient stream for xyz coordinates (Sec. 7.1):
+ * Bits per vertex of the coefficient stream for xyz coordinates (Sec. 8):
  * bpv = 3 bits (sum_b c_b) / n, the paper's 3 q_c c k / n with the tracked
  * c_b of every block; like the paper, it leaves out the connectivity and the
  * quantiser ranges (side information of 2 k reals per coordinate).
@@ -387,7 +388,7 @@ int bsp_bits_per_vertex(const bsp_mesh* mesh, int32_t bits, double* bpv);
 
 /*
  * Normalised mean square visual error between a mesh and its reconstruction
- * (Sec. 7.1, the NMSVE formula; mesh-wide, independent of any partition):
+ * (Sec. 8, the NMSVE formula; mesh-wide, independent of any partition):
  *     out[0] = (out[1] + out[2]) / (2 n)
  *     out[1] = ||v - v~||            over all 3 n coordinates
  *     out[2] = ||GL(v) - GL(v~)||    GL(v)_i = v_i - sum_j v_j / d_ij / sum_j 1 / d_ij

@@ -25,12 +25,16 @@ or a documented choice here):
   * Rayleigh-Ritz (optional, not in the paper): H = V^T L V, ascending Ritz order.
   * dynamic c: relative Frobenius residual, growth by c_step columns
     [e/||e||, counter-hash columns], see ``oi_track_dynamic``.
-  * codec (Sec. 7.1): a uniform quantiser per block and coefficient column
+  * codec (Sec. 7.1, Sec. 8): a uniform quantiser per block and coefficient column
     over [min, max]; NMSVE as printed (unsquared norms, linear value), GL with
     each geometry's own edge lengths, see ``quantize`` and ``nmsve``.
+  * fine denoising (Sec. 7.2): face neighbourhood = faces sharing a vertex;
+    normals filtered with the input's centroids and areas, see
+    ``bilateral_normals``, ``fit_vertices`` and ``normal_angle_error``.
 
 Parity status: every function here is pinned by tests in
-``tests/test_oracle_pins.py`` and ``tests/test_oracle_codec_pins.py`` against
+``tests/test_oracle_pins.py``, ``tests/test_oracle_codec_pins.py`` and
+``tests/test_oracle_denoise_pins.py`` against
 closed forms, invariants, hand-worked examples or brute force.
 """
 from __future__ import annotations
@@ -302,12 +306,12 @@ def reconstruct(mesh: Mesh, U: List[np.ndarray], E: List[np.ndarray], m: int) ->
 
 
 # ---------------------------------------------------------------------------
-# Sec. 7.1: compression (uniform quantisation of the coefficients, bits per
-# vertex, NMSVE)
+# Sec. 7.1 compression, with the quantisation, bits per vertex and NMSVE of
+# Sec. 8's evaluation
 # ---------------------------------------------------------------------------
 
 def quantize(E: List[np.ndarray], bits: int):
-    """Uniform scalar quantisation of every block's coefficients to ``bits`` bits (Sec. 7.1).
+    """Uniform scalar quantisation of every block's coefficients to ``bits`` bits (Sec. 7.1, Sec. 8).
 
     The paper gives the bit count (q_c = 12) but not the range.  Reading: each
     column of each block E[b] (c_b x cols) is coded over its own range
@@ -352,7 +356,7 @@ def dequantize(codes: List[np.ndarray], ranges: List[np.ndarray], bits: int,
 
 
 def bits_per_vertex(c_blocks, n: int, bits: int) -> float:
-    """Coefficient bits per vertex, 3 q_c c k / n_d of Sec. 7.1 with per-block c_b.
+    """Coefficient bits per vertex, 3 q_c c k / n_d of Sec. 8 with per-block c_b.
 
     Counts the coded xyz coefficients only (no connectivity, no ranges), as
     the paper does.
@@ -361,7 +365,7 @@ def bits_per_vertex(c_blocks, n: int, bits: int) -> float:
 
 
 def geometric_laplacian(X: np.ndarray, faces: np.ndarray) -> np.ndarray:
-    """GL(v_i) = v_i - sum_j v_j / d_ij / sum_j 1 / d_ij over mesh neighbours (Sec. 7.1, NMSVE).
+    """GL(v_i) = v_i - sum_j v_j / d_ij / sum_j 1 / d_ij over mesh neighbours (Sec. 8, NMSVE).
 
     Neighbours come from the edges of all faces; d_ij is the edge length in
     the geometry X itself.  Readings: a neighbour at distance 0 gets no
@@ -386,7 +390,7 @@ def geometric_laplacian(X: np.ndarray, faces: np.ndarray) -> np.ndarray:
 
 
 def nmsve(X: np.ndarray, X_rec: np.ndarray, faces: np.ndarray):
-    """Normalised mean square visual error of Sec. 7.1.
+    """Normalised mean square visual error of Sec. 8.
 
     (||v - v~|| + ||GL(v) - GL(v~)||) / (2 n) with v, v~ the 3n stacked
     coordinates, norms as printed (unsquared), value linear (the paper's dB
@@ -399,6 +403,122 @@ def nmsve(X: np.ndarray, X_rec: np.ndarray, faces: np.ndarray):
     a = float(np.linalg.norm(X - Xr))
     g = float(np.linalg.norm(geometric_laplacian(X, faces) - geometric_laplacian(Xr, faces)))
     return (a + g) / (2.0 * n), a, g
+
+
+# ---------------------------------------------------------------------------
+# Sec. 7.2: fine denoising after the coarse spectral step (bilateral filter of
+# the face normals, then vertex positions fitted to the filtered normals)
+# ---------------------------------------------------------------------------
+
+def face_geometry(X: np.ndarray, faces: np.ndarray):
+    """Unit normals, centroids and areas of the faces (Sec. 7.2, face normal equation).
+
+    n_i = (v2 - v1) x (v3 - v1) / ||(v2 - v1) x (v3 - v1)||, m_i the centroid,
+    A_i = ||(v2 - v1) x (v3 - v1)|| / 2.  Reading: a degenerate face (zero
+    cross product) gets the zero vector as its normal and area 0.
+    """
+    X = np.asarray(X, dtype=np.float64)
+    f = np.asarray(faces, dtype=np.int64).reshape(-1, 3)
+    cr = np.cross(X[f[:, 1]] - X[f[:, 0]], X[f[:, 2]] - X[f[:, 0]])
+    ln = np.linalg.norm(cr, axis=1)
+    nrm = np.zeros_like(cr)
+    ok = ln > 0
+    nrm[ok] = cr[ok] / ln[ok, None]
+    cen = (X[f[:, 0]] + X[f[:, 1]] + X[f[:, 2]]) / 3.0
+    return nrm, cen, 0.5 * ln
+
+
+def vertex_faces(faces: np.ndarray, n: int) -> List[np.ndarray]:
+    """Index set F_v of the faces incident to every vertex (Sec. 7.2)."""
+    f = np.asarray(faces, dtype=np.int64).reshape(-1, 3)
+    lists = [[] for _ in range(n)]
+    for i, tri in enumerate(f):
+        for v in set(tri.tolist()):
+            lists[v].append(i)
+    return [np.array(sorted(l), dtype=np.int64) for l in lists]
+
+
+def face_rings(faces: np.ndarray, n: int) -> List[np.ndarray]:
+    """Neighbourhood N(f_i) of every face for the bilateral filter (Sec. 7.2).
+
+    Reading (the paper leaves it open): the faces that share at least one
+    vertex with f_i, f_i included.
+    """
+    f = np.asarray(faces, dtype=np.int64).reshape(-1, 3)
+    vf = vertex_faces(f, n)
+    return [np.unique(np.concatenate([vf[v] for v in tri])) for tri in f]
+
+
+def bilateral_normals(X: np.ndarray, faces: np.ndarray, sigma_s: float, sigma_r: float,
+                      iters: int) -> np.ndarray:
+    """Bilateral filter of the face normals (Sec. 7.2, Eqs. BF, Wm, Wn), ``iters`` times.
+
+    n_i <- normalise( sum_{j in N(f_i)} A_j K_s(m_i, m_j) K_r(n_i, n_j) n_j ),
+    K_s = exp(-||m_i - m_j||^2 / (2 sigma_s^2)), K_r = exp(-||n_i - n_j||^2 /
+    (2 sigma_r^2)); W_i is the normalisation.  Readings: centroids and areas
+    stay those of X (the filter moves no vertex); each pass filters the
+    previous pass's normals; a face whose weighted sum vanishes keeps its
+    normal.
+    """
+    X = np.asarray(X, dtype=np.float64)
+    nrm, cen, area = face_geometry(X, faces)
+    rings = face_rings(faces, X.shape[0])
+    for _ in range(iters):
+        new = nrm.copy()
+        for i, J in enumerate(rings):
+            ks = np.exp(-np.sum((cen[i] - cen[J]) ** 2, axis=1) / (2.0 * sigma_s ** 2))
+            kr = np.exp(-np.sum((nrm[i] - nrm[J]) ** 2, axis=1) / (2.0 * sigma_r ** 2))
+            acc = np.sum((area[J] * ks * kr)[:, None] * nrm[J], axis=0)
+            ln = np.linalg.norm(acc)
+            if ln > 0:
+                new[i] = acc / ln
+        nrm = new
+    return nrm
+
+
+def fit_vertices(X: np.ndarray, faces: np.ndarray, normals: np.ndarray, iters: int) -> np.ndarray:
+    """Vertex update to match the filtered normals (Sec. 7.2, Eqs. iter1 and iter2), ``iters`` times.
+
+    v <- v + (1 / |F_v|) sum_{z in F_v} n_z [n_z^T (m_z - v)], with m_z the
+    centroid of face z at the current positions; every vertex moves from the
+    previous iterate's positions.  A vertex in no face stays.
+    """
+    X = np.asarray(X, dtype=np.float64).copy()
+    f = np.asarray(faces, dtype=np.int64).reshape(-1, 3)
+    vf = vertex_faces(f, X.shape[0])
+    for _ in range(iters):
+        cen = (X[f[:, 0]] + X[f[:, 1]] + X[f[:, 2]]) / 3.0
+        Xn = X.copy()
+        for v, F in enumerate(vf):
+            if F.size == 0:
+                continue
+            d = np.sum(normals[F] * (cen[F] - X[v]), axis=1)
+            Xn[v] = X[v] + np.sum(normals[F] * d[:, None], axis=0) / F.size
+        X = Xn
+    return X
+
+
+def fine_denoise(X: np.ndarray, faces: np.ndarray, sigma_s: float, sigma_r: float,
+                 normal_iters: int, vertex_iters: int):
+    """The fine step of the coarse-to-fine denoising (Sec. 7.2): filtered normals, fitted vertices."""
+    nrm = bilateral_normals(X, faces, sigma_s, sigma_r, normal_iters)
+    return fit_vertices(X, faces, nrm, vertex_iters), nrm
+
+
+def normal_angle_error(X: np.ndarray, X_ref: np.ndarray, faces: np.ndarray) -> float:
+    """Mean angle theta (degrees) between corresponding face normals of two meshes (Sec. 8).
+
+    Reading: the angle is atan2(||n x n_ref||, n . n_ref); faces that are
+    degenerate in either mesh are left out of the mean (0 if none is left).
+    """
+    n1, _, _ = face_geometry(X, faces)
+    n2, _, _ = face_geometry(X_ref, faces)
+    ok = (np.linalg.norm(n1, axis=1) > 0) & (np.linalg.norm(n2, axis=1) > 0)
+    if not np.any(ok):
+        return 0.0
+    ang = np.arctan2(np.linalg.norm(np.cross(n1[ok], n2[ok]), axis=1),
+                     np.sum(n1[ok] * n2[ok], axis=1))
+    return float(np.degrees(np.mean(ang)))
 
 
 # ---------------------------------------------------------------------------

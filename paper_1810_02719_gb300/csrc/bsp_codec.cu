@@ -2,7 +2,7 @@
 // metric.
 //
 //  * Quantisation: the coefficients E[b] of every block are coded with q bits
-//    per value by a uniform scalar quantiser (Sec. 7.1, bits-per-vertex
+//    per value by a uniform scalar quantiser (Sec. 8, the bits-per-vertex
 //    formula with q_c = 12).  The paper does not state the quantiser's range;
 //    here every (block, column) pair has its own [lo, hi] = [min, max] over
 //    the block's c_b coefficients, sent as side information:
@@ -11,7 +11,7 @@
 //    evaluated in the coefficients' own precision with every operation
 //    rounded on its own (no contraction into FMA), so that the codes are a
 //    deterministic function of the inputs.
-//  * NMSVE (Sec. 7.1): (||v - v~|| + ||GL(v) - GL(v~)||) / (2 n) over the 3 n
+//  * NMSVE (Sec. 8): (||v - v~|| + ||GL(v) - GL(v~)||) / (2 n) over the 3 n
 //    coordinates, with the geometric Laplacian
 //        GL(v_i) = v_i - sum_j v_j / d_ij / sum_j 1 / d_ij
 //    over the mesh neighbours j of i (all faces, across block borders) and

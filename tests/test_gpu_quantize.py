@@ -1,4 +1,4 @@
-"""GPU codec (Sec. 7.1) vs the oracle, through the C ABI.
+"""GPU codec (Sec. 7.1, Sec. 8) vs the oracle, through the C ABI.
 
 Codes and quantiser ranges are integers and extreme values decided in the
 coefficients' own precision on both sides: they must match bit for bit, and

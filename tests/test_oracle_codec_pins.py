@@ -1,4 +1,4 @@
-"""Pins for the oracle's compression codec (Sec. 7.1): uniform quantisation of
+"""Pins for the oracle's compression codec (Sec. 7.1, Sec. 8): uniform quantisation of
 the coefficients, bits per vertex, and the NMSVE with its geometric Laplacian.
 
 Every check compares the oracle with something computed another way: the
