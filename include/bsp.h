@@ -407,6 +407,47 @@ int bsp_bits_per_vertex(const bsp_mesh* mesh, int32_t bits, double* bpv);
 int bsp_nmsve(const void* X, const void* X_rec, int32_t dtype, int64_t n, const int32_t* faces,
               int64_t m, double* out, void* stream);
 
+/*
+ * Fine denoising step of the coarse-to-fine denoising (Sec. 7.2), applied
+ * after the coarse step v^ = U U^T v (bsp_reconstruct) or to any mesh:
+ *  1. face normals, centroids and areas of X (Sec. 7.2, face normal equation;
+ *     a degenerate face has normal 0 and area 0);
+ *  2. normal_iters passes of the bilateral normal filter (Eqs. BF, Wm, Wn)
+ *         n_i <- normalise( sum_j A_j exp(-||m_i - m_j||^2 / (2 sigma_s^2))
+ *                                      exp(-||n_i - n_j||^2 / (2 sigma_r^2)) n_j )
+ *     over the faces j that share a vertex with face i (i included), each
+ *     pass on the previous pass's normals with the centroids and areas of X;
+ *     a face whose sum vanishes keeps its normal;
+ *  3. vertex_iters updates (Eqs. iter1, iter2)
+ *         v <- v + (1 / |F_v|) sum_{z in F_v} n_z [n_z . (m_z - v)]
+ *     with the centroids m_z at the current positions, all vertices moving
+ *     from the previous iterate; a vertex in no face stays.
+ * Arithmetic in the precision of `dtype` (exp as the CUDA math library
+ * computes it).
+ *   X, X_out      host or device [n x 3] of dtype (BSP_DT_F32 or BSP_DT_F64);
+ *                 X_out may not alias X.
+ *   normals_out   NULL, or host or device [m x 3] of dtype: the filtered normals.
+ *   faces         host or device int32 [m x 3], vertex ids in [0, n).
+ *   sigma_s, sigma_r  kernel widths, positive; iterations >= 0.
+ * Errors: BSP_ERR_INVALID_ARG (bad index, sizes, dtype or widths),
+ * BSP_ERR_OOM, BSP_ERR_CUDA.  Allocates its own scratch and synchronises.
+ */
+int bsp_fine_denoise(const void* X, void* X_out, void* normals_out, int32_t dtype, int64_t n,
+                     const int32_t* faces, int64_t m, double sigma_s, double sigma_r,
+                     int32_t normal_iters, int32_t vertex_iters, void* stream);
+
+/*
+ * theta of the evaluation (Sec. 8): the mean over faces of the angle between
+ * the normal of a face in X and in X_ref (same faces), atan2(||n x n'||,
+ * n . n'), in degrees; faces degenerate in either mesh are left out (0 if
+ * none is left).  Accumulated in FP64.
+ *   X, X_ref   host or device [n x 3] of dtype (BSP_DT_F32 or BSP_DT_F64).
+ *   faces      host or device int32 [m x 3].
+ *   theta_deg  host double.
+ */
+int bsp_normal_angle_error(const void* X, const void* X_ref, int32_t dtype, int64_t n,
+                           const int32_t* faces, int64_t m, double* theta_deg, void* stream);
+
 /* Thread-local message describing the last failure on this thread ("" if none). */
 const char* bsp_last_error(void);
 

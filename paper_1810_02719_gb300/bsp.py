@@ -89,6 +89,8 @@ def _load():
         "bsp_dequantize": (C.c_int, [P, P, P, I32, I32, P, P]),
         "bsp_bits_per_vertex": (C.c_int, [P, I32, C.POINTER(D)]),
         "bsp_nmsve": (C.c_int, [P, P, I32, I64, P, I64, P, P]),
+        "bsp_fine_denoise": (C.c_int, [P, P, P, I32, I64, P, I64, D, D, I32, I32, P]),
+        "bsp_normal_angle_error": (C.c_int, [P, P, I32, I64, P, I64, C.POINTER(D), P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -110,7 +112,7 @@ def exported_symbols():
             "bsp_set_profiling", "bsp_get_kernel_times", "bsp_onorm_noalloc",
             "bsp_filter_forward", "bsp_filter_backward", "bsp_reconstruct_bf16",
             "bsp_autotune", "bsp_quantize", "bsp_dequantize", "bsp_bits_per_vertex",
-            "bsp_nmsve"]
+            "bsp_nmsve", "bsp_fine_denoise", "bsp_normal_angle_error"]
 
 
 def _check(code):
@@ -304,6 +306,24 @@ def bsp_nmsve(X, X_rec, dtype, n, faces, m, stream=None):
     _check(_lib.bsp_nmsve(_ptr(X), _ptr(X_rec), dtype, n, _ptr(faces), m, _ptr(out),
                           _stream_ptr(stream)))
     return float(out[0]), float(out[1]), float(out[2])
+
+
+def bsp_fine_denoise(X, X_out, dtype, n, faces, m, sigma_s, sigma_r, normal_iters,
+                     vertex_iters, normals_out=None, stream=None):
+    """Bilateral normal filter + vertex fitting of an n x 3 mesh (fine denoising step)."""
+    faces = _i32(faces)
+    _check(_lib.bsp_fine_denoise(_ptr(X), _ptr(X_out), _ptr(normals_out), dtype, n, _ptr(faces),
+                                 m, float(sigma_s), float(sigma_r), normal_iters, vertex_iters,
+                                 _stream_ptr(stream)))
+
+
+def bsp_normal_angle_error(X, X_ref, dtype, n, faces, m, stream=None) -> float:
+    """Mean angle (degrees) between corresponding face normals of two meshes."""
+    faces = _i32(faces)
+    out = C.c_double()
+    _check(_lib.bsp_normal_angle_error(_ptr(X), _ptr(X_ref), dtype, n, _ptr(faces), m,
+                                       C.byref(out), _stream_ptr(stream)))
+    return out.value
 
 
 def bsp_spmm(mesh, P, Y, c, stream=None):

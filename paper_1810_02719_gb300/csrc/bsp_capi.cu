@@ -953,6 +953,23 @@ int scratch(int slot, size_t bytes, void** out) {
   return rc;
 }
 
+// Device buffers of one synchronous call, freed when it returns.
+struct DevBufs {
+  std::vector<void*> p;
+  ~DevBufs() {
+    for (void* q : p) cudaFree(q);
+  }
+  void* get(size_t bytes) {
+    void* q = nullptr;
+    if (cudaMalloc(&q, bytes ? bytes : 16) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    p.push_back(q);
+    return q;
+  }
+};
+
 // X_out = U U^T X for n x 3 coordinates (real type), through the projection
 // and reconstruction kernels; X and X_out host or device.
 int bsp_reconstruct_projected(bsp_mesh* M, const void* X, void* X_out, cudaStream_t s) {
@@ -1580,21 +1597,7 @@ int bsp_nmsve(const void* X, const void* X_rec, int32_t dtype, int64_t n, const 
     return fail(BSP_ERR_INVALID_ARG, "dtype must be BSP_DT_F32 or BSP_DT_F64");
   cudaStream_t s = (cudaStream_t)stream;
   const size_t xb = dtype == BSP_DT_F64 ? 8 : 4;
-  struct Bufs {
-    std::vector<void*> p;
-    ~Bufs() {
-      for (void* q : p) cudaFree(q);
-    }
-    void* get(size_t bytes) {
-      void* q = nullptr;
-      if (cudaMalloc(&q, bytes ? bytes : 16) != cudaSuccess) {
-        cudaGetLastError();
-        return nullptr;
-      }
-      p.push_back(q);
-      return q;
-    }
-  } bufs;
+  DevBufs bufs;
   const void* dX = X;
   const void* dXr = X_rec;
   const int32_t* dF = faces;
@@ -1646,6 +1649,142 @@ int bsp_nmsve(const void* X, const void* X_rec, int32_t dtype, int64_t n, const 
   out[1] = std::sqrt(acc[0]);
   out[2] = std::sqrt(acc[1]);
   out[0] = (out[1] + out[2]) / (2.0 * (double)n);
+  return BSP_OK;
+}
+
+int bsp_fine_denoise(const void* X, void* X_out, void* normals_out, int32_t dtype, int64_t n,
+                     const int32_t* faces, int64_t m, double sigma_s, double sigma_r,
+                     int32_t normal_iters, int32_t vertex_iters, void* stream) {
+  g_err.clear();
+  if (!X || !X_out || (m > 0 && !faces)) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
+  if (n < 1 || n >= INT32_MAX || m < 0 || m > INT32_MAX / 3)
+    return fail(BSP_ERR_INVALID_ARG, "n or m out of range");
+  if (dtype != BSP_DT_F32 && dtype != BSP_DT_F64)
+    return fail(BSP_ERR_INVALID_ARG, "dtype must be BSP_DT_F32 or BSP_DT_F64");
+  if (!(sigma_s > 0) || !(sigma_r > 0) || !std::isfinite(sigma_s) || !std::isfinite(sigma_r))
+    return fail(BSP_ERR_INVALID_ARG, "sigma_s and sigma_r must be positive and finite");
+  if (normal_iters < 0 || vertex_iters < 0)
+    return fail(BSP_ERR_INVALID_ARG, "iteration counts must be >= 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t xb = dtype == BSP_DT_F64 ? 8 : 4;
+  DevBufs bufs;
+  const size_t xbytes = (size_t)n * 3 * xb, fbytes = (size_t)(m > 0 ? m : 1) * 3 * xb;
+  char* X0 = (char*)bufs.get(xbytes);
+  char* X1 = (char*)bufs.get(xbytes);
+  char* N0 = (char*)bufs.get(fbytes);
+  char* N1 = (char*)bufs.get(fbytes);
+  char* cen = (char*)bufs.get(fbytes);
+  char* area = (char*)bufs.get((size_t)(m > 0 ? m : 1) * xb);
+  char* w = (char*)bufs.get(16 + 3 * (size_t)(n + 1) * sizeof(int32_t));
+  if (!X0 || !X1 || !N0 || !N1 || !cen || !area || !w)
+    return fail(BSP_ERR_OOM, "device allocation failed");
+  int* d_status = (int*)w;
+  int32_t* cnt = (int32_t*)(w + 16);
+  int32_t* off = cnt + (n + 1);
+  int32_t* cur = off + (n + 1);
+  CU(cudaMemsetAsync(w, 0, 16 + 3 * (size_t)(n + 1) * sizeof(int32_t), s));
+  int rc;
+  if ((rc = to_device(X0, X, xbytes, s)) != BSP_OK) return rc;
+  const int32_t* dF = faces;
+  if (m > 0 && !is_device_ptr(faces)) {
+    void* t = bufs.get((size_t)m * 3 * sizeof(int32_t));
+    if (!t) return fail(BSP_ERR_OOM, "device allocation failed");
+    CU(cudaMemcpyAsync(t, faces, (size_t)m * 3 * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    dF = (const int32_t*)t;
+  }
+  launch_vf_table(m, dF, n, cnt, d_status, s);
+  long long total = 0;
+  if ((rc = exclusive_scan(cnt, off, n, d_status, s, &total)) != BSP_OK) return fail(rc, "scan failed");
+  int st = 0;
+  CU(cudaMemcpy(&st, d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st & ST_BAD_INDEX) return fail(BSP_ERR_INVALID_ARG, "face vertex index out of range");
+  if (st) return fail(BSP_ERR_INVALID_ARG, "too many face entries");
+  int32_t* vf = (int32_t*)bufs.get((size_t)(total > 0 ? total : 1) * sizeof(int32_t));
+  if (!vf) return fail(BSP_ERR_OOM, "device allocation failed");
+  launch_vf_fill(m, dF, n, off, cur, vf, s);
+  void* Xf = nullptr;
+  void* Nf = nullptr;
+  if (dtype == BSP_DT_F64) {
+    double *xf, *nf;
+    rc = launch_fine_denoise<double>(n, m, dF, off, vf, (double*)X0, (double*)X1, (double*)N0,
+                                     (double*)N1, (double*)cen, (double*)area, sigma_s, sigma_r,
+                                     normal_iters, vertex_iters, &xf, &nf, s);
+    Xf = xf;
+    Nf = nf;
+  } else {
+    float *xf, *nf;
+    rc = launch_fine_denoise<float>(n, m, dF, off, vf, (float*)X0, (float*)X1, (float*)N0,
+                                    (float*)N1, (float*)cen, (float*)area, sigma_s, sigma_r,
+                                    normal_iters, vertex_iters, &xf, &nf, s);
+    Xf = xf;
+    Nf = nf;
+  }
+  if (rc) return fail(rc, "fine denoising launch failed");
+  if ((rc = from_device(X_out, Xf, xbytes, s)) != BSP_OK) return rc;
+  if (normals_out && m > 0 && (rc = from_device(normals_out, Nf, (size_t)m * 3 * xb, s)) != BSP_OK)
+    return rc;
+  CU(cudaStreamSynchronize(s));
+  return BSP_OK;
+}
+
+int bsp_normal_angle_error(const void* X, const void* X_ref, int32_t dtype, int64_t n,
+                           const int32_t* faces, int64_t m, double* theta_deg, void* stream) {
+  g_err.clear();
+  if (!X || !X_ref || !theta_deg || (m > 0 && !faces))
+    return fail(BSP_ERR_INVALID_ARG, "NULL argument");
+  if (n < 1 || n >= INT32_MAX || m < 0 || m > INT32_MAX / 3)
+    return fail(BSP_ERR_INVALID_ARG, "n or m out of range");
+  if (dtype != BSP_DT_F32 && dtype != BSP_DT_F64)
+    return fail(BSP_ERR_INVALID_ARG, "dtype must be BSP_DT_F32 or BSP_DT_F64");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t xb = dtype == BSP_DT_F64 ? 8 : 4;
+  const size_t xbytes = (size_t)n * 3 * xb;
+  DevBufs bufs;
+  const void* dX = X;
+  const void* dXr = X_ref;
+  const int32_t* dF = faces;
+  if (!is_device_ptr(X)) {
+    void* t = bufs.get(xbytes);
+    if (!t) return fail(BSP_ERR_OOM, "device allocation failed");
+    CU(cudaMemcpyAsync(t, X, xbytes, cudaMemcpyHostToDevice, s));
+    dX = t;
+  }
+  if (!is_device_ptr(X_ref)) {
+    void* t = bufs.get(xbytes);
+    if (!t) return fail(BSP_ERR_OOM, "device allocation failed");
+    CU(cudaMemcpyAsync(t, X_ref, xbytes, cudaMemcpyHostToDevice, s));
+    dXr = t;
+  }
+  if (m > 0 && !is_device_ptr(faces)) {
+    void* t = bufs.get((size_t)m * 3 * sizeof(int32_t));
+    if (!t) return fail(BSP_ERR_OOM, "device allocation failed");
+    CU(cudaMemcpyAsync(t, faces, (size_t)m * 3 * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    dF = (const int32_t*)t;
+  }
+  // face indices are checked by the vertex -> face count (nothing else is kept)
+  char* w = (char*)bufs.get(32 + (size_t)(n + 1) * sizeof(int32_t));
+  if (!w) return fail(BSP_ERR_OOM, "device allocation failed");
+  int* d_status = (int*)w;
+  double* d_acc = (double*)(w + 8);
+  unsigned long long* d_cnt = (unsigned long long*)(w + 16);
+  CU(cudaMemsetAsync(w, 0, 32 + (size_t)(n + 1) * sizeof(int32_t), s));
+  launch_vf_table(m, dF, n, (int32_t*)(w + 32), d_status, s);
+  int st = 0;
+  CU(cudaMemcpyAsync(&st, d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  if (st & ST_BAD_INDEX) return fail(BSP_ERR_INVALID_ARG, "face vertex index out of range");
+  int rc = dtype == BSP_DT_F64
+               ? launch_normal_angle<double>(m, dF, (const double*)dX, (const double*)dXr, d_acc,
+                                             d_cnt, s)
+               : launch_normal_angle<float>(m, dF, (const float*)dX, (const float*)dXr, d_acc,
+                                            d_cnt, s);
+  if (rc) return fail(rc, "normal angle launch failed");
+  double acc = 0.0;
+  unsigned long long c = 0;
+  CU(cudaMemcpyAsync(&acc, d_acc, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(&c, d_cnt, sizeof(c), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  *theta_deg = c ? acc / (double)c * (180.0 / 3.14159265358979323846) : 0.0;
   return BSP_OK;
 }
 

@@ -237,6 +237,22 @@ template <typename T>
 int launch_nm_err(int64_t n, const int32_t* off, const int32_t* nbr, const T* X, const T* Xr,
                   double* acc, cudaStream_t s);
 
+// Fine denoising and normal-angle metric (bsp_denoise.cu).  The vertex -> face
+// table: counts (status bit ST_BAD_INDEX on a bad face), then after a scan the
+// fill and a per-vertex sort.
+void launch_vf_table(int64_t m, const int32_t* faces, int64_t n, int32_t* cnt, int* status,
+                     cudaStream_t s);
+void launch_vf_fill(int64_t m, const int32_t* faces, int64_t n, const int32_t* off, int32_t* cur,
+                    int32_t* vf, cudaStream_t s);
+template <typename T>
+int launch_fine_denoise(int64_t n, int64_t m, const int32_t* faces, const int32_t* off,
+                        const int32_t* vf, T* X0, T* X1, T* n0, T* n1, T* cen, T* area,
+                        double sigma_s, double sigma_r, int normal_iters, int vertex_iters,
+                        T** X_final, T** n_final, cudaStream_t s);
+template <typename T>
+int launch_normal_angle(int64_t m, const int32_t* faces, const T* X, const T* Xr, double* acc,
+                        unsigned long long* cnt, cudaStream_t s);
+
 // Start matrices and dynamic-c helpers (bsp_dyn.cu)
 template <typename T>
 void launch_init_starts(const int32_t* batch, int nbatch, const int32_t* bptr,
