@@ -383,8 +383,8 @@ def denoise_report(bsp, args, h, xyz, faces, dfaces, k, n, device, stream, devic
         bsp.bsp_reconstruct(h, En, 3, Xc, stream)
 
     def fine():
-        bsp.bsp_fine_denoise(Xc, Xf, None, bsp.BSP_DT_F32, n, dfaces, m, sigma_s, sigma_r,
-                             n_it, v_it, stream=stream)
+        bsp.bsp_fine_denoise(Xc, Xf, bsp.BSP_DT_F32, n, dfaces, m, sigma_s, sigma_r, n_it, v_it,
+                             stream=stream)
 
     t_coarse = device_time(coarse, reps=3)
     t_fine = device_time(fine, reps=3)

@@ -195,8 +195,11 @@ __global__ void __launch_bounds__(kDT) k_normal_angle(int64_t m, const int32_t* 
       }
     double a[3], b[3];
     if (!unit_normal(P[0], P[1], P[2], a) || !unit_normal(Q[0], Q[1], Q[2], b)) continue;
-    const double cx = a[1] * b[2] - a[2] * b[1], cy = a[2] * b[0] - a[0] * b[2],
-                 cz = a[0] * b[1] - a[1] * b[0];
+    // products rounded on their own: identical normals give a cross product
+    // of exactly 0 (an FMA would leave the rounding residue of one product)
+    const double cx = __dsub_rn(__dmul_rn(a[1], b[2]), __dmul_rn(a[2], b[1]));
+    const double cy = __dsub_rn(__dmul_rn(a[2], b[0]), __dmul_rn(a[0], b[2]));
+    const double cz = __dsub_rn(__dmul_rn(a[0], b[1]), __dmul_rn(a[1], b[0]));
     s += atan2(sqrt(cx * cx + cy * cy + cz * cz), a[0] * b[0] + a[1] * b[1] + a[2] * b[2]);
     ++c;
   }
