@@ -680,7 +680,6 @@ int track_dynamic(bsp_mesh* M, const void* X, double tol, int c_min, int c_max, 
     return rc;
   if ((rc = to_device(M->d_starts, V0, (size_t)M->root_rows * c_min * sizeof(T), s)) != BSP_OK)
     return rc;
-  size_t dummy = 0;
   if ((rc = ensure(&M->d_X, &M->cap_X, (size_t)M->n * 3 * sizeof(T))) != BSP_OK) return rc;
   if ((rc = to_device(M->d_X, X, (size_t)M->n * 3 * sizeof(T), s)) != BSP_OK) return rc;
   if (!M->d_action) {
@@ -693,7 +692,6 @@ int track_dynamic(bsp_mesh* M, const void* X, double tol, int c_min, int c_max, 
       return fail(BSP_ERR_OOM, "device allocation failed");
     }
   }
-  static_cast<void>(dummy);
   const int32_t* d_forced = nullptr;
   if (forced) {
     if ((rc = to_device(M->d_forced, forced, sizeof(int32_t) * M->k, s)) != BSP_OK) return rc;
