@@ -24,7 +24,9 @@ or a documented choice here):
     orthonormalised by Onorm (the paper uses the SVD of the first block, Sec. 4).
   * Rayleigh-Ritz (optional, not in the paper): H = V^T L V, ascending Ritz order.
   * dynamic c: relative Frobenius residual, growth by c_step columns
-    [e/||e||, counter-hash columns], see ``oi_track_dynamic``.
+    [e/||e||, counter-hash columns], see ``oi_track_dynamic``; the paper's own
+    one-column policy between two thresholds, with the branch directions of
+    the text, is ``doi_paper_block`` / ``doi_paper_track``.
   * codec (Sec. 7.1, Sec. 8): a uniform quantiser per block and coefficient column
     over [min, max]; NMSVE as printed (unsquared norms, linear value), GL with
     each geometry's own edge lengths, see ``quantize`` and ``nmsve``.
@@ -33,8 +35,8 @@ or a documented choice here):
     ``bilateral_normals``, ``fit_vertices`` and ``normal_angle_error``.
 
 Parity status: every function here is pinned by tests in
-``tests/test_oracle_pins.py``, ``tests/test_oracle_codec_pins.py`` and
-``tests/test_oracle_denoise_pins.py`` against
+``tests/test_oracle_pins.py``, ``tests/test_oracle_codec_pins.py``,
+``tests/test_oracle_denoise_pins.py`` and ``tests/test_oracle_doi_pins.py`` against
 closed forms, invariants, hand-worked examples or brute force.
 """
 from __future__ import annotations
@@ -659,6 +661,68 @@ def oi_track_dynamic(mesh: Mesh, X: np.ndarray, starts: np.ndarray, tol: float =
             min(c_max, (n_b // c_step) * c_step), c_step, seed,
             b if block_ids is None else int(block_ids[b]), fc)
     return U, cs, met, rhos
+
+
+def doi_paper_block(L: np.ndarray, X: np.ndarray, V0: np.ndarray, delta: float, z: int,
+                    eps_l: float, eps_h: float, c_min: int, c_max: int, t_cap: int):
+    """The paper's own dynamic OI for one submesh (Sec. 5, Algorithm 2), one column at a time.
+
+    Every iteration applies Algorithm 1 once, U = Onorm(R^z U), and measures
+    the summed residual e = sum_{j in x, y, z} (v_j - U U^T v_j) (Sec. 5,
+    Eq. residual).  Branch directions as the text states them (Algorithm 2
+    prints them swapped): ||e|| > eps_h grows the basis by e/||e|| (the next
+    iteration's Onorm(R^z [U, e/||e||]) is Eq. newU), ||e|| < eps_l keeps the
+    first c - 1 columns, anything else stops.  Readings: the width stays in
+    [c_min, c_max] (a branch that would leave it stops instead), at most
+    t_cap iterations run, and a basis left with an appended column at the
+    cap is orthonormalised once more.
+    Returns (U, c, iterations, ||e|| of the last iteration).
+    """
+    U = np.asarray(V0, dtype=np.float64)
+    ne = 0.0
+    for t in range(1, t_cap + 1):
+        U, _ = onorm(apply_S(L, U, delta, z))
+        e = (X - U @ (U.T @ X)).sum(axis=1)
+        ne = float(np.linalg.norm(e))
+        c = U.shape[1]
+        if ne > eps_h and c < c_max:
+            U = np.concatenate([U, (e / ne)[:, None]], axis=1)
+        elif ne < eps_l and c > c_min:
+            U = U[:, :c - 1]
+        else:
+            return U, c, t, ne
+    U, _ = onorm(U)
+    return U, U.shape[1], t_cap, ne
+
+
+def doi_paper_track(mesh: Mesh, X: np.ndarray, starts: np.ndarray, c0: int, eps_l: float,
+                    eps_h: float, c_min: int = 1, c_max: int = 128, t_cap: int = 32,
+                    delta: float = 1e-2, z: int = 1):
+    """The paper's dynamic OI over all blocks in topological order (Sec. 5, Algorithm 2).
+
+    A root starts from the first c0 columns of its rows of ``starts``; a child
+    starts from its parent's final basis and width (c_i <- c_{i-1}, row
+    transfer for unequal sizes).  Returns (U list, c array, iterations array).
+    """
+    k = mesh.k
+    U = [None] * k
+    cs = np.zeros(k, dtype=np.int64)
+    its = np.zeros(k, dtype=np.int64)
+    off = 0
+    root_off = {}
+    for b in range(k):
+        if mesh.parent[b] < 0:
+            root_off[b] = off
+            off += mesh.blocks[b].verts.size
+    for b in range(k):
+        blk = mesh.blocks[b]
+        n_b = blk.verts.size
+        p = mesh.parent[b]
+        V0 = starts[root_off[b]:root_off[b] + n_b, :c0] if p < 0 else row_transfer(U[p], n_b)
+        U[b], cs[b], its[b], _ = doi_paper_block(
+            laplacian(blk, mesh.literal_degree), X[blk.verts], V0, delta, z, eps_l, eps_h,
+            c_min, min(c_max, n_b), t_cap)
+    return U, cs, its
 
 
 # ---------------------------------------------------------------------------
