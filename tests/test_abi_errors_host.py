@@ -69,3 +69,16 @@ def test_onorm_noalloc_size_limits(bsp):
     _invalid(bsp, bsp.bsp_onorm_noalloc, Y, Q, 128, 65, match="2048")
     _invalid(bsp, bsp.bsp_onorm_noalloc, Y, Q, 4, 8, match="c <= n")
     _invalid(bsp, bsp.bsp_onorm_noalloc, None, Q, 4, 2, match="required")
+
+
+def test_mesh_options_are_checked_before_the_device(bsp):
+    from paper_1810_02719_gb300 import synth
+    xyz, faces = synth.torus(8)
+    ptr, verts = synth.tile_partition(8, 4)
+    parent = synth.raster_chain(len(ptr) - 1)
+    bad = [dict(delta=0.0), dict(delta=-1.0), dict(z=0), dict(precision=3),
+           dict(weight_mode=5), dict(cg_rtol=0.0), dict(cg_max_steps=0), dict(cols_per_cta=3)]
+    for kw in bad:
+        _invalid(bsp, bsp.bsp_mesh_create, xyz, faces, ptr, verts, parent, bsp.make_opts(**kw))
+    _invalid(bsp, bsp.bsp_mesh_create, xyz, faces, ptr, verts, parent, bsp.make_opts(), n=0,
+             match="positive")
