@@ -12,7 +12,10 @@
  * per block for a reconstruction-quality target (Sec. 5, Algorithm 2), and
  * projects/reconstructs coordinates E = U^T v, v~ = U E (Sec. 3 GFT;
  * Sec. 7.1 compression; Sec. 7.2 coarse denoising; Sec. 7.3 all frames of a
- * dynamic mesh with one basis).
+ * dynamic mesh with one basis).  Around that path it offers the codec and
+ * quality measures the paper evaluates (q-bit quantisation of the
+ * coefficients, bits per vertex, NMSVE, the mean face-normal angle; Sec. 8)
+ * and the fine denoising step after the coarse one (Sec. 7.2).
  *
  * Conventions for every entry point:
  *  - Returns a bsp_status; no C++ exception crosses this boundary.  On error,
