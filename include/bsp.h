@@ -30,6 +30,10 @@
  *  - Matrices are row-major.  "real" means float when the mesh precision is
  *    BSP_PREC_F32 or BSP_PREC_MIXED and double when it is BSP_PREC_F64.
  *  - The caller owns every buffer it passes; the library copies what it keeps.
+ *  - Different meshes may be used from different host threads at the same
+ *    time; one mesh must not be used by two threads at once (the library's
+ *    per-call scratch and error message are per thread; bsp_onorm_noalloc
+ *    documents its own shared scratch).
  *  - Blocks are numbered 0..k-1 and must be topologically sorted:
  *    parent[b] < b, or parent[b] = -1 for a root (Sec. 4: "the subsequent ones
  *    are processed in a topologically sorted order").

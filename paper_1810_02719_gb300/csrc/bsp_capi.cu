@@ -114,7 +114,8 @@ int read_host(std::vector<V>& out, const V* src, size_t count) {
   return BSP_OK;
 }
 
-bool g_realloc = false;  // set when ensure() replaces a buffer (cached graphs go stale)
+// ensure() replaced a buffer during this thread's current call (cached graphs go stale)
+thread_local bool g_realloc = false;
 
 int ensure(void** p, size_t* cap, size_t bytes) {
   if (*cap >= bytes && *p) return BSP_OK;
