@@ -432,7 +432,7 @@ int bsp_nmsve(const void* X, const void* X_rec, int32_t dtype, int64_t n, const 
  * Arithmetic in the precision of `dtype` (exp as the CUDA math library
  * computes it).
  *   X, X_out      host or device [n x 3] of dtype (BSP_DT_F32 or BSP_DT_F64);
- *                 X_out may not alias X.
+ *                 X is copied to the device first, so X_out may alias X.
  *   normals_out   NULL, or host or device [m x 3] of dtype: the filtered normals.
  *   faces         host or device int32 [m x 3], vertex ids in [0, n).
  *   sigma_s, sigma_r  kernel widths, positive; iterations >= 0.
