@@ -27,6 +27,8 @@ or a documented choice here):
     [e/||e||, counter-hash columns], see ``oi_track_dynamic``; the paper's own
     one-column policy between two thresholds, with the branch directions of
     the text, is ``doi_paper_block`` / ``doi_paper_track``.
+  * overlapped parts (Sec. 6.1): induced subgraph per part, copies weighted
+    by their degree in the part, see ``weighted_average``.
   * codec (Sec. 7.1, Sec. 8): a uniform quantiser per block and coefficient column
     over [min, max]; NMSVE as printed (unsquared norms, linear value), GL with
     each geometry's own edge lengths, see ``quantize`` and ``nmsve``.
@@ -36,7 +38,8 @@ or a documented choice here):
 
 Parity status: every function here is pinned by tests in
 ``tests/test_oracle_pins.py``, ``tests/test_oracle_codec_pins.py``,
-``tests/test_oracle_denoise_pins.py`` and ``tests/test_oracle_doi_pins.py`` against
+``tests/test_oracle_denoise_pins.py``, ``tests/test_oracle_doi_pins.py`` and
+``tests/test_oracle_overlap_pins.py`` against
 closed forms, invariants, hand-worked examples or brute force.
 """
 from __future__ import annotations
@@ -521,6 +524,72 @@ def normal_angle_error(X: np.ndarray, X_ref: np.ndarray, faces: np.ndarray) -> f
     ang = np.arctan2(np.linalg.norm(np.cross(n1[ok], n2[ok]), axis=1),
                      np.sum(n1[ok] * n2[ok], axis=1))
     return float(np.degrees(np.mean(ang)))
+
+
+# ---------------------------------------------------------------------------
+# Sec. 6.1: overlapped submeshes and the degree-weighted average (Algorithm 3)
+# ---------------------------------------------------------------------------
+
+def build_overlapped_mesh(n, block_ptr, block_verts, parent, faces=None, edges=None) -> Mesh:
+    """Parts that may share vertices (Sec. 6.1): each block's Laplacian is that of the
+    subgraph induced by its own vertex list, as in ``build_mesh``, but a vertex may
+    appear in several blocks (combinatorial weights)."""
+    ptr = np.asarray(block_ptr, dtype=np.int64)
+    bv = np.asarray(block_verts, dtype=np.int64)
+    E = undirected_edges(faces=faces, edges=edges)
+    blocks = []
+    for b in range(len(ptr) - 1):
+        verts = bv[ptr[b]:ptr[b + 1]]
+        loc = np.full(n, -1, dtype=np.int64)
+        loc[verts] = np.arange(verts.size)
+        inside = (loc[E[:, 0]] >= 0) & (loc[E[:, 1]] >= 0)
+        li, lj = loc[E[inside, 0]], loc[E[inside, 1]]
+        le = np.stack([np.minimum(li, lj), np.maximum(li, lj)], axis=1)
+        le = le[np.lexsort((le[:, 1], le[:, 0]))]
+        blocks.append(Block(verts=verts, edges=le, weights=np.ones(le.shape[0])))
+    return Mesh(n=n, blocks=blocks, parent=np.asarray(parent, dtype=np.int64), xyz=None,
+                literal_degree=False)
+
+
+def block_degrees(block: Block) -> np.ndarray:
+    """Degree of every local vertex inside its block: its neighbours in the induced subgraph."""
+    d = np.zeros(block.verts.size, dtype=np.int64)
+    np.add.at(d, block.edges[:, 0], 1)
+    np.add.at(d, block.edges[:, 1], 1)
+    return d
+
+
+def weighted_average(mesh: Mesh, Xb: List[np.ndarray], cols: int) -> np.ndarray:
+    """Algorithm 3 (Sec. 6.1): every vertex's position is the average of its copies in the
+    parts it belongs to, each weighted by the vertex's degree in that part.
+
+    Reading: a vertex whose weights sum to 0 (isolated in every part holding it)
+    takes the plain mean of its copies; a vertex in no part stays 0.
+    """
+    num = np.zeros((mesh.n, cols))
+    den = np.zeros(mesh.n)
+    cnt = np.zeros(mesh.n)
+    plain = np.zeros((mesh.n, cols))
+    for b, blk in enumerate(mesh.blocks):
+        w = block_degrees(blk).astype(np.float64)
+        np.add.at(num, blk.verts, w[:, None] * Xb[b])
+        np.add.at(den, blk.verts, w)
+        np.add.at(plain, blk.verts, Xb[b])
+        np.add.at(cnt, blk.verts, 1.0)
+    out = np.zeros((mesh.n, cols))
+    ok = den > 0
+    out[ok] = num[ok] / den[ok, None]
+    iso = (~ok) & (cnt > 0)
+    out[iso] = plain[iso] / cnt[iso, None]
+    return out
+
+
+def reconstruct_overlapped(mesh: Mesh, U: List[np.ndarray], X: np.ndarray) -> np.ndarray:
+    """Overlapped reconstruction (Sec. 6.1): every part reconstructs its own copy
+    U_b U_b^T X[b]; Algorithm 3 merges the copies."""
+    cols = X.shape[1]
+    Xb = [U[b] @ (U[b].T @ X[blk.verts]) for b, blk in enumerate(mesh.blocks)]
+    return weighted_average(mesh, Xb, cols)
 
 
 # ---------------------------------------------------------------------------

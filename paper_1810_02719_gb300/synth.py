@@ -145,6 +145,29 @@ def tile_partition(N: int, T: int):
     return ptr, verts
 
 
+def overlapped_tiles(N: int, T: int, r: int):
+    """Overlapped equal-size parts of an N x N periodic (torus) vertex grid.
+
+    Every T x T tile is extended by r rings of neighbouring vertices on each
+    side (wrapping around), so every part has (T + 2 r)^2 vertices and the
+    vertices within r of a tile border appear in 2 or 4 parts.  Parts in
+    raster order; inside a part, row-major local order.
+    Returns (block_ptr int32 [k+1], block_verts int32 [k (T + 2 r)^2]).
+    """
+    assert N % T == 0 and 0 <= r and T + 2 * r <= N
+    nt = N // T
+    S = T + 2 * r
+    ptr = np.arange(nt * nt + 1, dtype=np.int32) * (S * S)
+    verts = np.empty(nt * nt * S * S, dtype=np.int32)
+    li, lj = np.meshgrid(np.arange(S), np.arange(S), indexing="ij")
+    for bi in range(nt):
+        for bj in range(nt):
+            b = bi * nt + bj
+            g = ((bi * T - r + li) % N) * N + ((bj * T - r + lj) % N)
+            verts[ptr[b]:ptr[b + 1]] = g.ravel()
+    return ptr, verts
+
+
 def rect_partition(R: int, C: int, TR: int, TC: int):
     """Partition an R x C vertex grid into (R/TR)(C/TC) rectangular tiles of TR x TC.
 
