@@ -155,3 +155,17 @@ def _doi(L, X, V0, delta, z, eps_l, eps_h, c_min, c_max, t_cap, swap=False, stac
             return U, c, t, ne
     U, _ = O.onorm(U)
     return U, U.shape[1], t_cap, ne
+
+
+def test_higher_powers_of_r_converge_in_fewer_iterations():
+    """The trend of the paper's R^z experiments (Sec. 8): with the same number of OI steps,
+    a higher power z brings the basis closer to the exact eigenspace (the rate is
+    ((lambda_c + delta) / (lambda_{c+1} + delta))^z per step)."""
+    xyz, faces = synth.grid_heightfield(16, seed=0)
+    m = O.build_mesh(256, [0, 256], np.arange(256), [-1], faces=faces)
+    L = O.laplacian(m.blocks[0])
+    c = 6
+    W, _ = O.eigh_basis(L, c)
+    V0 = np.random.default_rng(5).standard_normal((256, c))
+    errs = [O.max_sine(O.oi_block(L, V0, 1e-2, z, 2, rr=False)[0], W) for z in (1, 2, 3, 4)]
+    assert errs[0] > errs[1] > errs[2] > errs[3]
