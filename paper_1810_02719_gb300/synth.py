@@ -168,6 +168,31 @@ def overlapped_tiles(N: int, T: int, r: int):
     return ptr, verts
 
 
+def expand_overlapped(block_ptr, block_verts, faces):
+    """Non-overlapping copy of an overlapped partition: every (part, vertex) pair
+    becomes its own vertex, and every part keeps the mesh edges whose two end
+    points it holds, re-indexed to its copies (an edge list, since a part may
+    hold an edge without holding a face around it).  A library that needs each
+    vertex in one block can then process the parts as they are; the copies are
+    merged back afterwards (``orig`` maps each copy to its vertex).
+    Returns (block_ptr, block_verts = arange, edges of the copies [E x 2], orig).
+    """
+    ptr = np.asarray(block_ptr, dtype=np.int64)
+    bv = np.asarray(block_verts, dtype=np.int64)
+    f = np.asarray(faces, dtype=np.int64).reshape(-1, 3)
+    e = np.concatenate([f[:, [0, 1]], f[:, [1, 2]], f[:, [2, 0]]])
+    e = np.unique(np.sort(e, axis=1), axis=0)
+    n = int(max(bv.max(), f.max())) + 1
+    out = []
+    for b in range(len(ptr) - 1):
+        loc = np.full(n, -1, dtype=np.int64)
+        loc[bv[ptr[b]:ptr[b + 1]]] = np.arange(ptr[b], ptr[b + 1])
+        le = loc[e]
+        out.append(le[np.all(le >= 0, axis=1)])
+    return (ptr.astype(np.int32), np.arange(ptr[-1], dtype=np.int32),
+            np.concatenate(out).astype(np.int32), bv.astype(np.int32))
+
+
 def rect_partition(R: int, C: int, TR: int, TC: int):
     """Partition an R x C vertex grid into (R/TR)(C/TC) rectangular tiles of TR x TC.
 

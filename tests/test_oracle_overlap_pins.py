@@ -122,3 +122,33 @@ def test_overlap_planted_mistakes_are_caught():
     for check, mut in mutants:
         with pytest.raises(AssertionError):
             check(O=mut)
+
+
+def test_expanded_copies_keep_edges_without_faces():
+    """A part holding both ends of an edge but no face around it keeps the edge."""
+    faces = np.array([[0, 1, 2], [1, 3, 2]])
+    ptr, verts = np.array([0, 3, 5]), np.array([0, 1, 2, 1, 2])     # part 1 = edge 1-2 only
+    eptr, everts, eedges, orig = synth.expand_overlapped(ptr, verts, faces)
+    assert np.array_equal(orig, verts)
+    assert sorted(map(tuple, eedges.tolist())) == [(0, 1), (0, 2), (1, 2), (3, 4)]
+
+
+def test_expanded_copies_reproduce_the_overlapped_parts():
+    """Running the non-overlapping path on the expanded copies gives every part the same
+    Laplacian as the overlapped part, and merging the copies' reconstructions by
+    Algorithm 3 equals the overlapped reconstruction."""
+    N, T, r, c = 12, 4, 1, 6
+    xyz, faces = synth.torus(N, seed=3)
+    ptr, verts = synth.overlapped_tiles(N, T, r)
+    parent = synth.raster_chain(len(ptr) - 1)
+    om = O.build_overlapped_mesh(N * N, ptr, verts, parent, faces=faces)
+    eptr, everts, eedges, orig = synth.expand_overlapped(ptr, verts, faces)
+    em = O.build_mesh(len(everts), eptr, everts, parent, edges=eedges)
+    for a, b in zip(om.blocks, em.blocks):
+        assert np.array_equal(O.laplacian(a), O.laplacian(b))
+    U = [O.eigh_basis(O.laplacian(b), c)[0] for b in om.blocks]
+    X_copies = xyz[orig]
+    rec = O.reconstruct(em, U, O.project(em, U, X_copies), 3)        # one row per copy
+    Xb = [rec[eb.verts] for eb in em.blocks]
+    assert np.allclose(O.weighted_average(om, Xb, 3), O.reconstruct_overlapped(om, U, xyz),
+                       atol=1e-13)
