@@ -801,7 +801,7 @@ def doi_paper_track(mesh: Mesh, X: np.ndarray, starts: np.ndarray, c0: int, eps_
 def principal_sines(U: np.ndarray, W: np.ndarray) -> np.ndarray:
     """Sines of the principal angles between span(U) and span(W) (both orthonormal bases).
 
-    cos(theta_i) are the singular values of U^T W; returned ascending in angle.
+    cos(theta_i) are the singular values of U^T W; returned largest angle first.
     """
     cosv = np.linalg.svd(U.T @ W, compute_uv=False)
     cosv = np.clip(cosv, 0.0, 1.0)

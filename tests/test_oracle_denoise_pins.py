@@ -305,3 +305,10 @@ def _bilateral(M, X, faces, sigma_s, sigma_r, iters):
                 new[i] = acc / ln
         nrm = new
     return nrm
+
+
+def test_face_rings_brute_force():
+    Y, g = grid(5, jitter=0.1, seed=9)
+    rings = O.face_rings(g, Y.shape[0])
+    for i, J in enumerate(brute_rings(g)):
+        assert np.array_equal(rings[i], J), i

@@ -496,3 +496,16 @@ def test_filter_gradients_match_finite_differences():
     _, _, _, xh = O.filter_loss_grads(mesh, noisy, clean, np.ones(E), c, t, starts)
     ref = O.reconstruct(mesh1, U, O.project(mesh1, U, noisy), 3)
     assert np.allclose(xh, ref, atol=1e-10)
+
+
+def test_comparison_metrics_closed_forms():
+    """projector_rel_error and max_sine on bases whose angles are known."""
+    e = np.eye(3)
+    X = np.array([[1.0], [1.0], [0.0]])
+    assert O.projector_rel_error(e[:, :1], e[:, 1:2], X) == pytest.approx(np.sqrt(2.0))
+    assert O.projector_rel_error(e[:, :2], e[:, :2], X) == 0.0
+    a = 0.3
+    U = np.array([[np.cos(a)], [np.sin(a)], [0.0]])
+    assert O.max_sine(U, e[:, :1]) == pytest.approx(np.sin(a), rel=1e-12)
+    assert O.principal_sines(np.c_[U, e[:, 2]], e[:, [0, 2]]) == pytest.approx([np.sin(a), 0.0],
+                                                                               abs=1e-12)
