@@ -338,10 +338,15 @@ int bsp_autotune(bsp_mesh* mesh, int32_t c, int32_t t_max, const void* V0_roots,
  * through their own allocator.  This call allocates nothing: its scratch is
  * a fixed static device array of about 145 KiB (every GPU that loads the
  * library holds it until the process exits).
- *   Y, Q     device float [n x c], row-major (Q may alias Y); the caller owns both.
+ *   Y, Q     device float [n x c], row-major (Q may alias Y); the caller owns
+ *            both.  Both must be device (or managed) memory of the current
+ *            device: a host pointer, or another GPU's, returns
+ *            BSP_ERR_INVALID_ARG before any GPU work.
  *   n, c     1 <= c <= n, n <= 2048, c <= 64; larger sizes return
  *            BSP_ERR_INVALID_ARG without touching the GPU.
- *   stream   cudaStream_t as void*; the call waits for its own work.
+ *   stream   cudaStream_t as void* (NULL: the legacy default stream).  Every
+ *            call copies its five parameters from host memory into the
+ *            scratch array and synchronises this stream before it returns.
  * The first call on each device looks up the scratch array's device address
  * (and configures the kernel), so make that first call before any stream
  * capture.  All calls share the one scratch array: calls that overlap on the

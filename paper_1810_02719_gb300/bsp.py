@@ -349,7 +349,24 @@ def bsp_get_kernel_times(mesh) -> dict:
 
 def bsp_onorm_noalloc(Y, Q, n, c, stream=None):
     """Allocation-free Q = Onorm(Y) of one block (device float [n x c] buffers owned
-    by the caller), for callers that must not allocate device memory while running."""
+    by the caller), for callers that must not allocate device memory while running.
+
+    Torch tensors must be contiguous float32 CUDA tensors of at least n * c
+    elements; with ``stream=None`` the call runs on the current torch stream of
+    Y's device, so it is ordered after the work that wrote Y.  Other objects
+    (raw pointers, NumPy arrays) go to the library unchanged, which rejects
+    anything that is not device memory of the current device.
+    """
+    tensors = [(name, t) for name, t in (("Y", Y), ("Q", Q)) if hasattr(t, "data_ptr")]
+    if tensors:
+        import torch
+        for name, t in tensors:
+            if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+            if t.numel() < n * c:
+                raise ValueError(f"{name} holds {t.numel()} elements, fewer than n * c")
+        if stream is None and hasattr(Y, "data_ptr"):
+            stream = torch.cuda.current_stream(Y.device)
     _check(_lib.bsp_onorm_noalloc(_ptr(Y), _ptr(Q), n, c, _stream_ptr(stream)))
 
 

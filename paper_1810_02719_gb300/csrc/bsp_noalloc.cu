@@ -37,6 +37,18 @@ int noalloc_fail(int code, const char* msg) {
   return code;
 }
 
+// True when p is device (or managed) memory of device `dev`: a host buffer or
+// another GPU's buffer would reach the kernel as a bad device address.
+bool on_device(const void* p, int dev) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) &&
+         at.device == dev;
+}
+
 }  // namespace
 
 extern "C" int bsp_onorm_noalloc(const float* Y, float* Q, int32_t n, int32_t c, void* stream) {
@@ -51,6 +63,9 @@ extern "C" int bsp_onorm_noalloc(const float* Y, float* Q, int32_t n, int32_t c,
     cudaGetLastError();
     return noalloc_fail(BSP_ERR_CUDA, "no usable current CUDA device");
   }
+  if (!on_device(Y, dev) || !on_device(Q, dev))
+    return noalloc_fail(BSP_ERR_INVALID_ARG,
+                        "Y and Q must be device memory of the current CUDA device");
   // One-time set-up per device, with that device current: the device address
   // of the static scratch array (its name is only a host stand-in here).
   void* base = nullptr;
