@@ -86,7 +86,21 @@ typedef struct bsp_opts {
   int32_t rayleigh_ritz;   /* 1: Rayleigh-Ritz after the OI steps of each block (ascending order). Default 1. */
   int32_t cols_per_cta;    /* CG column-slab width (1, 2, 4 or 8); 0 = automatic. */
   int32_t use_graph;       /* 1: capture the fixed-c tracking schedule in a CUDA graph. Default 1. */
+  int32_t schedule;        /* bsp_schedule: how the fixed-c schedule runs.  Default BSP_SCHED_AUTO. */
+  int32_t wait_limit_ms;   /* bound of a device-side wait for a block computed by another
+                              cluster of the persistent engine; on expiry the call returns
+                              BSP_ERR_TIMEOUT.  Default 2000. */
+  int32_t withhold_block;  /* test hook: block b >= 0 waits for a parent flag that is never
+                              set (the wait runs out: BSP_ERR_TIMEOUT).  Default -1 (none). */
 } bsp_opts;
+
+/* Execution of the fixed-c schedule (bsp_oi_track, FP32 precision).
+ *   BSP_SCHED_AUTO   persistent cluster engine when the shapes fit (c <= 64,
+ *                    blocks <= 1,024 rows, <= 16 neighbours per vertex, t_max >= 1),
+ *                    per-wave launches otherwise;
+ *   BSP_SCHED_WAVES  per-wave launches only (one CG and one Onorm launch per
+ *                    level of the block DAG). */
+typedef enum { BSP_SCHED_AUTO = 0, BSP_SCHED_WAVES = 1 } bsp_schedule;
 
 typedef struct bsp_stats {
   int64_t n;               /* vertices */

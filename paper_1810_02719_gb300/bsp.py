@@ -25,6 +25,7 @@ BSP_ERR_NOT_CONVERGED = 6
 
 BSP_PREC_F32, BSP_PREC_F64, BSP_PREC_MIXED = 0, 1, 2
 BSP_W_COMBINATORIAL, BSP_W_EDGE, BSP_W_INV_SQ_DIST = 0, 1, 2
+BSP_SCHED_AUTO, BSP_SCHED_WAVES = 0, 1
 BSP_DT_F32, BSP_DT_F64, BSP_DT_BF16 = 0, 1, 2
 
 _STATUS = {0: "BSP_OK", 1: "BSP_ERR_INVALID_ARG", 2: "BSP_ERR_OOM", 3: "BSP_ERR_CUDA",
@@ -36,7 +37,8 @@ class bsp_opts(C.Structure):
                 ("literal_degree", C.c_int32), ("precision", C.c_int32),
                 ("cg_rtol", C.c_double), ("cg_max_steps", C.c_int32),
                 ("rayleigh_ritz", C.c_int32), ("cols_per_cta", C.c_int32),
-                ("use_graph", C.c_int32)]
+                ("use_graph", C.c_int32), ("schedule", C.c_int32),
+                ("wait_limit_ms", C.c_int32), ("withhold_block", C.c_int32)]
 
 
 class bsp_stats(C.Structure):
@@ -331,7 +333,7 @@ def bsp_spmm(mesh, P, Y, c, stream=None):
 
 
 KERNEL_CLASSES = ["init", "cg", "gram", "reduce", "chol", "panel", "rr", "jacobi", "project",
-                  "recon", "spmm", "dyn"]
+                  "recon", "spmm", "dyn", "oi"]
 
 
 def bsp_set_profiling(mesh, on):

@@ -184,7 +184,7 @@ void release(bsp_mesh* m) {
                   m->d_gcol, m->d_rho, m->d_X, m->d_Gp_rr, m->d_Rsm_rr, m->d_theta_rr,
                   m->d_ckV, m->d_ckY,
                   m->d_adj_gp, m->d_adj_thin, m->d_adj_rows, m->d_Ubf, m->d_Ebf,
-                  m->d_spmm_chunks};
+                  m->d_spmm_chunks, m->d_ready};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (m->graph_exec) cudaGraphExecDestroy(m->graph_exec);
@@ -484,6 +484,39 @@ int ensure_rr_groups(bsp_mesh* M, int c) {
   return BSP_OK;
 }
 
+// The whole fixed-c schedule in one launch of the persistent cluster engine
+// (FP32).  BSP_ERR_INVALID_ARG: the engine's cluster shape cannot be resident
+// here (the caller falls back to the per-wave launches).
+int enqueue_engine(bsp_mesh* M, int c, int t_max, cudaStream_t s, int* launches) {
+  int maxwave = 0;
+  for (auto& w : M->waves) maxwave = std::max(maxwave, (int)w.size());
+  if (maxwave > 1 || M->opts.withhold_block >= 0)
+    CU(cudaMemsetAsync(M->d_ready, 0, sizeof(int) * (M->k + 2), s));
+  OiClusterArgs oa;
+  oa.order = M->d_waves;
+  oa.nblocks = M->k;
+  oa.k = M->k;
+  oa.parent = M->d_parent;
+  oa.root_off = M->d_root_off;
+  oa.starts = (const float*)M->d_starts;
+  oa.U = (float*)M->d_U;
+  oa.ld = M->c_cap;
+  oa.c = c;
+  oa.t_max = t_max;
+  oa.z = M->opts.z;
+  oa.delta = M->opts.delta;
+  oa.rtol = M->opts.cg_rtol;
+  oa.max_steps = M->opts.cg_max_steps;
+  oa.ready = M->d_ready;
+  oa.status = M->d_status;
+  oa.stats = M->d_cgstats;
+  oa.wait_limit_us = (long long)M->opts.wait_limit_ms * 1000;
+  oa.withhold = M->opts.withhold_block;
+  const int rc = launch_oi_cluster(view<float>(M), oa, M->max_nb, M->max_deg, M->engine_ncl, s);
+  if (rc == BSP_OK) ++*launches;
+  return rc;
+}
+
 // Enqueue the fixed-c schedule on stream s; returns a status, counts launches.
 template <typename T, typename TA>
 int enqueue_fixed(bsp_mesh* M, int c, int t_max, cudaStream_t s, int* launches) {
@@ -492,7 +525,16 @@ int enqueue_fixed(bsp_mesh* M, int c, int t_max, cudaStream_t s, int* launches) 
   T* U = (T*)M->d_U;
   T* Y = (T*)M->d_Y;
   int rc;
-  for (int l = 0; l < levels; ++l) {
+  bool engine = false;
+  if constexpr (sizeof(T) == 4 && sizeof(TA) == 4) {
+    if (M->opts.schedule == BSP_SCHED_AUTO && M->engine_c == c && M->engine_ncl > 0 &&
+        oi_cluster_fits(c, t_max, M->max_nb, M->max_deg, M->min_nb)) {
+      if ((rc = enqueue_engine(M, c, t_max, s, launches)) != BSP_OK)
+        return fail(rc, "launch failed (cluster engine)");
+      engine = true;
+    }
+  }
+  for (int l = 0; l < levels && !engine; ++l) {
     const int nbw = (int)M->waves[l].size();
     const int32_t* batch = M->d_waves + M->h_wave_off[l];
     int wmax = 0;
@@ -607,6 +649,19 @@ int track_fixed(bsp_mesh* M, int c, int t_max, const void* V0, cudaStream_t s) {
   g_realloc = false;
   if ((rc = ensure(&M->d_starts, &M->cap_starts, (size_t)M->root_rows * c * sizeof(T))) != BSP_OK)
     return rc;
+  if ((rc = ensure((void**)&M->d_ready, &M->cap_ready, sizeof(int) * (M->k + 2))) != BSP_OK)
+    return rc;
+  if (sizeof(T) == 4 && sizeof(TA) == 4 && M->engine_c != c) {
+    // the engine's attributes and residency, before any capture
+    int maxwave = 0;
+    for (auto& w : M->waves) maxwave = std::max(maxwave, (int)w.size());
+    M->engine_ncl = 0;
+    if (oi_cluster_fits(c, std::max(t_max, 1), M->max_nb, M->max_deg, M->min_nb) &&
+        prepare_oi_cluster(view<float>(M), c, M->max_nb, M->max_deg, maxwave, &M->engine_ncl) !=
+            BSP_OK)
+      M->engine_ncl = 0;
+    M->engine_c = c;
+  }
   if (M->opts.rayleigh_ritz && (rc = ensure_rr_groups<T, TA>(M, c)) != BSP_OK) return rc;
   if (g_realloc && M->graph_exec) {
     cudaGraphExecDestroy(M->graph_exec);
@@ -1023,6 +1078,9 @@ void bsp_opts_default(bsp_opts* o) {
   o->rayleigh_ritz = 1;
   o->cols_per_cta = 0;
   o->use_graph = 1;
+  o->schedule = BSP_SCHED_AUTO;
+  o->wait_limit_ms = 2000;
+  o->withhold_block = -1;
 }
 
 const char* bsp_last_error(void) { return g_err.c_str(); }

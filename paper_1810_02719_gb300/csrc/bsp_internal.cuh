@@ -43,7 +43,7 @@ struct CgStats {
 // the launching stream around every launch, eager mode only).
 enum KernelClass : int {
   KC_INIT = 0, KC_CG, KC_GRAM, KC_REDUCE, KC_CHOL, KC_PANEL, KC_RR, KC_JACOBI,
-  KC_PROJECT, KC_RECON, KC_SPMM, KC_DYN, KC_COUNT
+  KC_PROJECT, KC_RECON, KC_SPMM, KC_DYN, KC_OI, KC_COUNT
 };
 struct Profiler {
   std::vector<cudaEvent_t> ev[KC_COUNT];  // pairs (start, stop)
@@ -188,6 +188,34 @@ int launch_cholqr2_fused(const DenseArgs& a, const T* Y, T* Q, TA* Gp, int maxch
 void configure_fused_kernels();
 void set_last_error(const char* msg);  // message for bsp_last_error() on this thread
 extern bool g_disable_fused;  // force the multi-kernel Onorm (A/B checks)
+
+// Persistent cluster engine of the fixed-c schedule (bsp_oi_cluster.cu): every
+// block's solves and CholeskyQR2 on chip, blocks in topological order, one
+// cluster of ceil(c / 4) CTAs per dependency path, bounded waits on the
+// parents' ready flags between clusters.
+struct OiClusterArgs {
+  const int32_t* order; int nblocks;   // blocks in topological (wave) order
+  int k;                               // blocks of the mesh (ready has k + 2 slots)
+  const int32_t* parent; const int32_t* root_off;
+  const float* starts;                 // roots' start rows, [root rows x c]
+  float* U; int ld; int c;
+  int t_max; int z; double delta; double rtol; int max_steps;
+  int* ready;                          // [k] flags, [k] abort word, [k + 1] never set
+  int* status; CgStats* stats;
+  long long wait_limit_us;             // bound of one wait for a parent's flag
+  int withhold;                        // test hook: this block's wait never sees its flag
+  int rpm = 0;                         // panel rows per CTA (set by the launcher)
+};
+extern bool g_disable_oi_cluster;      // force the per-wave launches (A/B checks)
+bool oi_cluster_fits(int c, int t_max, int max_nb, int max_deg, int min_nb);
+// Outside any stream capture: sets the kernel's attributes and returns in
+// *nclusters how many clusters run at once (at most max_wave);
+// BSP_ERR_INVALID_ARG when the cluster shape cannot be resident (the caller
+// falls back to the per-wave launches).
+int prepare_oi_cluster(const MeshView<float>& mv, int c, int max_nb, int max_deg, int max_wave,
+                       int* nclusters);
+int launch_oi_cluster(const MeshView<float>& mv, const OiClusterArgs& a, int max_nb, int max_deg,
+                      int nclusters, cudaStream_t s);
 
 // Projection / reconstruction (bsp_proj.cu)
 struct ProjArgs {
@@ -335,6 +363,9 @@ struct bsp_mesh {
   void* d_Ubf = nullptr;
   size_t cap_Ubf = 0;
   bool ubf_valid = false;
+  int* d_ready = nullptr;              // cluster engine: ready flags + abort word
+  size_t cap_ready = 0;
+  int engine_c = -1, engine_ncl = 0;   // engine prepared for width c: clusters (0: not usable)
   int32_t* d_spmm_chunks = nullptr;   // tiled operator product: 4 int32 per chunk
   int spmm_nchunks = 0, spmm_max_span = 0, spmm_max_nnz = 0;
   void* d_Ebf = nullptr;   // BF16 copy of the coefficients of a reconstruction call
