@@ -601,14 +601,21 @@ int enqueue_fixed(bsp_mesh* M, int c, int t_max, cudaStream_t s, int* launches) 
         return fail(rc, "launch failed (Onorm)");
     }
   }
-  // Rayleigh-Ritz does not change the spans the chain depends on, and no
-  // later wave reads its rotation: it runs once after the last wave, batched
-  // over the groups of ensure_rr_groups().
-  if (M->opts.rayleigh_ritz) {
+  // The engine leaves every block's basis after one CholeskyQR pass (same
+  // span, orthonormal to O(kappa^2 u)); the second pass, which no later block
+  // needs, runs here batched over all blocks.  Rayleigh-Ritz does not change
+  // the spans the chain depends on, and no later wave reads its rotation: it
+  // also runs once after the last wave.  Both use the groups of
+  // ensure_rr_groups().
+  if (engine || M->opts.rayleigh_ritz) {
     for (size_t g = 0; g + 1 < M->rr_group.size(); ++g) {
       const int g0 = M->rr_group[g], nbg = M->rr_group[g + 1] - g0;
       DenseArgs da{M->d_waves + g0, nbg, M->d_bptr, M->d_cb, M->c_cap, c, M->rr_wmax[g],
                    M->d_status};
+      if (engine &&
+          (rc = launch_cholqr2<T, TA>(da, U, U, (TA*)M->d_Gp_rr, (T*)M->d_Rsm_rr, s, launches, 1)))
+        return fail(rc, "launch failed (second CholeskyQR pass)");
+      if (!M->opts.rayleigh_ritz) continue;
       da.sweeps = &M->d_cgstats->jacobi_sweeps;
       rc = launch_rayleigh_ritz<T, TA>(da, view<T>(M), U, (TA*)M->d_Gp_rr, (T*)M->d_Rsm_rr,
                                        (T*)M->d_theta_rr, s, launches);
@@ -662,7 +669,7 @@ int track_fixed(bsp_mesh* M, int c, int t_max, const void* V0, cudaStream_t s) {
       M->engine_ncl = 0;
     M->engine_c = c;
   }
-  if (M->opts.rayleigh_ritz && (rc = ensure_rr_groups<T, TA>(M, c)) != BSP_OK) return rc;
+  if ((rc = ensure_rr_groups<T, TA>(M, c)) != BSP_OK) return rc;
   if (g_realloc && M->graph_exec) {
     cudaGraphExecDestroy(M->graph_exec);
     M->graph_exec = nullptr;

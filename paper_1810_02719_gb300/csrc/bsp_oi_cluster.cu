@@ -17,10 +17,10 @@
 //     reduce-scatter and broadcast; every CTA factorises the c x c Gram
 //     itself (identical inputs, identical results), with the factor's
 //     inverse built alongside on the identity, and applies it to its panel.
-//     The second pass, whose
-//     Gram is I + E with E of the order of kappa^2 u, uses the first-order
-//     factor I - (strict upper E + diag E / 2) when max |E| <= 1e-4 (its
-//     orthogonality error is 0.75 |E|^2), the full Cholesky otherwise;
+//     This is one CholeskyQR pass: its output spans the same subspace and is
+//     orthonormal to O(kappa^2 u), which is all the next solve needs.  The
+//     second pass, which only restores orthonormality to working precision,
+//     runs after the engine, batched over all blocks (the host enqueues it);
 //   * the orthonormal panel goes back to the column layout in the CTAs'
 //     shared memory, where the next block of the path reads its start (same
 //     size: row r of the child starts from row r of the parent), and to U in
@@ -40,7 +40,6 @@ constexpr int kNT = 512;                 // threads per CTA (16 warps)
 constexpr int kWarps = kNT / 32;
 constexpr int kCMax = 64;                // widest basis (16 CTAs x 4 columns)
 constexpr int kLDA = kCMax + 4;          // row stride of the c x c work matrices
-constexpr float kNearIdentity = 1e-4f;   // second-pass first-order threshold
 
 // ---------------------------------------------------------------- cluster helpers
 BSP_DEV uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -318,23 +317,25 @@ BSP_DEV void cg_group(const Pattern<MAXR, ELLW, WEIGHTED>& pat, float4* rs, floa
       for (int m = 0; m < MAXR; ++m) { p[m][j] = r[m][j]; s[m][j] = w[m][j]; }
     }
     int steps = 0, col_steps = 0;
+    // converged columns keep x and r (step length 0); no branches on the columns
     while (any) {
       if (steps >= max_steps) { cnt.unconverged = true; break; }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) col_steps += act[j] ? 1 : 0;
+      float ae[4], be[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        if (act[j] && !(dlt[j] > 0.f)) {   // (p, A p) <= 0: the recurrence broke down
-          cnt.breakdown = true;
-          act[j] = false;
-        }
-        if (!act[j]) continue;
-#pragma unroll
-        for (int m = 0; m < MAXR; ++m) {
-          x[m][j] += alpha[j] * p[m][j];
-          r[m][j] -= alpha[j] * s[m][j];
-        }
+        const bool ok = act[j] && dlt[j] > 0.f;   // (p, A p) <= 0: the recurrence broke down
+        cnt.breakdown = cnt.breakdown || (act[j] && !ok);
+        act[j] = ok;
+        col_steps += ok ? 1 : 0;
+        ae[j] = ok ? alpha[j] : 0.f;
       }
+#pragma unroll
+      for (int m = 0; m < MAXR; ++m)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          x[m][j] += ae[j] * p[m][j];
+          r[m][j] -= ae[j] * s[m][j];
+        }
       put_rows<MAXR>(rs, r, nbk);
       __syncthreads();
       pat.apply(rs, r, w);
@@ -351,22 +352,26 @@ BSP_DEV void cg_group(const Pattern<MAXR, ELLW, WEIGHTED>& pat, float4* rs, floa
       any = false;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        if (!act[j]) continue;
         const float gnew = sums[j], dnew = sums[4 + j];
-        if (!(gnew > bn2[j])) { act[j] = false; continue; }
-        const float beta = __fdividef(gnew, gam[j]);
-        const float den = dnew - beta * __fdividef(gnew, alpha[j]);
-        if (!(den > 0.f)) { cnt.breakdown = true; act[j] = false; continue; }
-        alpha[j] = __fdividef(gnew, den);
-        gam[j] = gnew;
-        dlt[j] = den;
-#pragma unroll
-        for (int m = 0; m < MAXR; ++m) {
-          p[m][j] = r[m][j] + beta * p[m][j];
-          s[m][j] = w[m][j] + beta * s[m][j];
-        }
-        any = true;
+        const bool go = act[j] && gnew > bn2[j];
+        const float beta = go ? __fdividef(gnew, gam[j]) : 0.f;
+        const float den = go ? dnew - beta * __fdividef(gnew, alpha[j]) : 1.f;
+        const bool ok = go && den > 0.f;
+        cnt.breakdown = cnt.breakdown || (go && !ok);
+        alpha[j] = ok ? __fdividef(gnew, den) : 0.f;
+        gam[j] = ok ? gnew : gam[j];
+        dlt[j] = ok ? den : dlt[j];
+        act[j] = ok;
+        be[j] = ok ? beta : 0.f;
+        any = any || ok;
       }
+#pragma unroll
+      for (int m = 0; m < MAXR; ++m)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          p[m][j] = r[m][j] + be[j] * p[m][j];
+          s[m][j] = w[m][j] + be[j] * s[m][j];
+        }
     }
     cnt.total += col_steps;
     cnt.max = max(cnt.max, steps);
@@ -383,8 +388,8 @@ struct Dense {
   float* Gp;     // [64 x 64] partial Gram of this CTA's panel (also the T buffer of the inverse)
   float* A;      // [64 x kLDA] the summed Gram, then R (upper)
   float* M;      // [64 x kLDA] the right factor applied to the panel
-  float4* PT;    // [64] rows K..K+3 of R, per column (Cholesky panel)
-  float* dinv;   // [16 x 16] inverses of R's 4 x 4 diagonal blocks
+  float4* PT;    // [144] rows K..K+7 of R, per column at col8(j) (Cholesky panel)
+  float* dinv;   // [2 x 64] inverses of R's 8 x 8 diagonal blocks (alternating)
   float* dsc;    // [64] Jacobi scaling
   float* red;    // 2 x 16 x 8 reduction buffer
   int* ctl;      // [8] cluster-uniform control words
@@ -457,44 +462,58 @@ BSP_DEV void gram_allreduce(const Dense& d, int q, int P, int cpad) {
   }
 }
 
-// Cholesky of a symmetric 4 x 4 block given by its upper entries a (in
-// registers), by one thread: writes W = R^-1 (upper, row-major 4 x 4) to w.
-// A non-positive or non-finite pivot is replaced by 1 and reported in *fail.
-BSP_DEV void factor4(const float (&a)[4][4], float* w, int* fail) {
-  float R[4][4], W[4][4];
+BSP_DEV float dot4(float4 a, float4 b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
+BSP_DEV float dot8(const float4* a, const float4* b) { return dot4(a[0], b[0]) + dot4(a[1], b[1]); }
+// Column j's 8 values in the per-column panels PT / BT: float4 index 2j + j/4
+// (16 bytes of skew every 4 columns, so the column groups 4 t that one warp
+// reads for different tiles t fall into different shared-memory banks).
+BSP_DEV int col8(int j) { return 2 * j + (j >> 2); }
+
+// Cholesky of the symmetric 8 x 8 diagonal block of A at (K, K) (upper
+// entries, already updated) by one thread, in registers: writes W = R^-1
+// (upper, row-major 8 x 8, zeros below) to w.  A non-positive or non-finite
+// pivot is replaced by 1 and reported in *fail.
+BSP_DEV void factor8(const float* A, int K, float* w, int* fail) {
+  float R[8][8], W[8][8];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    float s = a[q][q];
+  for (int q = 0; q < 8; ++q)
 #pragma unroll
-    for (int p = 0; p < q; ++p) s -= R[p][q] * R[p][q];
-    if (!(s > 0.f) || !isfinite(s)) { *fail = 1; s = 1.f; }
-    const float rq = rsqrtf(s);
-    R[q][q] = s * rq;
+    for (int r = q; r < 8; ++r) R[q][r] = A[(K + q) * kLDA + K + r];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    float sq = R[q][q];
+#pragma unroll
+    for (int p = 0; p < q; ++p) sq -= R[p][q] * R[p][q];
+    if (!(sq > 0.f) || !isfinite(sq)) { *fail = 1; sq = 1.f; }
+    const float rq = rsqrtf(sq);
+    R[q][q] = sq * rq;
     W[q][q] = rq;
 #pragma unroll
-    for (int r = q + 1; r < 4; ++r) {
-      float t = a[q][r];
+    for (int r = q + 1; r < 8; ++r) {
+      float t = R[q][r];
 #pragma unroll
       for (int p = 0; p < q; ++p) t -= R[p][q] * R[p][r];
       R[q][r] = t * rq;
     }
   }
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
+  for (int q = 0; q < 8; ++q)
 #pragma unroll
-    for (int r = q + 1; r < 4; ++r) {
+    for (int r = q + 1; r < 8; ++r) {
       float t = 0.f;
 #pragma unroll
       for (int p = q; p < r; ++p) t += W[q][p] * R[p][r];
       W[q][r] = -t * W[r][r];
     }
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
-    *reinterpret_cast<float4*>(w + 4 * q) =
-        make_float4(q <= 0 ? W[q][0] : 0.f, q <= 1 ? W[q][1] : 0.f, q <= 2 ? W[q][2] : 0.f, W[q][3]);
+  for (int q = 0; q < 8; ++q) {
+    float row[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) row[r] = r >= q ? W[q][r] : 0.f;
+    *reinterpret_cast<float4*>(w + 8 * q) = make_float4(row[0], row[1], row[2], row[3]);
+    *reinterpret_cast<float4*>(w + 8 * q + 4) = make_float4(row[4], row[5], row[6], row[7]);
+  }
 }
-
-BSP_DEV float dot4(float4 a, float4 b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
 
 // Upper-triangle tile (ti, tj) of a T x T tile grid, ti <= tj, from its
 // row-major index u (closed form, corrected by at most one step).
@@ -509,108 +528,117 @@ BSP_DEV void upper_tile(int T, int u, int& ti, int& tj) {
 }
 
 // M = D R^-1 for the Jacobi-scaled Cholesky D G D = R^T R (G in A's upper
-// triangle, rows and columns >= c already the identity).  Right-looking,
-// blocked by 4.  The elimination that turns D G D into R is applied to the
-// identity alongside (B, kept lower triangular in M's storage), which leaves
-// B = R^-T at the end: no separate inversion.  Per block step: thread 0 has
-// already factorised the diagonal block (W = R_KK^-1); the threads of the cpad
-// columns form the block's rows of R (PT) and of B (BT); then every trailing
-// entry of A and every entry of B below the block is updated, while thread 0
-// updates and factorises the next diagonal block in registers.  Two barriers
-// per block step.  Ends with a barrier.
+// triangle, rows and columns >= c already the identity; padded to a multiple
+// of 8 with the identity).  Right-looking, blocked by 8.  The elimination
+// that turns D G D into R is applied to the identity alongside (B, lower
+// triangular, in M's storage), which leaves B = R^-T: no separate inversion.
+// Per block step: W = R_KK^-1 is known; the threads of the columns form the
+// block's 8 rows of R (PT) and of B (BT); then warp 0 updates the next
+// diagonal block and one lane factorises it in registers, while the other
+// warps update the trailing part of A and the rows of B below the block.
+// Two barriers per block step.  Ends with a barrier.
 BSP_DEV void chol_inverse(const Dense& d, int cpad) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = cpad >> 2;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int cp8 = (cpad + 7) & ~7, nt = cp8 >> 3;
   float* A = d.A;
   float* B = d.M;
-  float4* BT = reinterpret_cast<float4*>(d.Gp);   // new rows K..K+3 of B, per column
-  for (int i = tid; i < cpad; i += kNT) {
-    const float g = A[i * kLDA + i];
-    const bool ok = g > 0.f && isfinite(g);
-    if (!ok) d.ctl[1] = 1;
-    d.dsc[i] = ok ? rsqrtf(g) : 1.f;
+  float4* PT = d.PT;                                // 8 rows of R per column at col8(j)
+  float4* BT = reinterpret_cast<float4*>(d.Gp);     // 8 new rows of B per column
+  for (int i = tid; i < cp8; i += kNT) {
+    float sc = 1.f;
+    if (i < cpad) {
+      const float g = A[i * kLDA + i];
+      const bool ok = g > 0.f && isfinite(g);
+      if (!ok) d.ctl[1] = 1;
+      sc = ok ? rsqrtf(g) : 1.f;
+    }
+    d.dsc[i] = sc;
   }
   __syncthreads();
-  for (int i = warp; i < cpad; i += kWarps)
-    for (int j = lane; j < cpad; j += 32) {
-      if (j >= i) A[i * kLDA + j] *= d.dsc[i] * d.dsc[j];
+  for (int i = warp; i < cp8; i += kWarps)
+    for (int j = lane; j < cp8; j += 32) {
+      if (i >= cpad || j >= cpad) A[i * kLDA + j] = i == j ? 1.f : 0.f;
+      else if (j >= i) A[i * kLDA + j] *= d.dsc[i] * d.dsc[j];
       B[i * kLDA + j] = i == j ? 1.f : 0.f;
     }
   __syncthreads();
-  if (tid == 0) {
-    float a[4][4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int r = q; r < 4; ++r) a[q][r] = A[q * kLDA + r];
-    factor4(a, d.dinv, &d.ctl[1]);
-  }
+  if (tid == 0) factor8(A, 0, d.dinv, &d.ctl[1]);
   __syncthreads();
   for (int kb = 0; kb < nt; ++kb) {
-    const int K = 4 * kb;
-    const float* W = d.dinv + kb * 16;
-    // rows K..K+3 of R (A columns > K+3) and of B (B columns <= K+3): x <- W^T x
-    if (tid < cpad) {
+    const int K = 8 * kb;
+    const float* W = d.dinv + (kb & 1) * 64;
+    // rows K..K+7 of R (A columns > K+7) and of B (B columns <= K+7): x <- W^T x
+    if (tid < cp8) {
       const int j = tid;
-      const bool inB = j < K + 4;
+      const bool inB = j < K + 8;
       const float* src = inB ? B : A;
-      const float a0 = src[K * kLDA + j], a1 = src[(K + 1) * kLDA + j],
-                  a2 = src[(K + 2) * kLDA + j], a3 = src[(K + 3) * kLDA + j];
-      const float r0 = W[0] * a0;
-      const float r1 = W[1] * a0 + W[5] * a1;
-      const float r2 = W[2] * a0 + W[6] * a1 + W[10] * a2;
-      const float r3 = W[3] * a0 + W[7] * a1 + W[11] * a2 + W[15] * a3;
+      float a[8], r[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) a[q] = src[(K + q) * kLDA + j];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        float t = 0.f;
+#pragma unroll
+        for (int p = 0; p <= q; ++p) t += W[p * 8 + q] * a[p];
+        r[q] = t;
+      }
+      const float4 lo = make_float4(r[0], r[1], r[2], r[3]), hi = make_float4(r[4], r[5], r[6], r[7]);
       if (inB) {
-        B[K * kLDA + j] = r0;
-        B[(K + 1) * kLDA + j] = r1;
-        B[(K + 2) * kLDA + j] = r2;
-        B[(K + 3) * kLDA + j] = r3;
-        BT[j] = make_float4(r0, r1, r2, r3);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) B[(K + q) * kLDA + j] = r[q];
+        BT[col8(j)] = lo;
+        BT[col8(j) + 1] = hi;
       } else {
-        d.PT[j] = make_float4(r0, r1, r2, r3);
+        PT[col8(j)] = lo;
+        PT[col8(j) + 1] = hi;
       }
     }
     __syncthreads();
     if (kb + 1 == nt) break;
-    const int T = nt - kb - 1, K1 = K + 4;
-    const int na = 4 * (T * (T + 1) / 2 - 1);   // trailing A tile rows but the next diagonal tile
-    const int nb = 4 * T * (kb + 1);            // B rows below the block x column tiles <= kb
-    const float inv_cols = 1.f / (float)(kb + 1);
-    if (tid == 0) {
-      float4 pr[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) pr[q] = d.PT[K1 + q];
-      float a[4][4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int r = q; r < 4; ++r) a[q][r] = A[(K1 + q) * kLDA + K1 + r] - dot4(pr[q], pr[r]);
-      factor4(a, d.dinv + (kb + 1) * 16, &d.ctl[1]);
-    }
-    for (int it = tid - 1; it >= 0 && it < na + nb; it += kNT - 1) {   // threads 1 .. kNT-1
-      if (it < na) {
-        const int ii = it & 3;
-        int ti, tj;
-        upper_tile(T, (it >> 2) + 1, ti, tj);
-        const int i = K1 + 4 * ti + ii, j0 = K1 + 4 * tj;
-        const float4 pi = d.PT[i];
-        float4 v = *reinterpret_cast<float4*>(A + i * kLDA + j0);
-        v.x -= dot4(pi, d.PT[j0]);
-        v.y -= dot4(pi, d.PT[j0 + 1]);
-        v.z -= dot4(pi, d.PT[j0 + 2]);
-        v.w -= dot4(pi, d.PT[j0 + 3]);
-        *reinterpret_cast<float4*>(A + i * kLDA + j0) = v;
-      } else {
-        const int e = it - na;
-        const int row = __float2int_rz(((float)e + 0.5f) * inv_cols);
-        const int t = e - row * (kb + 1);
-        const int i = K1 + row, j0 = 4 * t;
-        const float4 pi = d.PT[i];
-        float4 v = *reinterpret_cast<float4*>(B + i * kLDA + j0);
-        v.x -= dot4(pi, BT[j0]);
-        v.y -= dot4(pi, BT[j0 + 1]);
-        v.z -= dot4(pi, BT[j0 + 2]);
-        v.w -= dot4(pi, BT[j0 + 3]);
-        *reinterpret_cast<float4*>(B + i * kLDA + j0) = v;
+    const int K8 = K + 8;
+    if (warp == 0) {
+      // next diagonal block: its 36 upper entries, then one lane factorises it
+      for (int e = lane; e < 36; e += 32) {
+        int q = 0, rem = e;
+        while (rem >= 8 - q) { rem -= 8 - q; ++q; }
+        const int r = q + rem;
+        A[(K8 + q) * kLDA + K8 + r] -= dot8(PT + col8(K8 + q), PT + col8(K8 + r));
+      }
+      __syncwarp();
+      if (lane == 0) factor8(A, K8, d.dinv + ((kb + 1) & 1) * 64, &d.ctl[1]);
+    } else {
+      const int t0 = K8 >> 2, T = (cp8 >> 2) - t0;    // trailing 4 x 4 tile grid
+      const int na = 4 * (T * (T + 1) / 2 - 3);        // but the next diagonal block's 3 tiles
+      const int nb = (cp8 - K8) * (K8 >> 2);           // B rows below x column groups
+      const float inv_g = 1.f / (float)(K8 >> 2);
+      for (int it = tid - 32; it < na + nb; it += kNT - 32) {
+        if (it < na) {
+          // skip tiles (0,0), (0,1) (u = 0, 1) and (1,1) (u = T)
+          int u = (it >> 2) + 2;
+          if (u >= T) ++u;
+          int ti, tj;
+          upper_tile(T, u, ti, tj);
+          const int i = 4 * (t0 + ti) + (it & 3), j0 = 4 * (t0 + tj);
+          const float4* pi = PT + col8(i);
+          float4 v = *reinterpret_cast<float4*>(A + i * kLDA + j0);
+          v.x -= dot8(pi, PT + col8(j0));
+          v.y -= dot8(pi, PT + col8(j0 + 1));
+          v.z -= dot8(pi, PT + col8(j0 + 2));
+          v.w -= dot8(pi, PT + col8(j0 + 3));
+          *reinterpret_cast<float4*>(A + i * kLDA + j0) = v;
+        } else {
+          const int e = it - na;
+          const int row = __float2int_rz(((float)e + 0.5f) * inv_g);
+          const int g = e - row * (K8 >> 2);
+          const int i = K8 + row, j0 = 4 * g;
+          const float4* pi = PT + col8(i);
+          float4 v = *reinterpret_cast<float4*>(B + i * kLDA + j0);
+          v.x -= dot8(pi, BT + col8(j0));
+          v.y -= dot8(pi, BT + col8(j0 + 1));
+          v.z -= dot8(pi, BT + col8(j0 + 2));
+          v.w -= dot8(pi, BT + col8(j0 + 3));
+          *reinterpret_cast<float4*>(B + i * kLDA + j0) = v;
+        }
       }
     }
     __syncthreads();
@@ -623,39 +651,6 @@ BSP_DEV void chol_inverse(const Dense& d, int cpad) {
       if (j > i) B[j * kLDA + i] = 0.f;
     }
   __syncthreads();
-}
-
-// Second CholeskyQR pass when the Gram of the orthonormalised panel is
-// I + E with max |E| <= kNearIdentity: M = I - (strict upper E + diag(E)/2),
-// the first-order inverse Cholesky factor of I + E.  Ends with a barrier.
-BSP_DEV void near_identity_factor(const Dense& d, int cpad) {
-  for (int e = threadIdx.x; e < cpad * cpad; e += kNT) {
-    const int i = e / cpad, j = e - i * cpad;
-    const float a = d.A[i * kLDA + j];
-    d.M[i * kLDA + j] = j > i ? -a : (j == i ? 1.5f - 0.5f * a : 0.f);
-  }
-  __syncthreads();
-}
-
-// max over i <= j < cpad of |A_ij - delta_ij|, CTA-wide (same value in every thread).
-BSP_DEV float max_dev_identity(const Dense& d, int cpad) {
-  float m = 0.f;
-  for (int e = threadIdx.x; e < cpad * cpad; e += kNT) {
-    const int i = e / cpad, j = e - i * cpad;
-    if (j >= i) {
-      const float a = d.A[i * kLDA + j] - (i == j ? 1.f : 0.f);
-      m = fmaxf(m, isfinite(a) ? fabsf(a) : INFINITY);
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) d.red[threadIdx.x >> 5] = m;
-  __syncthreads();
-  float r = 0.f;
-#pragma unroll
-  for (int w = 0; w < kWarps; ++w) r = fmaxf(r, d.red[w]);
-  __syncthreads();
-  return r;
 }
 
 // S <- S M for the panel (nr rows, cpad columns; M upper triangular).  Warp
@@ -727,8 +722,8 @@ __global__ void __launch_bounds__(kNT, 1) k_oi_cluster(MeshView<float> mv, OiClu
   d.A = d.Gp + 64 * 64;
   d.M = d.A + 64 * kLDA;
   d.PT = reinterpret_cast<float4*>(d.M + 64 * kLDA);
-  d.dinv = reinterpret_cast<float*>(d.PT + 64);
-  d.dsc = d.dinv + 256;
+  d.dinv = reinterpret_cast<float*>(d.PT + 144);
+  d.dsc = d.dinv + 128;
   d.red = d.dsc + 64;
   d.ctl = reinterpret_cast<int*>(d.red + 2 * kWarps * 8 + kWarps);
   if (tid < 8) d.ctl[tid] = 0;
@@ -755,9 +750,7 @@ __global__ void __launch_bounds__(kNT, 1) k_oi_cluster(MeshView<float> mv, OiClu
       for (int i = c + tid; i < cpad; i += kNT) d.A[i * kLDA + i] = 1.f;   // padded columns
       if (tid == 0) d.ctl[1] = 0;
       __syncthreads();
-      const bool near = pass > 0 && max_dev_identity(d, cpad) <= kNearIdentity;
-      if (near) near_identity_factor(d, cpad);
-      else chol_inverse(d, cpad);
+      chol_inverse(d, cpad);
       if (d.ctl[1]) failed = 1;
       apply_right(S, nr, ldp, cpad, d.M);
     }
@@ -833,7 +826,7 @@ __global__ void __launch_bounds__(kNT, 1) k_oi_cluster(MeshView<float> mv, OiClu
         S[lr * ldp + j] = v;
       }
       __syncthreads();
-      onorm(r0, rp, nr, 2, false);
+      onorm(r0, rp, nr, 1, false);
     } else if (p != prev) {
       // same-size parent computed elsewhere: its rows, this CTA's 4 columns
       const float* Up = a.U + (size_t)mv.bptr[p] * a.ld;
@@ -864,7 +857,7 @@ __global__ void __launch_bounds__(kNT, 1) k_oi_cluster(MeshView<float> mv, OiClu
       }
       cluster_sync();
       t += g;
-      onorm(r0, rp, nr, t == sub ? 2 : 1, t == sub);
+      onorm(r0, rp, nr, 1, t == sub);
     }
     if (flags && q == 0 && tid == 0) st_release(a.ready + b, 1);
     prev = b;
@@ -886,7 +879,7 @@ template <int MAXR>
 size_t oi_cluster_smem(int P, int rpm) {
   const int ldp = 4 * P + 4;
   return (size_t)(MAXR * kNT + 1) * 16 + (size_t)rpm * ldp * 4 + 64 * 64 * 4 + 2 * 64 * kLDA * 4 +
-         64 * 16 + 256 * 4 + 64 * 4 + (2 * kWarps * 8 + kWarps) * 4 + 8 * 4;
+         144 * 16 + 128 * 4 + 64 * 4 + (2 * kWarps * 8 + kWarps) * 4 + 8 * 4;
 }
 
 template <int MAXR, int ELLW, bool W>
@@ -936,11 +929,14 @@ int dispatch(const MeshView<float>& mv, OiClusterArgs a, int max_nb, int max_deg
              bool query, cudaStream_t s, int* nclusters) {
   const int P = (a.c + 3) / 4;
   a.rpm = (((max_nb + P - 1) / P) + 3) & ~3;
-  const bool two = max_nb > kNT, wide = max_deg > 8;
-  if (!two) return wide ? launch_w<1, 16>(mv, a, P, ncl, query, s, nclusters)
-                        : launch_w<1, 8>(mv, a, P, ncl, query, s, nclusters);
-  return wide ? launch_w<2, 16>(mv, a, P, ncl, query, s, nclusters)
-              : launch_w<2, 8>(mv, a, P, ncl, query, s, nclusters);
+  const bool two = max_nb > kNT;
+  const int w = max_deg <= 6 ? 6 : max_deg <= 8 ? 8 : 16;   // ELL width
+  if (!two) return w == 6 ? launch_w<1, 6>(mv, a, P, ncl, query, s, nclusters)
+                   : w == 8 ? launch_w<1, 8>(mv, a, P, ncl, query, s, nclusters)
+                            : launch_w<1, 16>(mv, a, P, ncl, query, s, nclusters);
+  return w == 6 ? launch_w<2, 6>(mv, a, P, ncl, query, s, nclusters)
+       : w == 8 ? launch_w<2, 8>(mv, a, P, ncl, query, s, nclusters)
+                : launch_w<2, 16>(mv, a, P, ncl, query, s, nclusters);
 }
 
 }  // namespace
