@@ -6,6 +6,14 @@ noise), 1,024 blocks of 32 x 32 vertices in one warm-start chain (raster
 order), c = 64, 2 OI steps per block, Rayleigh-Ritz, then E = U^T X and
 X~ = U E for the xyz coordinates.  Metric: Mvertices/s.
 
+With N = 1 the line also carries, measured outside the timed region: the
+FP64 oracle on the host's cores (the chain's Algorithm 1 and the per-block
+eigendecomposition), the per-block dense eigensolver on the GPU, and the
+other workloads: ~2,000 uneven BFS blocks with dynamic c (with its
+one-block-per-launch and padded dense-eigh baselines and the subspace
+accuracy of both OI forms), 200 frames projected at once, and the
+differentiable filter (`--extras 0` leaves them out).
+
 Timing: W warm-up steps, then K steps, each bracketed by CUDA events on the
 launching stream; between steps a 512 MB buffer is written to flush L2 (the
 per-step inputs are smaller than L2).  Under torchrun every rank runs its own
@@ -113,6 +121,35 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def source_sha(rel):
+    """First 12 hex digits of the SHA-256 of a source file (relative to the repo)."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            return hashlib.sha256(f.read()).hexdigest()[:12]
+    except OSError:
+        return None
+
+
+def captured_traffic(kernel):
+    """DRAM bytes (read + write) per full-size launch of `kernel` from the ncu
+    capture recorded in profiles/dram_traffic.txt, or None when there is no
+    record or the kernel's source file has changed since the capture (the
+    record stores the file's hash).  Line format:
+    kernel source_file sha256_12 bytes_per_launch scale note..."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.txt")) as f:
+            lines = [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+    except OSError:
+        return None
+    for f in lines:
+        if len(f) >= 5 and f[0] == kernel:
+            if source_sha(f[1]) != f[2]:
+                return None
+            return float(f[3]) * float(f[4])
+    return None
+
+
 def slowest_rank_time(total_s, device=None):
     """Max over ranks of each rank's timed total (the job's wall time); the
     only collective of the multi-GPU run.  Identity without a process group."""
@@ -156,8 +193,10 @@ def run_ours(args, rank, world, device):
         return launches + 2
 
     # untimed: the CG layout picked by the library's autotuner on this mesh
+    # (it steers the per-wave launches; the FP32 chain runs on the persistent
+    # cluster engine, which has no such layout)
     tuned = None
-    if args.cs == 0:
+    if args.cs == 0 and args.precision != "f32":
         chosen, tt = bsp.bsp_autotune(h, args.c, args.t, V0, reps=2, stream=stream)
         tuned = {"cols_per_cta": chosen, "candidates_ms": tt}
 
@@ -221,13 +260,28 @@ def run_ours(args, rank, world, device):
     nb = args.tile * args.tile
     k = len(ptr) - 1
     c = args.c
+    nnz_row = prof_stats["nnz"] / n
+    # one CG column-step per row: the product (L + delta I) p (2 flops per
+    # stored entry and the diagonal) and ~10 vector flops; every solve also
+    # has two start-up products per column
+    per_col_step = 2.0 * (nnz_row + 1.0) + 10.0
+    solves = args.t
+    cg_flops = (prof_stats["cg_steps_total"] + 2.0 * solves * c * k) * nb * per_col_step
+    # one CholeskyQR pass: Gram (upper half, n c (c + 1)), triangular product
+    # Q = Y R^-1 (n c (c + 1)), Cholesky (c^3 / 3); a warm-started block has one
+    # pass on the engine, the root three (its start, then one per solve)
+    roots = int((np.asarray(parent) < 0).sum())
+    pass_flops = 2.0 * nb * c * (c + 1) + c ** 3 / 3.0
+    onorm_flops = (k + 2 * roots) * pass_flops
     # algorithmic FP32 flops of every kernel class over the profiled step
     work = {
+        "oi": (cg_flops + onorm_flops,
+               "k_oi_cluster (persistent cluster engine: every block's CG solves and one "
+               "CholeskyQR pass on one cluster of c/4 CTAs, blocks in chain order)"),
         # fused Onorm: Gram (2 n c^2) + Cholesky (c^3 / 3) + TRSM (n c^2) per pass;
         # a warm-started block's two solves share one two-pass launch
-        "chol": (2 * kernels.get("chol", {"launches": 0})["launches"] *
-                 (3.0 * nb * c ** 2 + c ** 3 / 3.0),
-                 "k_cholqr2_cluster (fused CholeskyQR2, one 8-CTA cluster per block)"),
+        "chol": (k * pass_flops,
+                 "k_cholqr2_cluster (second CholeskyQR pass, all blocks in one launch)"),
         # CG: one SpMV (2 flops per nonzero, ~6.75 per row) + ~10 vector flops per row per step
         "cg": (prof_stats["cg_steps_total"] * nb * (2.0 * 6.75 + 10),
                "k_cg1 (register-ELL CG, one column per CTA)"),
@@ -244,13 +298,17 @@ def run_ours(args, rank, world, device):
             "achieved": flops / (kernels[dom]["ms"] * 1e-3) / 1e12, "peak": peak_f32,
             "peak_source": "derived: 152 SM x 128 FP32 FMA/clk x 2 x median SM clock under load",
             "algorithmic_flops_per_launch": flops / kernels[dom]["launches"],
-            "critical_path": {kc: kernels[kc]["ms"] for kc in kernels}}
+            "critical_path": {kc: kernels[kc]["ms"] for kc in kernels},
+            "critical_path_how": "one more step run eagerly with CUDA events around every "
+                                 "launch (outside the timed region, same kernels)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["avg_launch_s"] = kernels[dom]["ms"] * 1e-3 / kernels[dom]["launches"]
-    # DRAM bytes of one launch of the per-block kernels from the committed ncu
-    # capture (profiles/ncu_full_cholqr2_cg1_jacobi_torus256_chain_c64.md); the
-    # per-block data stays in L2
-    roof["traffic"] = {"chol": 404.7e3, "cg": 309.5e3}.get(dom)
+    if dom == "oi":
+        # the chain runs on one cluster: c/4 of the 152 SMs
+        roof["sms_used"] = (c + 3) // 4
+        roof["cg_flops"], roof["onorm_flops"] = cg_flops, onorm_flops
+    roof["traffic"] = captured_traffic({"oi": "k_oi_cluster", "chol": "k_cholqr2_cluster"}.get(
+        dom, dom))
 
     # standalone operator product (L + delta I) P over all blocks, c columns (HBM-bound)
     P = torch.randn(n, args.c, device=device)
@@ -275,8 +333,8 @@ def run_ours(args, rank, world, device):
                            "in shared memory)", "bound": "hbm",
                  "achieved": achieved, "peak": peak_hbm, "peak_source": peak_kind, "unit": "GB/s",
                  "frac": achieved / peak_hbm,
-                 # profiles/ncu_full_spmm_tile_torus1M_c64.md (unchanged kernel)
-                 "traffic": 516.4e6, "algorithmic_bytes": alg_bytes,
+                 "traffic": captured_traffic("k_spmm_tile") if args.c == 64 else None,
+                 "algorithmic_bytes": alg_bytes,
                  "avg_launch_s": t_spmm}
 
     def device_time(fn, reps=10):
@@ -409,6 +467,81 @@ def denoise_report(bsp, args, h, xyz, faces, dfaces, k, n, device, stream, devic
 _ORACLE_SETUP = {}
 
 
+def _pin_blas_threads(n):
+    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = str(n)
+
+
+def _oracle_worker(job):
+    """Spawned process: the oracle's chain sample with `threads` BLAS threads."""
+    grid, tile, c, t, budget = job
+    a = argparse.Namespace(grid=grid, tile=tile, c=c, t=t)
+    return oracle_sample(a, budget)
+
+
+def _eigh_worker(job):
+    """Spawned process (one BLAS thread): FP64 eigh of dense block Laplacians
+    with the first c eigenvectors and the projection of xyz, for as many of the
+    given blocks as fit in the time budget (the paper's per-block "SVD")."""
+    from oracle import bsp_oracle as O
+    grid, tile, c, blocks, budget = job
+    xyz, faces = synth.torus(grid, seed=0)
+    ptr, verts = synth.tile_partition(grid, tile)
+    om = O.build_mesh(xyz.shape[0], ptr, verts, synth.raster_chain(len(ptr) - 1), faces=faces)
+    t0 = time.perf_counter()
+    done = 0
+    for b in blocks:
+        L = O.laplacian(om.blocks[b])
+        U, _ = O.eigh_basis(L, c)
+        Xb = xyz[om.blocks[b].verts]
+        _ = U @ (U.T @ Xb)
+        done += 1
+        if time.perf_counter() - t0 > budget:
+            break
+    return done, time.perf_counter() - t0
+
+
+def cpu_baselines(args, budget_s):
+    """The FP64 oracle on this host's cores, in spawned processes (safe next to
+    a live CUDA context): (i) Algorithm 1 on the chain's first blocks in one
+    process with all cores as BLAS threads (the chain is sequential), (ii) the
+    per-block eigendecomposition on a pool of one-thread workers, one per core
+    (blocks are independent)."""
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    ctx = mp.get_context("spawn")
+    saved = {v: os.environ.get(v) for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS",
+                                            "MKL_NUM_THREADS")}
+    try:
+        _pin_blas_threads(cores)
+        with ctx.Pool(1) as pool:
+            v, blocks, dt, _ = pool.apply(_oracle_worker,
+                                          ((args.grid, args.tile, args.c, args.t, budget_s),))
+        oi = {"value": v, "unit": "Mvertices/s", "cores": cores, "kind": "oracle",
+              "sample": f"Algorithm 1 on the first {blocks} of {(args.grid // args.tile) ** 2} "
+                        f"chain blocks in {dt:.1f} s (sequential chain, FP64 NumPy/LAPACK, "
+                        f"{cores} BLAS threads)"}
+        _pin_blas_threads(1)
+        k = (args.grid // args.tile) ** 2
+        per = [list(range(w, k, cores)) for w in range(cores)]
+        with ctx.Pool(cores) as pool:
+            res = pool.map(_eigh_worker, [(args.grid, args.tile, args.c, blk, budget_s / 2)
+                                          for blk in per])
+        nblk = sum(r[0] for r in res)
+        wall = max(r[1] for r in res)
+        eig = {"value": nblk * args.tile * args.tile / wall / 1e6, "unit": "Mvertices/s",
+               "cores": cores, "kind": "oracle per-block eigh",
+               "sample": f"{nblk} blocks on {cores} one-thread workers in {wall:.1f} s (FP64 "
+                         f"numpy.linalg.eigh, first c eigenvectors, projection)"}
+    finally:
+        for kk, vv in saved.items():
+            if vv is None:
+                os.environ.pop(kk, None)
+            else:
+                os.environ[kk] = vv
+    return oi, eig
+
+
 def oracle_sample(args, budget_s):
     """Time the oracle's Algorithm 1 chain on the first blocks of the workload
     (mesh generation and the oracle's edge lists are built once, untimed)."""
@@ -437,7 +570,74 @@ def oracle_sample(args, budget_s):
     return done * nb / dt / 1e6, done, dt, cores
 
 
-def run_batched(args, device):
+def block_dense(bsp, h, b, nb, m, pad_value=None):
+    """Dense FP64 Laplacian of block b (nb rows) from the library's CSR, padded
+    to m x m; the padding diagonal is pad_value, or 10 x the block's Gershgorin
+    bound when pad_value is None (host, numpy)."""
+    rp, cols, vals, diag = bsp.bsp_get_block_csr(h, b, nb)
+    rows = np.repeat(np.arange(nb), np.diff(rp))
+    L = np.zeros((m, m))
+    L[rows, cols.astype(np.int64)] = -vals
+    L[np.arange(nb), np.arange(nb)] = diag
+    if m > nb:
+        if pad_value is None:
+            bound = float((diag + np.bincount(rows, weights=np.abs(vals), minlength=nb)).max())
+            pad_value = 10.0 * bound
+        L[np.arange(nb, m), np.arange(nb, m)] = pad_value
+    return L
+
+
+def eigh_bucket_baseline(bsp, h, sizes, cb, X, verts, ptr, device, stream):
+    """The paper's per-block eigendecomposition ("SVD") on the same GPU for the
+    uneven blocks: dense FP32 block Laplacians padded to size buckets (512,
+    1,024, 2,048, 3,072; padding diagonal 10 x the block's Gershgorin bound so
+    the padded rows sort last), batched torch.linalg.eigh (cuSOLVER) per chunk,
+    the first c_b eigenvectors, projection and reconstruction of xyz.  Timed
+    with CUDA events around the eigh and the products (the dense assembly is
+    untimed)."""
+    import torch
+    k = len(sizes)
+    total, per_bucket = 0.0, {}
+    lo = 0
+    for m in (512, 1024, 2048, 3072):
+        ids = [b for b in range(k) if lo < sizes[b] <= m]
+        lo = m
+        if not ids:
+            continue
+        chunk = max(1, min(len(ids), int(1.5e9 // (m * m * 4 * 3))))
+        t_b = 0.0
+        for c0 in range(0, len(ids), chunk):
+            part = ids[c0:c0 + chunk]
+            Ls = np.empty((len(part), m, m), np.float32)
+            Xb = np.zeros((len(part), m, 3), np.float32)
+            for q, b in enumerate(part):
+                Ls[q] = block_dense(bsp, h, b, int(sizes[b]), m)
+                Xb[q, :sizes[b]] = X[verts[ptr[b]:ptr[b + 1]]]
+            Ld = torch.from_numpy(Ls).to(device)
+            Xd = torch.from_numpy(Xb).to(device)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lam, W = torch.linalg.eigh(Ld)
+            for q, b in enumerate(part):
+                Ub = W[q, :, :int(cb[b])]
+                _ = Ub @ (Ub.T @ Xd[q])
+            e1.record(stream)
+            e1.synchronize()
+            t_b += e0.elapsed_time(e1) / 1e3
+            del Ld, Xd, lam, W
+        per_bucket[str(m)] = {"blocks": len(ids), "s": t_b}
+        total += t_b
+    n = int(sum(sizes))
+    return {"value": n / total / 1e6, "unit": "Mvertices/s", "seconds": total,
+            "buckets": per_bucket,
+            "how": "torch.linalg.eigh (cuSOLVER) on dense FP32 block Laplacians padded to "
+                   "size buckets (padding diagonal 10 x Gershgorin bound), first c_b "
+                   "eigenvectors (the batched OI's widths), project+reconstruct xyz"}
+
+
+def run_batched(args, device, compare=False):
     """Uneven blocks with dynamic c: the 1024x1024 torus (1,048,576 v) cut by seeded
     BFS region growing into ~2,000 blocks of 300-3,000 vertices, a BFS forest of
     warm starts with several roots (every topological level of the forest is one
@@ -502,6 +702,16 @@ def run_batched(args, device):
     step()
     kt = bsp.bsp_get_kernel_times(h)
     bsp.bsp_set_profiling(h, 0)
+    # sampled blocks for the comparison with the exact eigenbasis
+    sample = []
+    if compare:
+        order = np.argsort(sizes)
+        sample = [int(order[int(q * (k - 1) / 11)]) for q in range(12)]
+    bases = {b: bsp.bsp_get_basis(h, b, int(sizes[b])).astype(np.float64)[:, :int(cb[b])]
+             for b in sample}
+    eig = eigh_bucket_baseline(bsp, h, sizes, cb, xyz, verts, ptr, device, stream) \
+        if compare else None
+    dense = {b: block_dense(bsp, h, b, int(sizes[b]), int(sizes[b])) for b in sample}
     # relative reconstruction error per block against the target
     Xon = Xo.cpu().double().numpy()
     errs = np.array([np.linalg.norm(Xon[verts[ptr[b]:ptr[b + 1]]] - xyz[verts[ptr[b]:ptr[b + 1]]]) /
@@ -531,6 +741,8 @@ def run_batched(args, device):
         Xp = Xo.cpu().double().numpy()
         ep = np.array([np.linalg.norm(Xp[verts[ptr[b]:ptr[b + 1]]] - xyz[verts[ptr[b]:ptr[b + 1]]]) /
                        np.linalg.norm(xyz[verts[ptr[b]:ptr[b + 1]]]) for b in range(k)])
+        pbases = {b: bsp.bsp_get_basis(h1, b, int(sizes[b])).astype(np.float64)[:, :int(cp[b])]
+                  for b in sample}
         plain = {"value": n / tp / 1e6, "unit": "Mvertices/s", "ms_per_step": 1e3 * tp,
                  "how": "same blocks chained in index order (one block per launch), FP32, "
                         "same dynamic-c target; one timed step",
@@ -540,6 +752,31 @@ def run_batched(args, device):
     levels = np.zeros(k, int)
     for b in range(k):
         levels[b] = 0 if parent[b] < 0 else levels[parent[b]] + 1
+    accuracy = None
+    if sample:
+        # principal-angle sines of the tracked bases against the exact lowest
+        # c_b eigenvectors (FP64 eigh on the host), for both OI forms
+        rows = []
+        for b in sample:
+            lam, W = np.linalg.eigh(dense[b])
+            ent = {"block": b, "n_b": int(sizes[b])}
+            for name, B in (("batched", bases), ("plain", pbases if plain else {})):
+                if b not in B:
+                    continue
+                U = B[b]
+                cc = U.shape[1]
+                sv = np.linalg.svd(W[:, :cc].T @ U, compute_uv=False)
+                ent[f"{name}_c"] = cc
+                ent[f"{name}_max_sine"] = float(np.sqrt(max(0.0, 1.0 - sv.min() ** 2)))
+                ent[f"{name}_gap_ratio"] = float((lam[cc] - lam[cc - 1]) / lam[cc])
+            rows.append(ent)
+        accuracy = {"vs": "exact FP64 eigh of the block Laplacian, first c_b eigenvectors",
+                    "blocks": rows,
+                    "batched_median_max_sine": float(np.median([r["batched_max_sine"]
+                                                                for r in rows])),
+                    "plain_median_max_sine": float(np.median([r["plain_max_sine"] for r in rows
+                                                              if "plain_max_sine" in r]))
+                    if plain else None}
     return {
         "value": job_value(n, 1, args.steps, total), "unit": "Mvertices/s",
         "ms_per_step": 1e3 * total / args.steps, "blocks_per_s": k * args.steps / total,
@@ -556,6 +793,8 @@ def run_batched(args, device):
                   "not_converged": st["not_converged"]},
         "autotune": {"cols_per_cta": chosen, "candidates_ms_fixed_c32": tt},
         "plain_one_block_per_launch": plain,
+        "eigh_baseline_padded_buckets": eig,
+        "subspace_accuracy": accuracy,
     }
 
 
@@ -678,7 +917,7 @@ def run_spmm(args, device):
             "ms_per_step": first["us"] * 1e-3,
             "roofline": {"kernel": "k_spmm_tile", "bound": "hbm", "achieved": first["GB/s"],
                          "peak": peak, "peak_source": kind, "unit": "GB/s", "frac": first["frac"],
-                         "traffic": 516.4e6 if args.c == 64 else None,
+                         "traffic": captured_traffic("k_spmm_tile") if args.c == 64 else None,
                          "algorithmic_bytes": first["algorithmic_bytes"],
                          "avg_launch_s": first["us"] * 1e-6},
             "by_width": out}
@@ -786,20 +1025,43 @@ def run_frames(args, device):
                      "note": "API calls (each ends with a stream synchronise and a status read)"},
         "kernel_ms": {"k_project_tc": 1e3 * k_pbf, "k_recon_tc": 1e3 * k_rbf},
         "rel_err_vs_fp64_oracle_first4blocks": errs,
-        # traffic: dram__bytes_read.sum + dram__bytes_write.sum of one launch
-        # (profiles/ncu_full_project_recon_tc_frames512x200_c48.md)
         "roofline": {"kernel": "k_project_tc (tcgen05, BF16 X, all frames)", "bound": "hbm",
                      "achieved": bytes_pbf / k_pbf / 1e9, "peak": peak_hbm, "unit": "GB/s",
                      "peak_source": peak_kind, "frac": bytes_pbf / k_pbf / 1e9 / peak_hbm,
-                     "traffic": 365.0e6, "algorithmic_bytes": bytes_pbf, "avg_launch_s": k_pbf,
+                     "traffic": captured_traffic("k_project_tc"), "algorithmic_bytes": bytes_pbf,
+                     "avg_launch_s": k_pbf,
                      "tensor_tflops": flops / k_pbf / 1e12},
         "roofline_reconstruct": {"kernel": "k_recon_tc", "bound": "hbm",
                                  "achieved": bytes_rbf / k_rbf / 1e9, "peak": peak_hbm,
                                  "unit": "GB/s", "frac": bytes_rbf / k_rbf / 1e9 / peak_hbm,
                                  "algorithmic_bytes": bytes_rbf, "avg_launch_s": k_rbf,
-                                 "traffic": 612.2e6,
+                                 "traffic": captured_traffic("k_recon_tc"),
                                  "tensor_tflops": flops / k_rbf / 1e12},
     }
+
+
+def run_extras(args, device):
+    """The other workloads, each short and outside the chain's timed region:
+    the batched dynamic-c workload with its one-block-per-launch and padded
+    dense-eigh baselines and the subspace accuracy of both OI forms against
+    the exact eigenbasis; the 200-frame projection; the differentiable filter."""
+    out = {}
+    jobs = (("batched", run_batched, dict(steps=3, warmup=2, precision="mixed", grid=1024,
+                                          plain_baseline=1), {"compare": True}),
+            ("frames", run_frames, dict(steps=3, warmup=2), {}),
+            ("filter", run_filter, dict(steps=3, warmup=2), {}))
+    for name, fn, over, kw in jobs:
+        a = argparse.Namespace(**vars(args))
+        for kk, vv in over.items():
+            setattr(a, kk, vv)
+        t0 = time.perf_counter()
+        try:
+            r = fn(a, device, **kw)
+        except Exception as exc:   # an extra must not stop the bench line
+            r = {"error": f"{type(exc).__name__}: {str(exc)[:200]}"}
+        r["host_seconds"] = time.perf_counter() - t0
+        out[name] = r
+    return out
 
 
 def main():
@@ -827,6 +1089,9 @@ def main():
     ap.add_argument("--roots", type=int, default=32, help="roots of the BFS warm-start forest")
     ap.add_argument("--plain-baseline", type=int, default=1,
                     help="batched: also time the same blocks one block per launch")
+    ap.add_argument("--extras", type=int, default=1,
+                    help="chain (N = 1): also report the batched, frames and filter workloads "
+                         "(outside the timed region)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -932,12 +1197,18 @@ def main():
         if world > 1:
             torch.distributed.destroy_process_group()
         return
-    cpu = None
+    cpu = cpu_eig = None
+    extras = {}
     if world == 1:
-        v, blocks, dt, cores = oracle_sample(args, args.cpu_budget)
-        cpu = {"value": v, "unit": "Mvertices/s", "cores": cores, "kind": "oracle",
-               "sample": f"first {blocks} of {(args.grid // args.tile) ** 2} chain blocks "
-                         f"({dt:.1f} s), FP64 NumPy/LAPACK"}
+        try:
+            cpu, cpu_eig = cpu_baselines(args, args.cpu_budget)
+        except Exception as exc:   # fall back to the oracle in this process
+            v, blocks, dt, cores = oracle_sample(args, args.cpu_budget)
+            cpu = {"value": v, "unit": "Mvertices/s", "cores": cores, "kind": "oracle",
+                   "sample": f"first {blocks} chain blocks ({dt:.1f} s), FP64 NumPy/LAPACK, "
+                             f"in-process ({str(exc)[:80]})"}
+        if args.extras:
+            extras = run_extras(args, device)
     line = {"metric": METRIC, "value": res["value"], "unit": "Mvertices/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -945,8 +1216,10 @@ def main():
             "data": "synthetic", "config": config_dict(args), "clocks": res["clocks"],
             "e2e": res["e2e"], "gpu_launches": res["launches"], "roofline": res["roofline"],
             "spmm_roofline": res["spmm_roofline"], "eig_baseline": res["eig_baseline"],
-            "kernels": res["kernels"], "cpu_baseline": cpu, "stats": res["stats"],
-            "autotune": res["autotune"], "codec": res["codec"], "denoise": res["denoise"]}
+            "kernels": res["kernels"], "cpu_baseline": cpu, "cpu_eigh_baseline": cpu_eig,
+            "stats": res["stats"], "autotune": res["autotune"], "codec": res["codec"],
+            "denoise": res["denoise"]}
+    line.update(extras)
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
