@@ -760,6 +760,8 @@ def run_batched(args, device, compare=False):
         for b in sample:
             lam, W = np.linalg.eigh(dense[b])
             ent = {"block": b, "n_b": int(sizes[b])}
+            Xs = xyz[verts[ptr[b]:ptr[b + 1]]]
+            rel = lambda Q: float(np.linalg.norm(Xs - Q @ (Q.T @ Xs)) / np.linalg.norm(Xs))
             for name, B in (("batched", bases), ("plain", pbases if plain else {})):
                 if b not in B:
                     continue
@@ -769,6 +771,8 @@ def run_batched(args, device, compare=False):
                 ent[f"{name}_c"] = cc
                 ent[f"{name}_max_sine"] = float(np.sqrt(max(0.0, 1.0 - sv.min() ** 2)))
                 ent[f"{name}_gap_ratio"] = float((lam[cc] - lam[cc - 1]) / lam[cc])
+                ent[f"{name}_rel_err_xyz"] = rel(U)
+                ent[f"eigh_rel_err_xyz_at_{name}_c"] = rel(W[:, :cc])
             rows.append(ent)
         accuracy = {"vs": "exact FP64 eigh of the block Laplacian, first c_b eigenvectors",
                     "blocks": rows,

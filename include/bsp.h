@@ -198,6 +198,34 @@ int bsp_set_edge_weights(bsp_mesh* mesh, const void* w, int64_t E);
 int bsp_oi_track(bsp_mesh* mesh, int32_t c, int32_t t_max, const void* V0_roots, void* stream);
 
 /*
+ * The paper's own dynamic OI (Sec. 5, Algorithm 2), one column at a time with
+ * two thresholds.  Per block, each iteration applies one Algorithm 1 step
+ * U = Onorm(R^z U) and measures e = sum over x, y, z of (X_b - U U^T X_b)
+ * (Eq. residual).  Branch directions as the text states them (the printed
+ * algorithm swaps them): ||e|| > eps_h grows U by the column e/||e|| (the next
+ * step's Onorm of R^z [U, e/||e||] is Eq. newU); ||e|| < eps_l keeps the
+ * first c - 1 columns; anything else stops the block.  The width stays in
+ * [c_min, min(c_max, n_b)] (a branch that would leave it stops instead), at
+ * most t_cap iterations run, and a basis still carrying an appended column at
+ * the cap is orthonormalised once more.  A root starts from its rows of
+ * V0_roots (c0 columns), a child from its parent's final basis and width (rows
+ * mapped r -> floor(r n_parent / n_b) when sizes differ).  The decisions are
+ * taken in FP64.
+ *   X         host or device real [n x 3] coordinates (global vertex order).
+ *   c0        1 <= c_min <= c0 <= c_max <= 128 (<= 64 with BSP_PREC_F64),
+ *             c0 <= every n_b.
+ *   eps_l, eps_h  0 < eps_l <= eps_h: absolute thresholds on ||e||.
+ *   t_cap     >= 1 iterations at most per block.
+ *   V0_roots  host or device real [sum over roots of n_b, c0].
+ *   c_out     host or device int32 [k] or NULL: final widths c_b.
+ *   iters_out host or device int32 [k] or NULL: iterations run per block.
+ * Errors: BSP_ERR_INVALID_ARG, BSP_ERR_NUMERICAL, BSP_ERR_NOT_CONVERGED, BSP_ERR_CUDA.
+ */
+int bsp_oi_track_paper_doi(bsp_mesh* mesh, const void* X, int32_t c0, double eps_l, double eps_h,
+                           int32_t c_min, int32_t c_max, int32_t t_cap, const void* V0_roots,
+                           int32_t* c_out, int32_t* iters_out, void* stream);
+
+/*
  * Dynamic-c orthogonal iterations (Sec. 5, Algorithm 2; quality-target reading).
  * Per block: start at c_parent (roots: c_min); run Algorithm 1 and
  * Rayleigh-Ritz; choose the smallest j in {c_step, 2 c_step, ...} with
@@ -264,6 +292,33 @@ int bsp_reconstruct_bf16(bsp_mesh* mesh, const float* E, int32_t cols, float* X_
  *           local vertex i of block b).  1 <= c <= 128.
  */
 int bsp_spmm(bsp_mesh* mesh, const void* P, void* Y, int32_t c, void* stream);
+
+/*
+ * Overlapped submeshes (Sec. 6.1, Algorithm 3): merge every vertex's copies
+ * into one position, the average of the copies weighted by the vertex's
+ * degree in each part (its number of neighbours in the part's induced
+ * subgraph).  Parts that share vertices are given to the library as an
+ * expanded mesh with one vertex per (part, vertex) copy, each part's induced
+ * edges re-indexed to its copies (so every copy lies in one block); tracking,
+ * projection and reconstruction run on that mesh as usual, and this call
+ * merges the reconstructed copies.  A copy's weight is its CSR row length in
+ * this mesh.  A vertex whose copies all have degree 0 takes the plain mean of
+ * its copies; a vertex with no copy gets 0.  Each vertex's copies are summed
+ * in ascending copy order (deterministic).
+ *   mesh      the expanded mesh (n = number of copies).
+ *   orig      host or device int32 [n]: the vertex of every copy, in [0, n_orig).
+ *   n_orig    number of vertices of the original mesh.
+ *   X_copies  host or device [n x cols] in the expanded mesh's vertex order (as
+ *             bsp_reconstruct writes it), element type x_dtype (BSP_DT_F32 or
+ *             BSP_DT_F64); the caller owns it.
+ *   X_out     host or device [n_orig x cols], same element type; caller-owned.
+ *   stream    cudaStream_t as void*; the call synchronises it.
+ * Errors: BSP_ERR_INVALID_ARG (NULL, n_orig < 1, cols < 1, dtype, an orig
+ * entry outside [0, n_orig)), BSP_ERR_OOM, BSP_ERR_CUDA.
+ */
+int bsp_merge_overlapped(const bsp_mesh* mesh, const int32_t* orig, int64_t n_orig,
+                         const void* X_copies, int32_t x_dtype, int32_t cols, void* X_out,
+                         void* stream);
 
 /*
  * Block low-pass filter X^ = U U^T X (Sec. 7.2, coarse denoising) made

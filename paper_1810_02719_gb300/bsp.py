@@ -83,6 +83,8 @@ def _load():
         "bsp_set_profiling": (C.c_int, [P, I32]),
         "bsp_get_kernel_times": (C.c_int, [P, P, P, I32]),
         "bsp_onorm_noalloc": (C.c_int, [P, P, I32, I32, P]),
+        "bsp_merge_overlapped": (C.c_int, [P, P, I64, P, I32, I32, P, P]),
+        "bsp_oi_track_paper_doi": (C.c_int, [P, P, I32, D, D, I32, I32, I32, P, P, P, P]),
         "bsp_filter_forward": (C.c_int, [P, I32, I32, P, P, P, P]),
         "bsp_filter_backward": (C.c_int, [P, P, P, P, P, P]),
         "bsp_reconstruct_bf16": (C.c_int, [P, P, I32, P, P]),
@@ -114,7 +116,8 @@ def exported_symbols():
             "bsp_set_profiling", "bsp_get_kernel_times", "bsp_onorm_noalloc",
             "bsp_filter_forward", "bsp_filter_backward", "bsp_reconstruct_bf16",
             "bsp_autotune", "bsp_quantize", "bsp_dequantize", "bsp_bits_per_vertex",
-            "bsp_nmsve", "bsp_fine_denoise", "bsp_normal_angle_error"]
+            "bsp_nmsve", "bsp_fine_denoise", "bsp_normal_angle_error", "bsp_merge_overlapped",
+            "bsp_oi_track_paper_doi"]
 
 
 def _check(code):
@@ -370,6 +373,26 @@ def bsp_onorm_noalloc(Y, Q, n, c, stream=None):
         if stream is None and hasattr(Y, "data_ptr"):
             stream = torch.cuda.current_stream(Y.device)
     _check(_lib.bsp_onorm_noalloc(_ptr(Y), _ptr(Q), n, c, _stream_ptr(stream)))
+
+
+def bsp_oi_track_paper_doi(mesh, X, c0, eps_l, eps_h, c_min, c_max, t_cap, V0_roots,
+                           stream=None):
+    """The paper's dynamic OI (Sec. 5, Algorithm 2, one column at a time, two
+    thresholds); returns (c per block, iterations per block) as int32 arrays."""
+    k = bsp_get_stats(mesh)["k"]
+    c = np.empty(k, np.int32)
+    its = np.empty(k, np.int32)
+    _check(_lib.bsp_oi_track_paper_doi(mesh, _ptr(X), c0, float(eps_l), float(eps_h), c_min,
+                                       c_max, t_cap, _ptr(V0_roots), _ptr(c), _ptr(its),
+                                       _stream_ptr(stream)))
+    return c, its
+
+
+def bsp_merge_overlapped(mesh, orig, n_orig, X_copies, x_dtype, cols, X_out, stream=None):
+    """Algorithm 3 (Sec. 6.1): degree-weighted mean of every vertex's copies in an
+    expanded (one vertex per part and copy) mesh; orig maps copies to vertices."""
+    _check(_lib.bsp_merge_overlapped(mesh, _ptr(_i32(orig)), int(n_orig), _ptr(X_copies),
+                                     x_dtype, cols, _ptr(X_out), _stream_ptr(stream)))
 
 
 def bsp_filter_forward(mesh, c, t_max, V0_roots, X, X_out, stream=None):

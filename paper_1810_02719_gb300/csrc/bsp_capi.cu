@@ -85,6 +85,18 @@ bool is_device_ptr(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Copy `bytes` of host data into a host-or-device destination (synchronises s).
+int to_host_or_device(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) return BSP_OK;
+  CU(cudaStreamSynchronize(s));
+  if (is_device_ptr(dst)) {
+    CU(cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice));
+  } else {
+    std::memcpy(dst, src, bytes);
+  }
+  return BSP_OK;
+}
+
 // Copy `bytes` from a host-or-device pointer into a device buffer.
 int to_device(void* dst, const void* src, size_t bytes, cudaStream_t s) {
   if (bytes == 0) return BSP_OK;
@@ -879,6 +891,138 @@ int track_dynamic(bsp_mesh* M, const void* X, double tol, int c_min, int c_max, 
 // Forward: Algorithm 1 without Rayleigh-Ritz, every step checkpointed
 // (V_0..V_t in d_ckV, Y_1..Y_t in d_ckY; Onorm by CholeskyQR2 at every step),
 // then X_out = U U^T X.  The next block's start is the parent's V_t.
+// The paper's dynamic OI (Sec. 5, Algorithm 2) with the text's branch
+// directions: per block, each iteration applies one Algorithm 1 step
+// U = Onorm(R^z U) and measures the summed residual e; ||e|| > eps_h grows U
+// by e/||e||, ||e|| < eps_l drops its last column, anything else stops the
+// block; the width stays in [c_min, min(c_max, n_b)], at most t_cap
+// iterations run, and a basis still carrying an appended column at the cap
+// is orthonormalised once more.  A root starts from its rows of V0 (c0
+// columns), a child from its parent's final basis and width.  The blocks of a
+// DAG level run as one batch; the host reads the stop flags after every
+// iteration and keeps the blocks still running.
+template <typename T, typename TA>
+int track_doi(bsp_mesh* M, const void* X, int c0, double eps_l, double eps_h, int c_min,
+              int c_max, int t_cap, const void* V0, int32_t* c_out, int32_t* iters_out,
+              cudaStream_t s) {
+  if (!X || !V0) return fail(BSP_ERR_INVALID_ARG, "X and V0_roots are required");
+  if (c_min < 1 || c0 < c_min || c_max < c0 || c_max > 128)
+    return fail(BSP_ERR_INVALID_ARG, "need 1 <= c_min <= c0 <= c_max <= 128");
+  if (sizeof(T) == 8 && c_max > 64) return fail(BSP_ERR_INVALID_ARG, "FP64 precision supports c <= 64");
+  if (c0 > M->min_nb) return fail(BSP_ERR_INVALID_ARG, "c0 exceeds the smallest block");
+  if (!(eps_l > 0) || !(eps_h >= eps_l)) return fail(BSP_ERR_INVALID_ARG, "need 0 < eps_l <= eps_h");
+  if (t_cap < 1) return fail(BSP_ERR_INVALID_ARG, "t_cap must be >= 1");
+  int maxbatch = 0;
+  for (auto& w : M->waves) maxbatch = std::max(maxbatch, (int)w.size());
+  int rc;
+  if ((rc = ensure_workspace<T, TA>(M, c_max, maxbatch)) != BSP_OK) return rc;
+  if ((rc = ensure(&M->d_starts, &M->cap_starts, (size_t)M->root_rows * c0 * sizeof(T))) != BSP_OK)
+    return rc;
+  if ((rc = to_device(M->d_starts, V0, (size_t)M->root_rows * c0 * sizeof(T), s)) != BSP_OK)
+    return rc;
+  if ((rc = ensure(&M->d_X, &M->cap_X, (size_t)M->n * 3 * sizeof(T))) != BSP_OK) return rc;
+  if ((rc = to_device(M->d_X, X, (size_t)M->n * 3 * sizeof(T), s)) != BSP_OK) return rc;
+  if (!M->d_action) {
+    if (cudaMalloc(&M->d_action, sizeof(int32_t) * M->k) != cudaSuccess ||
+        cudaMalloc(&M->d_round, sizeof(int32_t) * M->k) != cudaSuccess ||
+        cudaMalloc(&M->d_forced, sizeof(int32_t) * M->k) != cudaSuccess ||
+        cudaMalloc(&M->d_rho, sizeof(double) * M->k) != cudaSuccess ||
+        cudaMalloc(&M->d_gcol, sizeof(double) * M->n) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(BSP_ERR_OOM, "device allocation failed");
+    }
+  }
+  CU(cudaMemsetAsync(M->d_action, 0, sizeof(int32_t) * M->k, s));   // stop iteration per block
+  CU(cudaMemsetAsync(M->d_status, 0, sizeof(int), s));
+  CU(cudaMemsetAsync(M->d_cgstats, 0, sizeof(CgStats), s));
+  const MeshView<T> mv = view<T>(M);
+  T* U = (T*)M->d_U;
+  T* Y = (T*)M->d_Y;
+  const int c_cap = M->c_cap;
+  std::vector<int32_t>& hc = M->h_c;
+  hc.assign(M->k, 0);
+  std::vector<int32_t> cpar(M->k, 0), done(M->k, 0), its(M->k, 0);
+  int32_t* d_list = M->d_waves + 2 * M->k;   // scratch list area (last third)
+  int launches = 0;
+  for (size_t l = 0; l < M->waves.size(); ++l) {
+    std::vector<int32_t> active = M->waves[l];
+    for (int b : active) {
+      const int p = M->h_parent[b];
+      const int nb = M->h_bptr[b + 1] - M->h_bptr[b];
+      hc[b] = p < 0 ? c0 : std::min(hc[p], std::min(c_max, nb));
+      cpar[b] = p < 0 ? 0 : hc[p];
+    }
+    CU(cudaMemcpyAsync(M->d_cb, hc.data(), sizeof(int32_t) * M->k, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(M->d_cpar, cpar.data(), sizeof(int32_t) * M->k, cudaMemcpyHostToDevice, s));
+    auto stats = [&](int* wmax, int* cm) {
+      *wmax = 0;
+      *cm = 0;
+      for (int b : active) {
+        *wmax = std::max(*wmax, M->h_bptr[b + 1] - M->h_bptr[b]);
+        *cm = std::max(*cm, hc[b]);
+      }
+    };
+    int wmax, cm;
+    stats(&wmax, &cm);
+    CU(cudaMemcpyAsync(d_list, active.data(), sizeof(int32_t) * active.size(),
+                       cudaMemcpyHostToDevice, s));
+    launch_init_starts<T>(d_list, (int)active.size(), M->d_bptr, M->d_parent, M->d_root_off,
+                          M->d_cb, M->d_cpar, (const T*)M->d_starts, c0, U, c_cap, wmax, cm, s);
+    ++launches;
+    for (int t = 1; t <= t_cap && !active.empty(); ++t) {
+      stats(&wmax, &cm);
+      const int nbw = (int)active.size();
+      DenseArgs da{d_list, nbw, M->d_bptr, M->d_cb, c_cap, cm, wmax, M->d_status};
+      CgArgs ca{d_list, nbw, M->d_cb, c_cap, 1, M->opts.delta, M->opts.cg_rtol,
+                M->opts.cg_max_steps, M->d_status, M->d_cgstats, M->max_deg};
+      const int cs = pick_cs(M, nbw, cm, sizeof(T));
+      // U = Onorm(R^z U): z solves, an Onorm after each (same span as R^z U)
+      for (int q = 0; q < M->opts.z; ++q) {
+        if ((rc = launch_cg<T>(mv, U, Y, ca, cs, wmax, cm, s)))
+          return fail(rc, "CG launch failed (block too large for shared memory?)");
+        ++launches;
+        if ((rc = launch_cholqr2<T, TA>(da, Y, U, (TA*)M->d_Gp, (T*)M->d_Rsm, s, &launches)))
+          return fail(rc, "launch failed (Onorm)");
+      }
+      if ((rc = launch_doi_decide<T>(d_list, nbw, M->d_bptr, M->d_verts, (const T*)M->d_X, U,
+                                     c_cap, M->d_cb, M->d_action, t, eps_l, eps_h, c_min, c_max,
+                                     (T*)M->d_gcol, (double*)M->d_rho, s)))
+        return fail(rc, "launch failed (decision)");
+      ++launches;
+      CU(cudaMemcpyAsync(done.data(), M->d_action, sizeof(int32_t) * M->k, cudaMemcpyDeviceToHost, s));
+      CU(cudaMemcpyAsync(hc.data(), M->d_cb, sizeof(int32_t) * M->k, cudaMemcpyDeviceToHost, s));
+      CU(cudaStreamSynchronize(s));
+      std::vector<int32_t> next;
+      for (int b : active) {
+        if (done[b]) its[b] = done[b];
+        else next.push_back(b);
+      }
+      active.swap(next);
+      if (!active.empty())
+        CU(cudaMemcpyAsync(d_list, active.data(), sizeof(int32_t) * active.size(),
+                           cudaMemcpyHostToDevice, s));
+    }
+    if (!active.empty()) {   // blocks at the iteration cap: one more Onorm
+      stats(&wmax, &cm);
+      DenseArgs da{d_list, (int)active.size(), M->d_bptr, M->d_cb, c_cap, cm, wmax, M->d_status};
+      if ((rc = launch_cholqr2<T, TA>(da, U, U, (TA*)M->d_Gp, (T*)M->d_Rsm, s, &launches)))
+        return fail(rc, "launch failed (Onorm)");
+      for (int b : active) its[b] = t_cap;
+    }
+  }
+  std::vector<int32_t> ce(M->k + 1, 0);
+  for (int b = 0; b < M->k; ++b) ce[b + 1] = ce[b] + hc[b];
+  CU(cudaMemcpyAsync(M->d_ceoff, ce.data(), sizeof(int32_t) * (M->k + 1), cudaMemcpyHostToDevice, s));
+  if (c_out && (rc = to_host_or_device(c_out, hc.data(), sizeof(int32_t) * M->k, s)) != BSP_OK)
+    return rc;
+  if (iters_out && (rc = to_host_or_device(iters_out, its.data(), sizeof(int32_t) * M->k, s)) != BSP_OK)
+    return rc;
+  M->stats.gpu_launches = launches;
+  M->tracked = true;
+  M->ubf_valid = false;
+  return stream_error_status(M, s);
+}
+
 template <typename T, typename TA>
 int filter_forward(bsp_mesh* M, int c, int t_max, const void* V0, cudaStream_t s) {
   if (c < 1 || c > 64 || c > M->min_nb)
@@ -1265,6 +1409,26 @@ int bsp_autotune(bsp_mesh* M, int32_t c, int32_t t_max, const void* V0, int32_t 
   return BSP_OK;
 }
 
+int bsp_oi_track_paper_doi(bsp_mesh* M, const void* X, int32_t c0, double eps_l, double eps_h,
+                           int32_t c_min, int32_t c_max, int32_t t_cap, const void* V0,
+                           int32_t* c_out, int32_t* iters_out, void* stream) {
+  g_err.clear();
+  if (!M) return fail(BSP_ERR_INVALID_ARG, "mesh is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  ProfScope ps(M);
+  switch (M->opts.precision) {
+    case BSP_PREC_F64:
+      return track_doi<double, double>(M, X, c0, eps_l, eps_h, c_min, c_max, t_cap, V0, c_out,
+                                       iters_out, s);
+    case BSP_PREC_F32:
+      return track_doi<float, float>(M, X, c0, eps_l, eps_h, c_min, c_max, t_cap, V0, c_out,
+                                     iters_out, s);
+    default:
+      return track_doi<float, double>(M, X, c0, eps_l, eps_h, c_min, c_max, t_cap, V0, c_out,
+                                      iters_out, s);
+  }
+}
+
 int bsp_oi_track_dynamic(bsp_mesh* M, const void* X, double rel_tol, int32_t c_min,
                          int32_t c_max, int32_t c_step, int32_t t_max, uint64_t seed,
                          const void* V0, const int32_t* forced_c, int32_t* c_out, void* stream) {
@@ -1445,6 +1609,65 @@ int bsp_reconstruct_bf16(bsp_mesh* M, const float* E, int32_t cols, float* X_out
   CU(cudaMemcpy(&st, M->d_status, sizeof(int), cudaMemcpyDeviceToHost));
   if (st & ST_TIMEOUT) return fail(BSP_ERR_TIMEOUT, "a bounded device wait expired");
   M->stats.gpu_launches = 2 + conv;
+  return BSP_OK;
+}
+
+int bsp_merge_overlapped(const bsp_mesh* M, const int32_t* orig, int64_t n_orig,
+                         const void* X_copies, int32_t x_dtype, int32_t cols, void* X_out,
+                         void* stream) {
+  g_err.clear();
+  if (!M || !orig || !X_copies || !X_out) return fail(BSP_ERR_INVALID_ARG, "NULL argument");
+  if (n_orig < 1 || n_orig > INT32_MAX) return fail(BSP_ERR_INVALID_ARG, "n_orig out of range");
+  if (cols < 1) return fail(BSP_ERR_INVALID_ARG, "cols must be >= 1");
+  if (x_dtype != BSP_DT_F32 && x_dtype != BSP_DT_F64)
+    return fail(BSP_ERR_INVALID_ARG, "x_dtype must be BSP_DT_F32 or BSP_DT_F64");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = M->n;
+  const size_t eb = x_dtype == BSP_DT_F64 ? 8 : 4;
+  // workspace: status, orig (device copy), copy weights, counts, offsets, cursors, lists
+  const size_t ints = 4 + (size_t)n + (size_t)n + 3 * ((size_t)n_orig + 1) + (size_t)n;
+  void* wsp;
+  int rc;
+  if ((rc = scratch(0, ints * sizeof(int32_t), &wsp))) return rc;
+  int32_t* st = static_cast<int32_t*>(wsp);
+  int32_t* d_orig = st + 4;
+  float* w = reinterpret_cast<float*>(d_orig + n);
+  int32_t* cnt = reinterpret_cast<int32_t*>(w + n);
+  int32_t* off = cnt + n_orig + 1;
+  int32_t* cur = off + n_orig + 1;
+  int32_t* list = cur + n_orig + 1;
+  const int32_t* orig_dev = orig;
+  if (!is_device_ptr(orig)) {
+    CU(cudaMemcpyAsync(d_orig, orig, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+    orig_dev = d_orig;
+  }
+  CU(cudaMemsetAsync(st, 0, sizeof(int32_t), s));
+  if ((rc = launch_ov_table(n, M->d_verts, M->d_rowptr, orig_dev, n_orig, w, cnt, st, s)))
+    return fail(rc, "launch failed (copy table)");
+  int h_st = 0;
+  CU(cudaMemcpyAsync(&h_st, st, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  long long total = 0;
+  if ((rc = exclusive_scan(cnt, off, n_orig, st, s, &total)) != BSP_OK) return rc;  // synchronises s
+  if (h_st & ST_BAD_INDEX) return fail(BSP_ERR_INVALID_ARG, "orig holds a vertex id outside [0, n_orig)");
+  if ((rc = launch_ov_fill(n, orig_dev, n_orig, off, cur, list, s)))
+    return fail(rc, "launch failed (copy lists)");
+  const void* dXc = X_copies;
+  if (!is_device_ptr(X_copies)) {
+    void* t;
+    if ((rc = scratch(1, (size_t)n * cols * eb, &t))) return rc;
+    CU(cudaMemcpyAsync(t, X_copies, (size_t)n * cols * eb, cudaMemcpyHostToDevice, s));
+    dXc = t;
+  }
+  void* dXo = X_out;
+  const bool host_out = !is_device_ptr(X_out);
+  if (host_out && (rc = scratch(2, (size_t)n_orig * cols * eb, &dXo))) return rc;
+  rc = eb == 8 ? launch_ov_merge<double>(n_orig, cols, off, list, w, (const double*)dXc,
+                                         (double*)dXo, s)
+               : launch_ov_merge<float>(n_orig, cols, off, list, w, (const float*)dXc,
+                                        (float*)dXo, s);
+  if (rc) return fail(rc, "launch failed (merge)");
+  if (host_out) CU(cudaMemcpyAsync(X_out, dXo, (size_t)n_orig * cols * eb, cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
   return BSP_OK;
 }
 

@@ -265,6 +265,95 @@ __global__ void __launch_bounds__(kT) k_dyn_grow(const int32_t* batch, const int
   if (threadIdx.x == 0) cb[b] = c + c_step;
 }
 
+// The paper's dynamic OI (Sec. 5, Algorithm 2): one decision per iteration
+// for every block of the batch.  E = U^T X and e = sum over x, y, z of
+// (X - U E) (Eq. residual), products in T over 32-row chunks accumulated in
+// FP64, ||e|| in FP64.  Then, branch directions as the text states them:
+// ||e|| > eps_h and c < min(c_max, n_b): column c of U becomes e/||e|| (the
+// next step's Onorm of R^z [U, e/||e||] is Eq. newU) and cb[b] = c + 1;
+// ||e|| < eps_l and c > c_min: cb[b] = c - 1 (the first c - 1 columns stay);
+// otherwise done[b] = t (the block stops).  enorm[b] = ||e||.
+template <typename T>
+__global__ void __launch_bounds__(kT) k_doi_decide(const int32_t* batch, const int32_t* bptr,
+                                                   const int32_t* verts, const T* __restrict__ X,
+                                                   T* U, int ld, int32_t* cb, int32_t* done,
+                                                   int t, double eps_l, double eps_h, int c_min,
+                                                   int c_max, T* gcol, double* enorm) {
+  __shared__ double Ered[kT / 32][3 * 32];
+  __shared__ T Es[kMaxC][3];
+  __shared__ double red[kT / 32];
+  __shared__ int s_act;
+  const int b = batch[blockIdx.x];
+  const int c = cb[b];
+  const int r0 = bptr[b], nb = bptr[b + 1] - r0;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int q = 0; q * 32 < c; ++q) {
+    const int j = q * 32 + lane;
+    double e0 = 0, e1 = 0, e2 = 0;
+    T f0 = 0, f1 = 0, f2 = 0;
+    int cnt = 0;
+    for (int i = w; i < nb; i += kT / 32) {
+      const T u = j < c ? U[(size_t)(r0 + i) * ld + j] : T(0);
+      const T* x = X + (size_t)verts[r0 + i] * 3;
+      f0 += u * x[0];
+      f1 += u * x[1];
+      f2 += u * x[2];
+      if (++cnt == 32) {
+        e0 += f0; e1 += f1; e2 += f2;
+        f0 = f1 = f2 = 0;
+        cnt = 0;
+      }
+    }
+    e0 += f0; e1 += f1; e2 += f2;
+    Ered[w][3 * lane] = e0;
+    Ered[w][3 * lane + 1] = e1;
+    Ered[w][3 * lane + 2] = e2;
+    __syncthreads();
+    if (threadIdx.x < 96) {
+      double sum = 0;
+      for (int ww = 0; ww < kT / 32; ++ww) sum += Ered[ww][threadIdx.x];
+      const int jj = q * 32 + threadIdx.x / 3;
+      if (jj < c) Es[jj][threadIdx.x % 3] = (T)sum;
+    }
+    __syncthreads();
+  }
+  double ee = 0;
+  for (int i = threadIdx.x; i < nb; i += kT) {
+    const T* x = X + (size_t)verts[r0 + i] * 3;
+    const T* u = U + (size_t)(r0 + i) * ld;
+    T h0 = 0, h1 = 0, h2 = 0;
+    for (int j = 0; j < c; ++j) {
+      const T uj = u[j];
+      h0 += uj * Es[j][0];
+      h1 += uj * Es[j][1];
+      h2 += uj * Es[j][2];
+    }
+    const double e = ((double)x[0] - (double)h0) + ((double)x[1] - (double)h1) +
+                     ((double)x[2] - (double)h2);
+    gcol[r0 + i] = (T)e;
+    ee += e * e;
+  }
+  const double n2 = block_reduce<T, double>(ee, red);
+  if (threadIdx.x == 0) {
+    const double ne = sqrt(n2);
+    const int cmx = c_max < nb ? c_max : nb;
+    int act = 0;
+    if (ne > eps_h && c < cmx) act = 1;
+    else if (ne < eps_l && c > c_min) act = 2;
+    if (act == 1) cb[b] = c + 1;
+    else if (act == 2) cb[b] = c - 1;
+    else done[b] = t;
+    enorm[b] = ne;
+    s_act = act;
+  }
+  __syncthreads();
+  if (s_act == 1) {
+    const double inv = 1.0 / sqrt(n2);
+    for (int i = threadIdx.x; i < nb; i += kT)
+      U[(size_t)(r0 + i) * ld + c] = (T)((double)gcol[r0 + i] * inv);
+  }
+}
+
 }  // namespace
 
 template <typename T>
@@ -311,6 +400,24 @@ int launch_dyn_grow(const int32_t* batch, int nbatch, const int32_t* bptr, int32
   prof_end(KC_DYN, s);
   return cudaGetLastError() == cudaSuccess ? BSP_OK : BSP_ERR_CUDA;
 }
+
+template <typename T>
+int launch_doi_decide(const int32_t* batch, int nbatch, const int32_t* bptr, const int32_t* verts,
+                      const T* X, T* U, int ld, int32_t* cb, int32_t* done, int t, double eps_l,
+                      double eps_h, int c_min, int c_max, T* gcol, double* enorm, cudaStream_t s) {
+  if (c_max > kMaxC) return BSP_ERR_INVALID_ARG;
+  prof_begin(KC_DYN, s);
+  k_doi_decide<T><<<nbatch, kT, 0, s>>>(batch, bptr, verts, X, U, ld, cb, done, t, eps_l, eps_h,
+                                        c_min, c_max, gcol, enorm);
+  prof_end(KC_DYN, s);
+  return cudaGetLastError() == cudaSuccess ? BSP_OK : BSP_ERR_CUDA;
+}
+template int launch_doi_decide<float>(const int32_t*, int, const int32_t*, const int32_t*,
+                                      const float*, float*, int, int32_t*, int32_t*, int, double,
+                                      double, int, int, float*, double*, cudaStream_t);
+template int launch_doi_decide<double>(const int32_t*, int, const int32_t*, const int32_t*,
+                                       const double*, double*, int, int32_t*, int32_t*, int,
+                                       double, double, int, int, double*, double*, cudaStream_t);
 
 template void launch_init_starts<float>(const int32_t*, int, const int32_t*, const int32_t*,
                                         const int32_t*, const int32_t*, const int32_t*,

@@ -297,6 +297,24 @@ int launch_dyn_grow(const int32_t* batch, int nbatch, const int32_t* bptr, int32
                     const int32_t* round, T* U, int ld, const T* gcol, uint64_t seed,
                     int c_step, int max_nb, cudaStream_t s);
 
+// Overlapped parts (bsp_overlap.cu): copy weights and copy counts per vertex,
+// then (after a scan of the counts) the per-vertex copy lists in copy order,
+// then the degree-weighted mean of Algorithm 3 (Sec. 6.1).
+int launch_ov_table(int64_t rows, const int32_t* verts, const int32_t* rowptr, const int32_t* orig,
+                    int64_t n_orig, float* w, int32_t* cnt, int* status, cudaStream_t s);
+int launch_ov_fill(int64_t rows, const int32_t* orig, int64_t n_orig, const int32_t* off,
+                   int32_t* cur, int32_t* list, cudaStream_t s);
+template <typename T>
+int launch_ov_merge(int64_t n_orig, int cols, const int32_t* off, const int32_t* list,
+                    const float* w, const T* Xc, T* Xo, cudaStream_t s);
+
+// The paper's dynamic OI (Sec. 5, Algorithm 2): per block of the batch, the
+// summed residual e and the grow / shrink / stop decision (bsp_dyn.cu).
+template <typename T>
+int launch_doi_decide(const int32_t* batch, int nbatch, const int32_t* bptr, const int32_t* verts,
+                      const T* X, T* U, int ld, int32_t* cb, int32_t* done, int t, double eps_l,
+                      double eps_h, int c_min, int c_max, T* gcol, double* enorm, cudaStream_t s);
+
 // Adjoint of the low-pass filter (bsp_adjoint.cu)
 struct AdjointArgs {
   const int32_t* batch; int k;          // all blocks
