@@ -1044,6 +1044,74 @@ def run_frames(args, device):
     }
 
 
+def run_split(args, rank, world, device):
+    """One mesh split across ranks: the 1024^2 torus cut into ~2,000 BFS blocks
+    with a 32-root warm-start forest; whole subtrees per rank (balanced by
+    vertex count), every rank tracks its sub-forest with dynamic c (MIXED),
+    projects and reconstructs its vertices, then one all-gather assembles the
+    whole reconstruction on every rank.  Strong scaling: the mesh is fixed.
+    (A rank keys the growth columns' counter hash on its own block numbers.)"""
+    import torch
+    import torch.distributed as dist
+    from paper_1810_02719_gb300 import bsp, forest
+    N = args.grid
+    xyz, faces = synth.torus(N, seed=0)
+    ptr, verts = synth.bfs_partition(N, target_blocks=6000 * N * N // (1024 * 1024),
+                                     min_size=300, max_size=3000, seed=0)
+    ptr, verts, parent = synth.block_forest(ptr, verts, N, roots=args.roots, seed=1)
+    n = N * N
+    starts = synth.gaussian_starts(ptr, parent, 8, seed=0)
+    part = forest.split_forest(ptr, verts, parent, world)[rank]
+    xr, er, lp, lv, lpar = forest.local_mesh_inputs(xyz, faces, part)
+    st = forest.local_starts(starts, ptr, parent, part)
+    kr = len(lp) - 1
+    h = bsp.bsp_mesh_create_edges(xr, er, lp, lv, lpar,
+                                  bsp.make_opts(precision=bsp.BSP_PREC_MIXED))
+    stream = torch.cuda.current_stream(device)
+    V0 = torch.tensor(st, dtype=torch.float32, device=device)
+    X = torch.tensor(xr, dtype=torch.float32, device=device)
+    ids = torch.tensor(part.block_verts, dtype=torch.int64, device=device)
+    c_out = torch.empty(max(kr, 1), dtype=torch.int32, device=device)
+    E = torch.empty(max(kr, 1) * 128, 3, dtype=torch.float32, device=device)
+    Xo = torch.empty_like(X)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
+
+    def step():
+        bsp.bsp_oi_track_dynamic(h, X, 2e-3, 8, 128, 8, args.t, 7, V0, None, c_out, stream)
+        bsp.bsp_project(h, X, bsp.BSP_DT_F32, 3, E, stream)
+        bsp.bsp_reconstruct(h, E, 3, Xo, stream)
+        return forest.gather_rows(Xo, ids, n)
+
+    for _ in range(args.warmup):
+        full = step()
+    torch.cuda.synchronize()
+    dist.barrier()
+    times = []
+    with Clocks(device.index) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            dist.barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            full = step()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+    total = slowest_rank_time(sum(times), device)
+    err = float(torch.linalg.norm(full.cpu().double() - torch.from_numpy(xyz)) /
+                torch.linalg.norm(torch.from_numpy(xyz)))
+    bsp.bsp_mesh_destroy(h)
+    return {"value": n * args.steps / total / 1e6, "unit": "Mvertices/s",
+            "ms_per_step": 1e3 * total / args.steps, "clocks": clk.summary(),
+            "scaling": "strong",
+            "split": {"ranks": world, "blocks_this_rank": int(kr),
+                      "vertices_this_rank": part.n_vertices,
+                      "roots_this_rank": int(part.roots.size)},
+            "gathered_rel_err_xyz": err}
+
+
 def run_extras(args, device):
     """The other workloads, each short and outside the chain's timed region:
     the batched dynamic-c workload with its one-block-per-launch and padded
@@ -1093,6 +1161,9 @@ def main():
     ap.add_argument("--roots", type=int, default=32, help="roots of the BFS warm-start forest")
     ap.add_argument("--plain-baseline", type=int, default=1,
                     help="batched: also time the same blocks one block per launch")
+    ap.add_argument("--split", default="none", choices=["none", "forest"],
+                    help="forest: one mesh (the batched workload) split by subtrees across "
+                         "the ranks, results all-gathered (strong scaling)")
     ap.add_argument("--extras", type=int, default=1,
                     help="chain (N = 1): also report the batched, frames and filter workloads "
                          "(outside the timed region)")
@@ -1134,10 +1205,31 @@ def main():
         return
 
     import torch
-    if world > 1:
-        torch.distributed.init_process_group("nccl")
+    if world > 1 or args.split == "forest":
+        if world == 1:
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            os.environ.setdefault("MASTER_PORT", "29533")
+            torch.distributed.init_process_group("nccl", rank=0, world_size=1)
+        else:
+            torch.distributed.init_process_group("nccl")
     device = torch.device("cuda", local)
     torch.cuda.set_device(device)
+    if args.split == "forest":
+        res = run_split(args, rank, world, device)
+        if rank == 0:
+            line = {"metric": METRIC, "impl": "ours", "n_gpus": world, "steps": args.steps,
+                    "warmup": args.warmup, "higher_is_better": True, "vs_baseline": None,
+                    "dtype": "f32+f64(gram,cholesky,rayleigh-ritz)", "data": "synthetic",
+                    "config": {"workload": f"torus {args.grid}x{args.grid}, ~2000 BFS blocks, "
+                                           f"{args.roots}-root forest split by subtrees over "
+                                           f"{world} ranks, dynamic c 8..128, all-gather of the "
+                                           f"reconstruction", "parallelism": f"subtrees{world}",
+                               "l2": "flushed between timed steps (512 MB write)"}}
+            line.update(res)
+            print(json.dumps(line))
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
     if args.config == "frames":
         res = run_frames(args, device)
         if rank == 0:
