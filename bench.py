@@ -1227,8 +1227,7 @@ def main():
                                "l2": "flushed between timed steps (512 MB write)"}}
             line.update(res)
             print(json.dumps(line))
-        if world > 1:
-            torch.distributed.destroy_process_group()
+        torch.distributed.destroy_process_group()
         return
     if args.config == "frames":
         res = run_frames(args, device)
