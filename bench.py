@@ -645,8 +645,8 @@ def run_batched(args, device, compare=False):
     reconstruction error of the block's xyz is <= 2e-3, 2 OI steps per round,
     FP32 solves with FP64 Gram/Cholesky/Rayleigh-Ritz (MIXED), then projection
     and reconstruction of xyz.  One step = bsp_oi_track_dynamic + bsp_project +
-    bsp_reconstruct through the C ABI (the dynamic rounds read their decisions
-    back on the host)."""
+    bsp_reconstruct through the C ABI (the rounds are decided on the device and
+    the whole tracking call replays one CUDA graph with conditional nodes)."""
     import torch
     from paper_1810_02719_gb300 import bsp
     N = args.grid

@@ -147,6 +147,7 @@ void configure_once() {
   static std::once_flag flag;
   std::call_once(flag, [] {
     configure_cg_kernels();
+    configure_cgt_kernels();
     configure_dense_kernels();
     configure_adjoint_kernels();
     configure_tc_kernels();
@@ -155,8 +156,8 @@ void configure_once() {
   });
 }
 
-// Sort a batch by the size bucket of the batched CG (rows per thread 1, 4, 8,
-// 16; blocks too large last) and return the bucket offsets off[0..4] and the
+// Sort a batch by the size bucket of the batched CG (up to 512, 1,024, 2,048,
+// 4,096 rows; blocks too large last) and return the bucket offsets off[0..4] and the
 // largest block of every bucket.
 void sort_by_bucket(const bsp_mesh* M, std::vector<int32_t>& list, int off[5], int rows[4]) {
   auto nb = [&](int b) { return M->h_bptr[b + 1] - M->h_bptr[b]; };
@@ -178,12 +179,13 @@ void sort_by_bucket(const bsp_mesh* M, std::vector<int32_t>& list, int off[5], i
   }
 }
 
-// The batched one-column-per-CTA CG, launched per size bucket, for batches of
-// several blocks (automatic column choice only; slab widths set by the caller
-// keep the shared-memory slab kernel).
+// The batched CG (team kernel, or one column per CTA), launched per size
+// bucket, for batches of several blocks (automatic column choice only; slab
+// widths set by the caller keep the shared-memory slab kernel).
 bool use_buckets(const bsp_mesh* M, int nbatch, int wmax) {
   return M->opts.cols_per_cta == 0 && nbatch >= 2 &&
-         cg1_fits(wmax, M->max_deg, M->real_bytes, M->d_wt != nullptr);
+         (cgt_fits(wmax, M->max_deg, M->real_bytes, M->d_wt != nullptr) ||
+          cg1_fits(wmax, M->max_deg, M->real_bytes, M->d_wt != nullptr));
 }
 
 int pad4(int c) { return (c + 3) & ~3; }
@@ -196,11 +198,14 @@ void release(bsp_mesh* m) {
                   m->d_gcol, m->d_rho, m->d_X, m->d_Gp_rr, m->d_Rsm_rr, m->d_theta_rr,
                   m->d_ckV, m->d_ckY,
                   m->d_adj_gp, m->d_adj_thin, m->d_adj_rows, m->d_Ubf, m->d_Ebf,
-                  m->d_spmm_chunks, m->d_ready};
+                  m->d_spmm_chunks, m->d_ready, m->d_live, m->d_dynctl, m->d_dyn_launches};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (m->graph_exec) cudaGraphExecDestroy(m->graph_exec);
+  if (m->dyn_exec) cudaGraphExecDestroy(m->dyn_exec);
   if (m->graph_stream) cudaStreamDestroy(m->graph_stream);
+  for (cudaStream_t q : m->dyn_stream)
+    if (q) cudaStreamDestroy(q);
 }
 
 int stream_error_status(bsp_mesh* m, cudaStream_t s) {
@@ -450,6 +455,10 @@ int ensure_workspace(bsp_mesh* M, int c_cap, int maxbatch) {
   if ((M->c_cap != c_cap || g_realloc) && M->graph_exec) {
     cudaGraphExecDestroy(M->graph_exec);
     M->graph_exec = nullptr;
+  }
+  if ((M->c_cap != c_cap || g_realloc) && M->dyn_exec) {
+    cudaGraphExecDestroy(M->dyn_exec);
+    M->dyn_exec = nullptr;
   }
   M->c_cap = c_cap;
   return BSP_OK;
@@ -736,6 +745,279 @@ int track_fixed(bsp_mesh* M, int c, int t_max, const void* V0, cudaStream_t s) {
   return stream_error_status(M, s);
 }
 
+// Per-block state of the dynamic schedules (allocated once per mesh, each
+// buffer on its first use).
+int ensure_dyn_state(bsp_mesh* M) {
+  struct Buf { void** p; size_t bytes; };
+  const Buf bufs[] = {{(void**)&M->d_action, sizeof(int32_t) * M->k},
+                      {(void**)&M->d_round, sizeof(int32_t) * M->k},
+                      {(void**)&M->d_forced, sizeof(int32_t) * M->k},
+                      {(void**)&M->d_rho, sizeof(double) * M->k},
+                      {(void**)&M->d_gcol, sizeof(double) * M->n},
+                      {(void**)&M->d_live, sizeof(int32_t) * M->k},
+                      {(void**)&M->d_dynctl, sizeof(DynCtl)}};
+  for (const Buf& b : bufs)
+    if (!*b.p && cudaMalloc(b.p, b.bytes) != cudaSuccess) {
+      *b.p = nullptr;
+      cudaGetLastError();
+      return fail(BSP_ERR_OOM, "device allocation failed");
+    }
+  return BSP_OK;
+}
+
+// ---------------------------------------------------------- dynamic c
+// The dynamic-c schedule (Sec. 5, Algorithm 2, with the reading of
+// oi_dynamic_block: rounds of Algorithm 1 + Rayleigh-Ritz, the smallest
+// passing prefix width, else c_step more columns) runs device-driven: per
+// block, live[b] says whether it still grows; the decision kernel clears it,
+// every kernel of a round skips blocks that are no longer live, and two
+// one-CTA kernels per round reduce the wave's state to "another round?" and
+// "largest live width".  No decision goes back to the host between rounds.
+// With use_graph the whole call is one CUDA graph: per wave, a SWITCH node
+// over width classes for the start, then a WHILE node over rounds whose body
+// is a SWITCH over width classes (launches sized for the largest live width,
+// a multiple of c_step = kDynClass), the conditions set by those kernels.  Without it
+// (or while profiling) the host replays the same launches, reading the class
+// and the "another round" flag back after each control kernel.
+constexpr int kDynClass = 8;
+constexpr int kDynMaxRounds = 64;
+
+struct DynParams {
+  int c_min, c_max, c_step, t_max;
+  double tol;
+  uint64_t seed;
+  const int32_t* forced;   // device copy or nullptr
+};
+
+int dyn_classes(int c_max) { return (c_max + kDynClass - 1) / kDynClass; }
+int dyn_class_width(int q, int c_max) { return std::min((q + 1) * kDynClass, c_max); }
+
+int wave_rows(const bsp_mesh* M, int l) {
+  int w = 0;
+  for (int b : M->waves[l]) w = std::max(w, M->h_bptr[b + 1] - M->h_bptr[b]);
+  return w;
+}
+
+// Start of wave l at widths <= cm: start matrices (roots: their rows of the
+// start matrix; children: the parent's basis, rows transferred) and Onorm.
+template <typename T, typename TA>
+int enqueue_dyn_start(bsp_mesh* M, int l, int cm, const DynParams& p, cudaStream_t s,
+                      int* launches) {
+  const int32_t* wave = M->d_waves + M->h_wave_off[l];
+  const int nw = (int)M->waves[l].size(), wmax = wave_rows(M, l);
+  T* U = (T*)M->d_U;
+  launch_init_starts<T>(wave, nw, M->d_bptr, M->d_parent, M->d_root_off, M->d_cb, M->d_cpar,
+                        (const T*)M->d_starts, p.c_min, U, M->c_cap, wmax, cm, s);
+  ++*launches;
+  DenseArgs da{wave, nw, M->d_bptr, M->d_cb, M->c_cap, cm, wmax, M->d_status};
+  return launch_cholqr2<T, TA>(da, U, U, (TA*)M->d_Gp, (T*)M->d_Rsm, s, launches);
+}
+
+// One round of wave l for the live blocks, widths <= cm: t_max steps of z
+// solves with an Onorm after each, Rayleigh-Ritz, the decision, and for the
+// blocks that grow: c_step new columns and an Onorm at widths <= cm + c_step.
+template <typename T, typename TA>
+int enqueue_dyn_round(bsp_mesh* M, int l, int cm, const DynParams& p, cudaStream_t s,
+                      int* launches) {
+  const int32_t* wave = M->d_waves + M->h_wave_off[l];
+  const int nw = (int)M->waves[l].size(), wmax = wave_rows(M, l);
+  const MeshView<T> mv = view<T>(M);
+  T* U = (T*)M->d_U;
+  T* Y = (T*)M->d_Y;
+  int rc;
+  DenseArgs da{wave, nw, M->d_bptr, M->d_cb, M->c_cap, cm, wmax, M->d_status};
+  da.live = M->d_live;
+  CgArgs ca{wave, nw, M->d_cb, M->c_cap, 1, M->opts.delta, M->opts.cg_rtol, M->opts.cg_max_steps,
+            M->d_status, M->d_cgstats, M->max_deg};
+  ca.live = M->d_live;
+  const int cs = pick_cs(M, nw, cm, sizeof(T));
+  const bool buckets = use_buckets(M, nw, wmax);
+  for (int t = 0; t < p.t_max * M->opts.z; ++t) {   // z solves per step, Onorm after each
+    rc = buckets ? launch_cg_buckets<T>(mv, U, Y, ca, M->wave_bucket[l].data(),
+                                        M->wave_bucket_rows[l].data(), cm, s)
+                 : launch_cg<T>(mv, U, Y, ca, cs, wmax, cm, s);
+    if (rc) return fail(rc, "CG launch failed");
+    ++*launches;
+    if ((rc = launch_cholqr2<T, TA>(da, Y, U, (TA*)M->d_Gp, (T*)M->d_Rsm, s, launches)))
+      return fail(rc, "launch failed");
+  }
+  da.sweeps = &M->d_cgstats->jacobi_sweeps;
+  if ((rc = launch_rayleigh_ritz<T, TA>(da, mv, U, (TA*)M->d_Gp, (T*)M->d_Rsm, (T*)M->d_theta, s,
+                                        launches)))
+    return fail(rc, "launch failed");
+  if ((rc = launch_dyn_decide<T, TA>(wave, nw, M->d_bptr, M->d_verts, (const T*)M->d_X, U,
+                                     M->c_cap, M->d_cb, M->d_action, p.forced, p.tol, p.c_step,
+                                     p.c_max, (T*)M->d_gcol, (TA*)M->d_rho, wmax, s, M->d_live)))
+    return fail(rc, "launch failed");
+  ++*launches;
+  if ((rc = launch_dyn_grow<T, TA>(wave, nw, M->d_bptr, M->d_cb, M->d_round, U, M->c_cap,
+                                   (const T*)M->d_gcol, p.seed, p.c_step, wmax, s, M->d_live)))
+    return fail(rc, "launch failed");
+  ++*launches;
+  DenseArgs dg = da;
+  dg.sweeps = nullptr;
+  dg.cmax = std::min(cm + p.c_step, p.c_max);
+  if ((rc = launch_cholqr2<T, TA>(dg, U, U, (TA*)M->d_Gp, (T*)M->d_Rsm, s, launches)))
+    return fail(rc, "launch failed");
+  return BSP_OK;
+}
+
+// A conditional node after the current capture frontier of s (which then
+// continues after the node); its body graphs in *bodies.
+int add_conditional(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                    unsigned size, std::vector<cudaGraph_t>* bodies) {
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  CU(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &nd));
+  if (st != cudaStreamCaptureStatusActive) return fail(BSP_ERR_CUDA, "stream is not capturing");
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = type;
+  np.conditional.size = size;
+  cudaGraphNode_t node;
+  CU(cudaGraphAddNode(&node, g, deps, nullptr, nd, &np));
+  bodies->assign(np.conditional.phGraph_out, np.conditional.phGraph_out + size);
+  CU(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  return BSP_OK;
+}
+
+// The graph of the whole dynamic-c schedule (see above).  counts[l][0..ncls)
+// and [ncls..2 ncls): launches of the start and round bodies of wave l.
+template <typename T, typename TA>
+int build_dyn_graph(bsp_mesh* M, const DynParams& p, std::vector<unsigned>* counts,
+                    cudaGraphExec_t* exec) {
+  const int ncls = dyn_classes(p.c_max);
+  const int levels = (int)M->waves.size();
+  counts->assign((size_t)levels * 2 * ncls, 0u);
+  cudaStream_t s0 = M->graph_stream, s1 = M->dyn_stream[0], s2 = M->dyn_stream[1];
+  const cudaStreamCaptureMode mode = cudaStreamCaptureModeRelaxed;
+  cudaGraph_t g;
+  CU(cudaGraphCreate(&g, 0));
+  auto abort_capture = [&](int rc) {
+    for (cudaStream_t q : {s2, s1, s0}) {
+      cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+      cudaStreamIsCapturing(q, &st);
+      if (st != cudaStreamCaptureStatusNone) {
+        cudaGraph_t t = nullptr;
+        cudaStreamEndCapture(q, &t);
+      }
+    }
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    return rc;
+  };
+  if (cudaStreamBeginCaptureToGraph(s0, g, nullptr, nullptr, 0, mode) != cudaSuccess)
+    return abort_capture(fail(BSP_ERR_CUDA, "graph capture failed to start"));
+  int rc = BSP_OK;
+  for (int l = 0; l < levels; ++l) {
+    const int32_t* wave = M->d_waves + M->h_wave_off[l];
+    const int nw = (int)M->waves[l].size();
+    unsigned* cnt = M->d_dyn_launches + (size_t)l * 2 * ncls;
+    unsigned* hcnt = counts->data() + (size_t)l * 2 * ncls;
+    cudaGraphConditionalHandle h_start, h_while, h_round;
+    if (cudaGraphConditionalHandleCreate(&h_start, g, 0, 0) != cudaSuccess ||
+        cudaGraphConditionalHandleCreate(&h_while, g, 1, cudaGraphCondAssignDefault) != cudaSuccess)
+      return abort_capture(fail(BSP_ERR_CUDA, "conditional handle"));
+    if ((rc = launch_dyn_wave_init(wave, nw, M->d_bptr, M->d_parent, M->d_cb, M->d_cpar, M->d_live,
+                                   M->d_round, p.c_min, p.c_max, p.c_step, kDynClass, ncls, cnt,
+                                   M->d_dynctl, 1, h_start, s0)))
+      return abort_capture(fail(rc, "launch failed"));
+    std::vector<cudaGraph_t> sb, wb, rb;
+    if ((rc = add_conditional(s0, h_start, cudaGraphCondTypeSwitch, ncls, &sb)))
+      return abort_capture(rc);
+    for (int q = 0; q < ncls; ++q) {
+      int n = 0;
+      if (cudaStreamBeginCaptureToGraph(s1, sb[q], nullptr, nullptr, 0, mode) != cudaSuccess)
+        return abort_capture(fail(BSP_ERR_CUDA, "graph capture failed to start"));
+      if ((rc = enqueue_dyn_start<T, TA>(M, l, dyn_class_width(q, p.c_max), p, s1, &n)))
+        return abort_capture(rc);
+      cudaGraph_t t;
+      if (cudaStreamEndCapture(s1, &t) != cudaSuccess)
+        return abort_capture(fail(BSP_ERR_CUDA, "graph capture"));
+      hcnt[q] = (unsigned)n;
+    }
+    if ((rc = add_conditional(s0, h_while, cudaGraphCondTypeWhile, 1, &wb))) return abort_capture(rc);
+    if (cudaGraphConditionalHandleCreate(&h_round, wb[0], 0, 0) != cudaSuccess ||
+        cudaStreamBeginCaptureToGraph(s1, wb[0], nullptr, nullptr, 0, mode) != cudaSuccess)
+      return abort_capture(fail(BSP_ERR_CUDA, "graph capture failed to start"));
+    if ((rc = launch_dyn_class(wave, nw, M->d_cb, M->d_live, kDynClass, ncls, cnt + ncls,
+                               M->d_dynctl, 1, h_round, s1)))
+      return abort_capture(fail(rc, "launch failed"));
+    if ((rc = add_conditional(s1, h_round, cudaGraphCondTypeSwitch, ncls, &rb)))
+      return abort_capture(rc);
+    for (int q = 0; q < ncls; ++q) {
+      int n = 0;
+      if (cudaStreamBeginCaptureToGraph(s2, rb[q], nullptr, nullptr, 0, mode) != cudaSuccess)
+        return abort_capture(fail(BSP_ERR_CUDA, "graph capture failed to start"));
+      if ((rc = enqueue_dyn_round<T, TA>(M, l, dyn_class_width(q, p.c_max), p, s2, &n)))
+        return abort_capture(rc);
+      cudaGraph_t t;
+      if (cudaStreamEndCapture(s2, &t) != cudaSuccess)
+        return abort_capture(fail(BSP_ERR_CUDA, "graph capture"));
+      hcnt[ncls + q] = (unsigned)n;
+    }
+    if ((rc = launch_dyn_next(wave, nw, M->d_live, kDynMaxRounds, M->d_dynctl, 1, h_while, s1)))
+      return abort_capture(fail(rc, "launch failed"));
+    cudaGraph_t t;
+    if (cudaStreamEndCapture(s1, &t) != cudaSuccess)
+      return abort_capture(fail(BSP_ERR_CUDA, "graph capture"));
+  }
+  cudaGraph_t t;
+  if (cudaStreamEndCapture(s0, &t) != cudaSuccess)
+    return abort_capture(fail(BSP_ERR_CUDA, "graph capture"));
+  const cudaError_t ie = cudaGraphInstantiate(exec, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess)
+    return fail(BSP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
+  return BSP_OK;
+}
+
+// The same schedule launched from the host: control values read back after
+// each control kernel (one synchronisation per kernel; profiling mode).
+template <typename T, typename TA>
+int run_dyn_eager(bsp_mesh* M, const DynParams& p, cudaStream_t s, int* launches) {
+  const int ncls = dyn_classes(p.c_max);
+  const unsigned* zeros = M->d_dyn_launches + (size_t)M->waves.size() * 2 * ncls;
+  DynCtl ctl;
+  auto read_ctl = [&]() -> int {
+    CU(cudaMemcpyAsync(&ctl, M->d_dynctl, sizeof(DynCtl), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    return BSP_OK;
+  };
+  int rc;
+  for (int l = 0; l < (int)M->waves.size(); ++l) {
+    const int32_t* wave = M->d_waves + M->h_wave_off[l];
+    const int nw = (int)M->waves[l].size();
+    if ((rc = launch_dyn_wave_init(wave, nw, M->d_bptr, M->d_parent, M->d_cb, M->d_cpar, M->d_live,
+                                   M->d_round, p.c_min, p.c_max, p.c_step, kDynClass, ncls, zeros,
+                                   M->d_dynctl, 0, 0, s)))
+      return fail(rc, "launch failed");
+    if ((rc = read_ctl())) return rc;
+    if (ctl.cls_start < ncls &&
+        (rc = enqueue_dyn_start<T, TA>(M, l, dyn_class_width(ctl.cls_start, p.c_max), p, s,
+                                       launches)))
+      return rc;
+    for (;;) {
+      if ((rc = launch_dyn_class(wave, nw, M->d_cb, M->d_live, kDynClass, ncls, zeros,
+                                 M->d_dynctl, 0, 0, s)))
+        return fail(rc, "launch failed");
+      if ((rc = read_ctl())) return rc;
+      if (ctl.cls_round < ncls &&
+          (rc = enqueue_dyn_round<T, TA>(M, l, dyn_class_width(ctl.cls_round, p.c_max), p, s,
+                                         launches)))
+        return rc;
+      if ((rc = launch_dyn_next(wave, nw, M->d_live, kDynMaxRounds, M->d_dynctl, 0, 0, s)))
+        return fail(rc, "launch failed");
+      if ((rc = read_ctl())) return rc;
+      if (!ctl.more) break;
+    }
+  }
+  return BSP_OK;
+}
+
 template <typename T, typename TA>
 int track_dynamic(bsp_mesh* M, const void* X, double tol, int c_min, int c_max, int c_step,
                   int t_max, uint64_t seed, const void* V0, const int32_t* forced,
@@ -751,137 +1033,71 @@ int track_dynamic(bsp_mesh* M, const void* X, double tol, int c_min, int c_max, 
   for (auto& w : M->waves) maxbatch = std::max(maxbatch, (int)w.size());
   int rc;
   if ((rc = ensure_workspace<T, TA>(M, c_max, maxbatch)) != BSP_OK) return rc;
+  bool realloc = g_realloc;
   if ((rc = ensure(&M->d_starts, &M->cap_starts, (size_t)M->root_rows * c_min * sizeof(T))) != BSP_OK)
     return rc;
+  if ((rc = ensure(&M->d_X, &M->cap_X, (size_t)M->n * 3 * sizeof(T))) != BSP_OK) return rc;
+  const int ncls = dyn_classes(c_max);
+  const size_t ncounts = (M->waves.size() + 1) * 2 * (size_t)ncls;
+  if ((rc = ensure((void**)&M->d_dyn_launches, &M->cap_dyn_launches,
+                   ncounts * sizeof(unsigned))) != BSP_OK)
+    return rc;
+  if ((rc = ensure_dyn_state(M)) != BSP_OK) return rc;
+  realloc = realloc || g_realloc;
   if ((rc = to_device(M->d_starts, V0, (size_t)M->root_rows * c_min * sizeof(T), s)) != BSP_OK)
     return rc;
-  if ((rc = ensure(&M->d_X, &M->cap_X, (size_t)M->n * 3 * sizeof(T))) != BSP_OK) return rc;
   if ((rc = to_device(M->d_X, X, (size_t)M->n * 3 * sizeof(T), s)) != BSP_OK) return rc;
-  if (!M->d_action) {
-    if (cudaMalloc(&M->d_action, sizeof(int32_t) * M->k) != cudaSuccess ||
-        cudaMalloc(&M->d_round, sizeof(int32_t) * M->k) != cudaSuccess ||
-        cudaMalloc(&M->d_forced, sizeof(int32_t) * M->k) != cudaSuccess ||
-        cudaMalloc(&M->d_rho, sizeof(double) * M->k) != cudaSuccess ||
-        cudaMalloc(&M->d_gcol, sizeof(double) * M->n) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(BSP_ERR_OOM, "device allocation failed");
-    }
-  }
-  const int32_t* d_forced = nullptr;
-  if (forced) {
-    if ((rc = to_device(M->d_forced, forced, sizeof(int32_t) * M->k, s)) != BSP_OK) return rc;
-    d_forced = M->d_forced;
-  }
-  CU(cudaMemsetAsync(M->d_round, 0, sizeof(int32_t) * M->k, s));
+  if (forced && (rc = to_device(M->d_forced, forced, sizeof(int32_t) * M->k, s)) != BSP_OK)
+    return rc;
   CU(cudaMemsetAsync(M->d_status, 0, sizeof(int), s));
   CU(cudaMemsetAsync(M->d_cgstats, 0, sizeof(CgStats), s));
-  const MeshView<T> mv = view<T>(M);
-  T* U = (T*)M->d_U;
-  T* Y = (T*)M->d_Y;
-  const int c_cap = M->c_cap;
+  CU(cudaMemsetAsync(M->d_dynctl, 0, sizeof(DynCtl), s));
+  DynParams p{c_min, c_max, c_step, t_max, tol, seed, forced ? M->d_forced : nullptr};
+  int launches = 0;
+  if (M->opts.use_graph && !M->profiling) {
+    const std::vector<double> key = {(double)sizeof(T), (double)sizeof(TA), (double)c_min,
+                                     (double)c_max, (double)c_step, (double)t_max, tol,
+                                     (double)(seed >> 32), (double)(seed & 0xffffffffu),
+                                     forced ? 1.0 : 0.0, (double)M->opts.z, M->opts.delta,
+                                     M->opts.cg_rtol, (double)M->opts.cg_max_steps,
+                                     (double)M->opts.cols_per_cta, (double)M->c_cap};
+    if (M->dyn_exec && (realloc || key != M->dyn_key)) {
+      cudaGraphExecDestroy(M->dyn_exec);
+      M->dyn_exec = nullptr;
+    }
+    if (!M->dyn_exec) {
+      if (!M->graph_stream) CU(cudaStreamCreateWithFlags(&M->graph_stream, cudaStreamNonBlocking));
+      for (auto& q : M->dyn_stream)
+        if (!q) CU(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
+      CU(cudaStreamSynchronize(s));
+      std::vector<unsigned> counts;
+      if ((rc = build_dyn_graph<T, TA>(M, p, &counts, &M->dyn_exec)) != BSP_OK) return rc;
+      counts.resize(ncounts, 0u);   // the eager path's zero counts at the end
+      CU(cudaMemcpy(M->d_dyn_launches, counts.data(), ncounts * sizeof(unsigned),
+                    cudaMemcpyHostToDevice));
+      M->dyn_key = key;
+    }
+    CU(cudaGraphLaunch(M->dyn_exec, s));
+  } else {
+    CU(cudaMemsetAsync(M->d_dyn_launches + (ncounts - 2 * ncls), 0, 2 * ncls * sizeof(unsigned), s));
+    if ((rc = run_dyn_eager<T, TA>(M, p, s, &launches)) != BSP_OK) return rc;
+  }
+  // the chosen widths and the launch count: one read-back at the end
   std::vector<int32_t>& hc = M->h_c;
   hc.assign(M->k, 0);
-  std::vector<int32_t> cpar(M->k, 0), act, rounds(M->k, 0);
-  int launches = 0;
-  for (size_t l = 0; l < M->waves.size(); ++l) {
-    std::vector<int32_t> active = M->waves[l];
-    int boff[5], brows[4];
-    sort_by_bucket(M, active, boff, brows);
-    for (int b : active) {
-      int p = M->h_parent[b];
-      int nb = M->h_bptr[b + 1] - M->h_bptr[b];
-      int cmaxb = std::min(c_max, (nb / c_step) * c_step);
-      hc[b] = p < 0 ? c_min : std::min(hc[p], cmaxb);
-      cpar[b] = p < 0 ? 0 : hc[p];
-    }
-    auto upload = [&](const std::vector<int32_t>& list, int32_t* dst) -> int {
-      CU(cudaMemcpyAsync(dst, list.data(), sizeof(int32_t) * list.size(), cudaMemcpyHostToDevice, s));
-      return BSP_OK;
-    };
-    CU(cudaMemcpyAsync(M->d_cb, hc.data(), sizeof(int32_t) * M->k, cudaMemcpyHostToDevice, s));
-    CU(cudaMemcpyAsync(M->d_cpar, cpar.data(), sizeof(int32_t) * M->k, cudaMemcpyHostToDevice, s));
-    int32_t* d_list = M->d_waves + 2 * M->k;  // scratch list area (last third)
-    if ((rc = upload(active, d_list))) return rc;
-    auto batch_stats = [&](const std::vector<int32_t>& list, int* wmax, int* cm) {
-      *wmax = 0;
-      *cm = 0;
-      for (int b : list) {
-        *wmax = std::max(*wmax, M->h_bptr[b + 1] - M->h_bptr[b]);
-        *cm = std::max(*cm, hc[b]);
-      }
-    };
-    int wmax, cm;
-    batch_stats(active, &wmax, &cm);
-    launch_init_starts<T>(d_list, (int)active.size(), M->d_bptr, M->d_parent, M->d_root_off,
-                          M->d_cb, M->d_cpar, (const T*)M->d_starts, c_min, U, c_cap, wmax, cm, s);
-    ++launches;
-    {
-      DenseArgs da{d_list, (int)active.size(), M->d_bptr, M->d_cb, c_cap, cm, wmax, M->d_status};
-      if ((rc = launch_cholqr2<T, TA>(da, U, U, (TA*)M->d_Gp, (T*)M->d_Rsm, s, &launches)))
-        return fail(rc, "launch failed");
-    }
-    for (int guard = 0; guard < 64 && !active.empty(); ++guard) {
-      batch_stats(active, &wmax, &cm);
-      const int nbw = (int)active.size();
-      DenseArgs da{d_list, nbw, M->d_bptr, M->d_cb, c_cap, cm, wmax, M->d_status};
-      CgArgs ca{d_list, nbw, M->d_cb, c_cap, 1, M->opts.delta, M->opts.cg_rtol,
-                M->opts.cg_max_steps, M->d_status, M->d_cgstats, M->max_deg};
-      const int cs = pick_cs(M, nbw, cm, sizeof(T));
-      const bool buckets = use_buckets(M, nbw, wmax);
-      for (int t = 0; t < t_max * M->opts.z; ++t) {   // z solves per step, Onorm after each
-        rc = buckets ? launch_cg_buckets<T>(mv, U, Y, ca, boff, brows, cm, s)
-                     : launch_cg<T>(mv, U, Y, ca, cs, wmax, cm, s);
-        if (rc) return fail(rc, "CG launch failed");
-        ++launches;
-        if ((rc = launch_cholqr2<T, TA>(da, Y, U, (TA*)M->d_Gp, (T*)M->d_Rsm, s, &launches)))
-          return fail(rc, "launch failed");
-      }
-      da.sweeps = &M->d_cgstats->jacobi_sweeps;
-      if ((rc = launch_rayleigh_ritz<T, TA>(da, mv, U, (TA*)M->d_Gp, (T*)M->d_Rsm, (T*)M->d_theta,
-                                            s, &launches)))
-        return fail(rc, "launch failed");
-      if ((rc = launch_dyn_decide<T, TA>(d_list, nbw, M->d_bptr, M->d_verts, (const T*)M->d_X, U,
-                                         c_cap, M->d_cb, M->d_action, d_forced, tol, c_step,
-                                         c_max, (T*)M->d_gcol, (TA*)M->d_rho, wmax, s)))
-        return fail(rc, "launch failed");
-      ++launches;
-      act.resize(M->k);
-      CU(cudaMemcpyAsync(act.data(), M->d_action, sizeof(int32_t) * M->k, cudaMemcpyDeviceToHost, s));
-      CU(cudaMemcpyAsync(hc.data(), M->d_cb, sizeof(int32_t) * M->k, cudaMemcpyDeviceToHost, s));
-      CU(cudaStreamSynchronize(s));
-      std::vector<int32_t> grow;
-      for (int b : active) {
-        int nb = M->h_bptr[b + 1] - M->h_bptr[b];
-        int cmaxb = std::min(c_max, (nb / c_step) * c_step);
-        if (act[b] == 1 && hc[b] < cmaxb) grow.push_back(b);
-      }
-      if (grow.empty()) break;
-      sort_by_bucket(M, grow, boff, brows);
-      if ((rc = upload(grow, d_list))) return rc;
-      CU(cudaMemcpyAsync(M->d_round, rounds.data(), sizeof(int32_t) * M->k, cudaMemcpyHostToDevice, s));
-      batch_stats(grow, &wmax, &cm);
-      if ((rc = launch_dyn_grow<T, TA>(d_list, (int)grow.size(), M->d_bptr, M->d_cb, M->d_round, U,
-                                       c_cap, (const T*)M->d_gcol, seed, c_step, wmax, s)))
-        return fail(rc, "launch failed");
-      ++launches;
-      for (int b : grow) {
-        hc[b] += c_step;
-        rounds[b] += 1;
-      }
-      DenseArgs dg{d_list, (int)grow.size(), M->d_bptr, M->d_cb, c_cap, cm + c_step, wmax,
-                   M->d_status};
-      if ((rc = launch_cholqr2<T, TA>(dg, U, U, (TA*)M->d_Gp, (T*)M->d_Rsm, s, &launches)))
-        return fail(rc, "launch failed");
-      active = grow;
-    }
-  }
+  DynCtl ctl;
+  CU(cudaMemcpyAsync(hc.data(), M->d_cb, sizeof(int32_t) * M->k, cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(&ctl, M->d_dynctl, sizeof(DynCtl), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
   std::vector<int32_t> ce(M->k + 1, 0);
   for (int b = 0; b < M->k; ++b) ce[b + 1] = ce[b] + hc[b];
   CU(cudaMemcpyAsync(M->d_ceoff, ce.data(), sizeof(int32_t) * (M->k + 1), cudaMemcpyHostToDevice, s));
   if (c_out) {
-    if ((rc = from_device(c_out, M->d_cb, sizeof(int32_t) * M->k, s)) != BSP_OK) return rc;
+    if (is_device_ptr(c_out)) CU(cudaMemcpyAsync(c_out, M->d_cb, sizeof(int32_t) * M->k,
+                                                 cudaMemcpyDeviceToDevice, s));
+    else std::memcpy(c_out, hc.data(), sizeof(int32_t) * M->k);
   }
-  M->stats.gpu_launches = launches;
+  M->stats.gpu_launches = (int)(ctl.launches + (unsigned long long)launches);
   M->tracked = true;
   M->ubf_valid = false;
   return stream_error_status(M, s);
@@ -922,16 +1138,7 @@ int track_doi(bsp_mesh* M, const void* X, int c0, double eps_l, double eps_h, in
     return rc;
   if ((rc = ensure(&M->d_X, &M->cap_X, (size_t)M->n * 3 * sizeof(T))) != BSP_OK) return rc;
   if ((rc = to_device(M->d_X, X, (size_t)M->n * 3 * sizeof(T), s)) != BSP_OK) return rc;
-  if (!M->d_action) {
-    if (cudaMalloc(&M->d_action, sizeof(int32_t) * M->k) != cudaSuccess ||
-        cudaMalloc(&M->d_round, sizeof(int32_t) * M->k) != cudaSuccess ||
-        cudaMalloc(&M->d_forced, sizeof(int32_t) * M->k) != cudaSuccess ||
-        cudaMalloc(&M->d_rho, sizeof(double) * M->k) != cudaSuccess ||
-        cudaMalloc(&M->d_gcol, sizeof(double) * M->n) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(BSP_ERR_OOM, "device allocation failed");
-    }
-  }
+  if ((rc = ensure_dyn_state(M)) != BSP_OK) return rc;
   CU(cudaMemsetAsync(M->d_action, 0, sizeof(int32_t) * M->k, s));   // stop iteration per block
   CU(cudaMemsetAsync(M->d_status, 0, sizeof(int), s));
   CU(cudaMemsetAsync(M->d_cgstats, 0, sizeof(CgStats), s));

@@ -111,6 +111,7 @@ __global__ void __launch_bounds__(kThreads) k_cg(MeshView<T> mv, const T* __rest
   __shared__ T red2[2][kWarps][2 * CS];
   __shared__ T red1[2][kWarps][CS];
   const int b = a.batch[blockIdx.y];
+  if (a.live && !a.live[b]) return;
   const int c = a.cb[b];
   const int j0 = blockIdx.x * CS;
   if (j0 >= c) return;
@@ -356,6 +357,7 @@ __global__ void __launch_bounds__(kThreads) k_cg1(MeshView<T> mv, const T* __res
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T red[2][kWarps][2];
   const int b = a.batch[blockIdx.y];
+  if (a.live && !a.live[b]) return;
   const int col = blockIdx.x;
   if (col >= a.cb[b]) return;
   const int r0 = mv.bptr[b];
@@ -652,16 +654,17 @@ bool cg1_fits(int max_nb, int max_deg, int real_bytes, bool weighted) {
   return bytes <= 220 * 1024;
 }
 
-// Size bucket of a block for the batched one-column-per-CTA CG: rows per
-// thread 1, 4, 8, 16 (buckets 0..3), -1 when the block is too large.
+// Size bucket of a block for the batched CG: up to 512, 1,024, 2,048 and
+// 4,096 rows (the team CG's teams of 1, 2, 4, 8 warps), -1 when the block is
+// too large.
 int cg_bucket(int nb) {
-  return nb <= kThreads ? 0 : nb <= 4 * kThreads ? 1 : nb <= 8 * kThreads ? 2
-                            : nb <= 16 * kThreads ? 3 : -1;
+  return nb <= 512 ? 0 : nb <= 1024 ? 1 : nb <= 2048 ? 2 : nb <= 4096 ? 3 : -1;
 }
 
 // CG over a batch sorted by size bucket (bucket_off[q] .. bucket_off[q + 1] of
 // a.batch holds bucket q): one launch per non-empty bucket, each sized for
-// its own largest block.
+// its own largest block; the team kernel where its shared memory fits, else
+// one column per CTA.
 template <typename T>
 int launch_cg_buckets(const MeshView<T>& mv, const T* V, T* Y, const CgArgs& a,
                       const int* bucket_off, const int* bucket_rows, int c_max, cudaStream_t s) {
@@ -674,7 +677,9 @@ int launch_cg_buckets(const MeshView<T>& mv, const T* V, T* Y, const CgArgs& a,
     CgArgs sub = a;
     sub.batch = a.batch + bucket_off[q];
     sub.nbatch = n;
-    rc = launch_cg1_rows<T>(mv, V, Y, sub, bucket_rows[q], c_max, s);
+    rc = cgt_fits(bucket_rows[q], a.max_deg, sizeof(T), mv.wt != nullptr)
+             ? launch_cgt<T>(mv, V, Y, sub, bucket_rows[q], c_max, s)
+             : launch_cg1_rows<T>(mv, V, Y, sub, bucket_rows[q], c_max, s);
   }
   prof_end(KC_CG, s);
   return rc;

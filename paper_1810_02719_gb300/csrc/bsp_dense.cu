@@ -30,6 +30,7 @@ __global__ void __launch_bounds__(kDT) k_gram(DenseArgs a, const T* __restrict__
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* S = reinterpret_cast<T*>(smem_raw);
   const int b = a.batch[blockIdx.y];
+  if (a.live && !a.live[b]) return;
   const int c = a.cb[b];
   const int cpad = pad4(a.cmax);
   const int r0 = a.bptr[b], nb = a.bptr[b + 1] - r0;
@@ -46,6 +47,7 @@ template <typename TA>
 __global__ void k_reduce(DenseArgs a, int CH, int maxch, bool upper, const TA* __restrict__ Gp,
                          TA* __restrict__ G) {
   const int b = a.batch[blockIdx.y];
+  if (a.live && !a.live[b]) return;
   const int cpad = pad4(a.cmax);
   const int nb = a.bptr[b + 1] - a.bptr[b];
   const int nch = (nb + CH - 1) / CH;
@@ -187,6 +189,7 @@ __global__ void __launch_bounds__(kDT) k_chol(DenseArgs a, const TG* __restrict_
                                               T* __restrict__ Mout) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int b = a.batch[blockIdx.x];
+  if (a.live && !a.live[b]) return;
   const int c = a.cb[b];
   const int cpad = pad4(a.cmax);
   TA* A = reinterpret_cast<TA*>(smem_raw);
@@ -209,6 +212,7 @@ __global__ void __launch_bounds__(kDT) k_panel_mul(DenseArgs a, const T* Y, T* Q
                                                    TA* __restrict__ Gp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int b = a.batch[blockIdx.y];
+  if (a.live && !a.live[b]) return;
   const int c = a.cb[b];
   const int cpad = pad4(a.cmax);
   const int r0 = a.bptr[b], nb = a.bptr[b + 1] - r0;
@@ -268,6 +272,7 @@ __global__ void __launch_bounds__(kDT) k_rr(DenseArgs a, MeshView<T> mv, const T
                                             int CH, int maxch, TA* __restrict__ Gp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int b = a.batch[blockIdx.y];
+  if (a.live && !a.live[b]) return;
   const int c = a.cb[b];
   const int cpad = pad4(a.cmax);
   const int r0 = a.bptr[b], nb = a.bptr[b + 1] - r0;
@@ -304,6 +309,7 @@ __global__ void __launch_bounds__(kDT) k_jacobi(DenseArgs a, const TA* __restric
                                                 T* __restrict__ Qout, T* __restrict__ theta) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int b = a.batch[blockIdx.x];
+  if (a.live && !a.live[b]) return;
   const int c = a.cb[b];
   const int cpad = pad4(a.cmax);
   const int ne = (c + 1) & ~1;  // even size for round-robin pairing (dummy index if c is odd)

@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(kT) k_dyn_decide(const int32_t* batch, const i
                                                    const T* __restrict__ U, int ld, int32_t* cb,
                                                    int32_t* action, const int32_t* forced,
                                                    double tol, int c_step, int c_max, T* gcol,
-                                                   TA* rho_out) {
+                                                   TA* rho_out, int32_t* live) {
   __shared__ TA Ered[kT / 32][3 * 32];
   __shared__ T Es[kMaxC][3];
   __shared__ TA red[kT / 32];
@@ -86,6 +86,7 @@ __global__ void __launch_bounds__(kT) k_dyn_decide(const int32_t* batch, const i
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   T* Xs = reinterpret_cast<T*>(dyn_smem);   // the block's coordinates, local order [nb x 3]
   const int b = batch[blockIdx.x];
+  if (live && !live[b]) return;
   const int c = cb[b];
   const int r0 = bptr[b], nb = bptr[b + 1] - r0;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -190,21 +191,27 @@ __global__ void __launch_bounds__(kT) k_dyn_decide(const int32_t* batch, const i
     action[b] = act;
     if (act == 0) cb[b] = cj;
     rho_out[b] = rho;
+    if (live) {
+      const int cmaxb = min(c_max, (nb / c_step) * c_step);
+      live[b] = (act == 1 && c < cmaxb) ? 1 : 0;
+    }
   }
 }
 
 // Append c_step columns at position c = cb[b]: [e/||e||, hash columns], all
 // projected off the current basis U[:, :c] (one classical Gram-Schmidt sweep;
-// the Onorm that follows re-orthonormalises).  Updates cb[b] += c_step.
+// the Onorm that follows re-orthonormalises).  Updates cb[b] += c_step and
+// round[b] += 1 (the hash counter of the next growth).
 template <typename T, typename TA>
 __global__ void __launch_bounds__(kT) k_dyn_grow(const int32_t* batch, const int32_t* bptr,
-                                                 int32_t* cb, const int32_t* round, T* U, int ld,
+                                                 int32_t* cb, int32_t* round, T* U, int ld,
                                                  const T* __restrict__ gcol, uint64_t seed,
-                                                 int c_step) {
+                                                 int c_step, const int32_t* live) {
   __shared__ TA red[kT / 32];
   __shared__ T Cm[kMaxC][8];              // U^T G, c x c_step (c_step <= 8)
   __shared__ T part[kT / 32][32 * 8];     // per-warp partial products (one 32-column slice)
   const int b = batch[blockIdx.x];
+  if (live && !live[b]) return;
   const int c = cb[b];
   const int r0 = bptr[b], nb = bptr[b + 1] - r0;
   const int rnd = round[b];
@@ -262,7 +269,98 @@ __global__ void __launch_bounds__(kT) k_dyn_grow(const int32_t* batch, const int
     }
     row[c + g] -= (s0 + s1) + (s2 + s3);
   }
-  if (threadIdx.x == 0) cb[b] = c + c_step;
+  if (threadIdx.x == 0) {
+    cb[b] = c + c_step;
+    round[b] = rnd + 1;
+  }
+}
+
+// ---- device-side control of the dynamic-c rounds (one CTA per wave)
+constexpr int kCT = 256;
+
+BSP_DEV int block_max(int v, int* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  int m = red[0];
+  for (int w = 1; w < kCT / 32; ++w) m = max(m, red[w]);
+  return m;
+}
+
+// width class of the largest width: ceil(c / cls_width) - 1, clamped to the
+// classes built (a width above every class selects none: no body runs)
+BSP_DEV int width_class(int cmax, int cls_width, int ncls) {
+  const int q = (cmax + cls_width - 1) / cls_width - 1;
+  return q < 0 ? 0 : (q < ncls ? q : ncls);
+}
+
+__global__ void __launch_bounds__(kCT) k_dyn_wave_init(
+    const int32_t* wave, int nw, const int32_t* bptr, const int32_t* parent, int32_t* cb,
+    int32_t* cpar, int32_t* live, int32_t* round, int c_min, int c_max, int c_step, int cls_width,
+    int ncls, const unsigned* start_launches, DynCtl* ctl, int set_handle,
+    cudaGraphConditionalHandle h_start) {
+  __shared__ int red[kCT / 32];
+  int mx = 0;
+  for (int i = threadIdx.x; i < nw; i += kCT) {
+    const int b = wave[i];
+    const int p = parent[b];
+    const int nb = bptr[b + 1] - bptr[b];
+    const int cmaxb = min(c_max, (nb / c_step) * c_step);
+    const int c = p < 0 ? c_min : min(cb[p], cmaxb);
+    cb[b] = c;
+    cpar[b] = p < 0 ? 0 : cb[p];
+    live[b] = 1;
+    round[b] = 0;
+    mx = max(mx, c);
+  }
+  mx = block_max(mx, red);
+  if (threadIdx.x == 0) {
+    const int q = width_class(mx, cls_width, ncls);
+    ctl->cls_start = q;
+    ctl->rounds = 0;
+    ctl->more = 1;
+    ctl->launches += 1 + (q < ncls ? start_launches[q] : 0u);
+    if (set_handle) cudaGraphSetConditional(h_start, (unsigned)q);
+  }
+}
+
+__global__ void __launch_bounds__(kCT) k_dyn_class(const int32_t* wave, int nw, const int32_t* cb,
+                                                   const int32_t* live, int cls_width, int ncls,
+                                                   const unsigned* round_launches, DynCtl* ctl,
+                                                   int set_handle,
+                                                   cudaGraphConditionalHandle h_round) {
+  __shared__ int red[kCT / 32];
+  int mx = 0;
+  for (int i = threadIdx.x; i < nw; i += kCT) {
+    const int b = wave[i];
+    if (live[b]) mx = max(mx, cb[b]);
+  }
+  mx = block_max(mx, red);
+  if (threadIdx.x == 0) {
+    const int q = width_class(mx, cls_width, ncls);
+    ctl->cls_round = q;
+    ctl->launches += 2 + (q < ncls ? round_launches[q] : 0u);
+    if (set_handle) cudaGraphSetConditional(h_round, (unsigned)q);
+  }
+}
+
+__global__ void __launch_bounds__(kCT) k_dyn_next(const int32_t* wave, int nw,
+                                                  const int32_t* live, int max_rounds, DynCtl* ctl,
+                                                  int set_handle,
+                                                  cudaGraphConditionalHandle h_while) {
+  __shared__ int red[kCT / 32];
+  int any = 0;
+  for (int i = threadIdx.x; i < nw; i += kCT) any |= live[wave[i]] ? 1 : 0;
+  any = block_max(any, red);
+  if (threadIdx.x == 0) {
+    const int r = ctl->rounds + 1;
+    ctl->rounds = r;
+    const int more = (any && r < max_rounds) ? 1 : 0;
+    ctl->more = more;
+    if (set_handle) cudaGraphSetConditional(h_while, (unsigned)more);
+  }
 }
 
 // The paper's dynamic OI (Sec. 5, Algorithm 2): one decision per iteration
@@ -373,13 +471,13 @@ template <typename T, typename TA>
 int launch_dyn_decide(const int32_t* batch, int nbatch, const int32_t* bptr, const int32_t* verts,
                       const T* X, const T* U, int ld, int32_t* cb, int32_t* action,
                       const int32_t* forced, double tol, int c_step, int c_max, T* gcol,
-                      TA* rho_out, int max_nb, cudaStream_t s) {
+                      TA* rho_out, int max_nb, cudaStream_t s, int32_t* live) {
   if (c_step < 8 || c_max > kMaxC) return BSP_ERR_INVALID_ARG;
   const size_t smem = (size_t)max_nb * 3 * sizeof(T);
   if (smem > 160 * 1024) return BSP_ERR_INVALID_ARG;
   prof_begin(KC_DYN, s);
   k_dyn_decide<T, TA><<<nbatch, kT, smem, s>>>(batch, bptr, verts, X, U, ld, cb, action, forced,
-                                               tol, c_step, c_max, gcol, rho_out);
+                                               tol, c_step, c_max, gcol, rho_out, live);
   prof_end(KC_DYN, s);
   return cudaGetLastError() == cudaSuccess ? BSP_OK : BSP_ERR_CUDA;
 }
@@ -392,12 +490,38 @@ void configure_dyn_kernels() {
 
 template <typename T, typename TA>
 int launch_dyn_grow(const int32_t* batch, int nbatch, const int32_t* bptr, int32_t* cb,
-                    const int32_t* round, T* U, int ld, const T* gcol, uint64_t seed,
-                    int c_step, int max_nb, cudaStream_t s) {
+                    int32_t* round, T* U, int ld, const T* gcol, uint64_t seed,
+                    int c_step, int max_nb, cudaStream_t s, const int32_t* live) {
   if (c_step > 8) return BSP_ERR_INVALID_ARG;
   prof_begin(KC_DYN, s);
-  k_dyn_grow<T, TA><<<nbatch, kT, 0, s>>>(batch, bptr, cb, round, U, ld, gcol, seed, c_step);
+  k_dyn_grow<T, TA><<<nbatch, kT, 0, s>>>(batch, bptr, cb, round, U, ld, gcol, seed, c_step,
+                                          live);
   prof_end(KC_DYN, s);
+  return cudaGetLastError() == cudaSuccess ? BSP_OK : BSP_ERR_CUDA;
+}
+
+int launch_dyn_wave_init(const int32_t* wave, int nw, const int32_t* bptr, const int32_t* parent,
+                         int32_t* cb, int32_t* cpar, int32_t* live, int32_t* round, int c_min,
+                         int c_max, int c_step, int cls_width, int ncls,
+                         const unsigned* start_launches, DynCtl* ctl, int set_handle,
+                         cudaGraphConditionalHandle h_start, cudaStream_t s) {
+  k_dyn_wave_init<<<1, kCT, 0, s>>>(wave, nw, bptr, parent, cb, cpar, live, round, c_min, c_max,
+                                    c_step, cls_width, ncls, start_launches, ctl, set_handle,
+                                    h_start);
+  return cudaGetLastError() == cudaSuccess ? BSP_OK : BSP_ERR_CUDA;
+}
+
+int launch_dyn_class(const int32_t* wave, int nw, const int32_t* cb, const int32_t* live,
+                     int cls_width, int ncls, const unsigned* round_launches, DynCtl* ctl,
+                     int set_handle, cudaGraphConditionalHandle h_round, cudaStream_t s) {
+  k_dyn_class<<<1, kCT, 0, s>>>(wave, nw, cb, live, cls_width, ncls, round_launches, ctl,
+                                set_handle, h_round);
+  return cudaGetLastError() == cudaSuccess ? BSP_OK : BSP_ERR_CUDA;
+}
+
+int launch_dyn_next(const int32_t* wave, int nw, const int32_t* live, int max_rounds, DynCtl* ctl,
+                    int set_handle, cudaGraphConditionalHandle h_while, cudaStream_t s) {
+  k_dyn_next<<<1, kCT, 0, s>>>(wave, nw, live, max_rounds, ctl, set_handle, h_while);
   return cudaGetLastError() == cudaSuccess ? BSP_OK : BSP_ERR_CUDA;
 }
 
@@ -430,23 +554,23 @@ template void launch_init_starts<double>(const int32_t*, int, const int32_t*, co
 template int launch_dyn_decide<float, double>(const int32_t*, int, const int32_t*, const int32_t*,
                                               const float*, const float*, int, int32_t*, int32_t*,
                                               const int32_t*, double, int, int, float*, double*,
-                                              int, cudaStream_t);
+                                              int, cudaStream_t, int32_t*);
 template int launch_dyn_decide<float, float>(const int32_t*, int, const int32_t*, const int32_t*,
                                              const float*, const float*, int, int32_t*, int32_t*,
                                              const int32_t*, double, int, int, float*, float*, int,
-                                             cudaStream_t);
+                                             cudaStream_t, int32_t*);
 template int launch_dyn_decide<double, double>(const int32_t*, int, const int32_t*,
                                                const int32_t*, const double*, const double*, int,
                                                int32_t*, int32_t*, const int32_t*, double, int,
-                                               int, double*, double*, int, cudaStream_t);
+                                               int, double*, double*, int, cudaStream_t, int32_t*);
 template int launch_dyn_grow<float, double>(const int32_t*, int, const int32_t*, int32_t*,
-                                            const int32_t*, float*, int, const float*, uint64_t,
-                                            int, int, cudaStream_t);
+                                            int32_t*, float*, int, const float*, uint64_t,
+                                            int, int, cudaStream_t, const int32_t*);
 template int launch_dyn_grow<float, float>(const int32_t*, int, const int32_t*, int32_t*,
-                                           const int32_t*, float*, int, const float*, uint64_t,
-                                           int, int, cudaStream_t);
+                                           int32_t*, float*, int, const float*, uint64_t,
+                                           int, int, cudaStream_t, const int32_t*);
 template int launch_dyn_grow<double, double>(const int32_t*, int, const int32_t*, int32_t*,
-                                             const int32_t*, double*, int, const double*, uint64_t,
-                                             int, int, cudaStream_t);
+                                             int32_t*, double*, int, const double*, uint64_t,
+                                             int, int, cudaStream_t, const int32_t*);
 
 }  // namespace bsp

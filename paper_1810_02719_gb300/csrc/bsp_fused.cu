@@ -326,6 +326,7 @@ __global__ void __launch_bounds__(kDT) k_cholqr2_cluster(DenseArgs a, const T* Y
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int slot = blockIdx.y;
   const int b = a.batch[slot];
+  if (a.live && !a.live[b]) return;
   const int c = a.cb[b];
   const int cpad = pad4(a.cmax);
   const int p = blockIdx.x;

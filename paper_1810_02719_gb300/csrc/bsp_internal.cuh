@@ -145,6 +145,9 @@ struct CgArgs {
   // right-hand sides read from the rows of block vsrc[b] instead of block b
   // (a warm start read in place from a same-size parent); nullptr: own rows
   const int32_t* vsrc = nullptr;
+  // [k] per-block flags: a CTA whose block has live[b] == 0 returns at once
+  // (the device-driven dynamic-c rounds); nullptr: every block of the batch
+  const int32_t* live = nullptr;
 };
 extern bool g_disable_cg1;  // force the shared-memory CG kernel (A/B checks)
 template <typename T>
@@ -154,6 +157,13 @@ int launch_cg(const MeshView<T>& mv, const T* V, T* Y, const CgArgs& a, int cs, 
 // (rows per thread 1, 4, 8, 16), bucket_off[0..4] (host) delimiting the
 // buckets and bucket_rows[q] the largest block of bucket q.
 int cg_bucket(int nb);   // -1 when the block is too large (> 4,096 rows)
+// Team CG (bsp_cgt.cu): one column per team of 1-8 warps, the pattern in
+// shared memory once per CTA; blocks up to 4,096 rows, degrees up to 16.
+bool cgt_fits(int max_nb, int max_deg, int real_bytes, bool weighted);
+template <typename T>
+int launch_cgt(const MeshView<T>& mv, const T* V, T* Y, const CgArgs& a, int max_nb, int c_max,
+               cudaStream_t s);
+void configure_cgt_kernels();
 bool cg1_fits(int max_nb, int max_deg, int real_bytes, bool weighted);
 template <typename T>
 int launch_cg_buckets(const MeshView<T>& mv, const T* V, T* Y, const CgArgs& a,
@@ -173,6 +183,7 @@ struct DenseArgs {
   int max_nb;               // largest n_b in the batch
   int* status;
   int* sweeps = nullptr;    // optional: Jacobi sweeps performed (summed)
+  const int32_t* live = nullptr;  // as CgArgs::live
 };
 template <typename T, typename TA>
 int launch_cholqr2(const DenseArgs& a, const T* Y, T* Q, TA* Gp, T* Rsm, cudaStream_t s,
@@ -287,15 +298,48 @@ void launch_init_starts(const int32_t* batch, int nbatch, const int32_t* bptr,
                         const int32_t* parent, const int32_t* root_off, const int32_t* cb,
                         const int32_t* cpar, const T* starts, int ld_start, T* U, int ld,
                         int max_nb, int cmax, cudaStream_t s, const T* Usrc = nullptr);
+// live (optional, [k]): the decision clears live[b] unless block b grows
+// (not met and below min(c_max, n_b rounded down to c_step)); the growth step
+// skips blocks with live[b] == 0 and advances round[b] of the others.
 template <typename T, typename TA>
 int launch_dyn_decide(const int32_t* batch, int nbatch, const int32_t* bptr, const int32_t* verts,
                       const T* X, const T* U, int ld, int32_t* cb, int32_t* action,
                       const int32_t* forced, double tol, int c_step, int c_max, T* gcol,
-                      TA* rho_out, int max_nb, cudaStream_t s);
+                      TA* rho_out, int max_nb, cudaStream_t s, int32_t* live = nullptr);
 template <typename T, typename TA>
 int launch_dyn_grow(const int32_t* batch, int nbatch, const int32_t* bptr, int32_t* cb,
-                    const int32_t* round, T* U, int ld, const T* gcol, uint64_t seed,
-                    int c_step, int max_nb, cudaStream_t s);
+                    int32_t* round, T* U, int ld, const T* gcol, uint64_t seed,
+                    int c_step, int max_nb, cudaStream_t s, const int32_t* live = nullptr);
+
+// Device-side control of the dynamic-c schedule: one wave's state between
+// rounds.  A graph replays the rounds under conditional nodes (a WHILE over
+// rounds, a SWITCH over width classes) whose values these kernels set; the
+// eager path reads the same fields back instead.
+struct DynCtl {
+  int cls_start;                 // width class of the wave's start bases
+  int cls_round;                 // width class of the next round (largest live width)
+  int more;                      // another round follows
+  int rounds;                    // rounds run in this wave
+  unsigned long long launches;   // kernels launched by the schedule (summed over the call)
+};
+// Wave start: widths (root c_min, child min(parent width, c_max, n_b rounded
+// down)), parent widths, live = 1, round = 0; the start's width class.
+// Launch counts: ctl->launches += start_launches[class] + 1.
+int launch_dyn_wave_init(const int32_t* wave, int nw, const int32_t* bptr, const int32_t* parent,
+                         int32_t* cb, int32_t* cpar, int32_t* live, int32_t* round, int c_min,
+                         int c_max, int c_step, int cls_width, int ncls,
+                         const unsigned* start_launches, DynCtl* ctl, int set_handle,
+                         cudaGraphConditionalHandle h_start, cudaStream_t s);
+// Round class: the largest width among live blocks -> ctl->cls_round and the
+// SWITCH handle; ctl->launches += round_launches[class] + 2 (this kernel and
+// the round's end).
+int launch_dyn_class(const int32_t* wave, int nw, const int32_t* cb, const int32_t* live,
+                     int cls_width, int ncls, const unsigned* round_launches, DynCtl* ctl,
+                     int set_handle, cudaGraphConditionalHandle h_round, cudaStream_t s);
+// Round end: ctl->more = any live block and fewer than max_rounds rounds run;
+// sets the WHILE handle.
+int launch_dyn_next(const int32_t* wave, int nw, const int32_t* live, int max_rounds, DynCtl* ctl,
+                    int set_handle, cudaGraphConditionalHandle h_while, cudaStream_t s);
 
 // Overlapped parts (bsp_overlap.cu): copy weights and copy counts per vertex,
 // then (after a scan of the counts) the per-vertex copy lists in copy order,
@@ -399,6 +443,15 @@ struct bsp_mesh {
   cudaGraphExec_t graph_exec = nullptr;
   int graph_c = -1, graph_t = -1, graph_launches = 0, graph_cs = -1;
   cudaStream_t graph_stream = nullptr;
+  // dynamic-c schedule: device state and its graph (conditional nodes), keyed
+  // by the call's parameters
+  int32_t* d_live = nullptr;
+  bsp::DynCtl* d_dynctl = nullptr;
+  unsigned* d_dyn_launches = nullptr;  // per wave: start and round launch counts per class
+  size_t cap_dyn_launches = 0;
+  cudaGraphExec_t dyn_exec = nullptr;
+  std::vector<double> dyn_key;
+  cudaStream_t dyn_stream[2] = {nullptr, nullptr};
   bsp_stats stats{};
   // low-pass filter checkpoints (last bsp_filter_forward)
   void* d_ckV = nullptr;
