@@ -156,18 +156,18 @@ void configure_once() {
   });
 }
 
-// Sort a batch by the size bucket of the batched CG (up to 512, 1,024, 2,048,
-// 4,096 rows; blocks too large last) and return the bucket offsets off[0..4] and the
+// Sort a batch by the size bucket of the batched CG (cg_bucket; blocks too
+// large last) and return the bucket offsets off[0..kCgBuckets] and the
 // largest block of every bucket.
-void sort_by_bucket(const bsp_mesh* M, std::vector<int32_t>& list, int off[5], int rows[4]) {
+void sort_by_bucket(const bsp_mesh* M, std::vector<int32_t>& list, int* off, int* rows) {
   auto nb = [&](int b) { return M->h_bptr[b + 1] - M->h_bptr[b]; };
   auto key = [&](int b) {
     const int q = cg_bucket(nb(b));
-    return q < 0 ? 4 : q;
+    return q < 0 ? kCgBuckets : q;
   };
   std::stable_sort(list.begin(), list.end(), [&](int a, int b) { return key(a) < key(b); });
   off[0] = 0;
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < kCgBuckets; ++q) {
     int cnt = 0, mx = 0;
     for (int b : list)
       if (key(b) == q) {
@@ -206,6 +206,11 @@ void release(bsp_mesh* m) {
   if (m->graph_stream) cudaStreamDestroy(m->graph_stream);
   for (cudaStream_t q : m->dyn_stream)
     if (q) cudaStreamDestroy(q);
+  for (int q = 0; q < kCgBuckets - 1; ++q) {
+    if (m->cg_fork.aux[q]) cudaStreamDestroy(m->cg_fork.aux[q]);
+    if (m->cg_fork.join[q]) cudaEventDestroy(m->cg_fork.join[q]);
+  }
+  if (m->cg_fork.fork) cudaEventDestroy(m->cg_fork.fork);
 }
 
 int stream_error_status(bsp_mesh* m, cudaStream_t s) {
@@ -401,6 +406,13 @@ int create_common(const double* xyz, int64_t n, const int32_t* tri, int64_t m, i
   M->stats.intra_edges = M->intra_edges;
   M->stats.max_block = M->max_nb;
   M->stats.levels = levels;
+  // side streams of the batched CG (bucket launches run side by side)
+  for (int q = 0; q < kCgBuckets - 1; ++q)
+    if (cudaStreamCreateWithFlags(&M->cg_fork.aux[q], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&M->cg_fork.join[q], cudaEventDisableTiming) != cudaSuccess)
+      return bail(fail(BSP_ERR_CUDA, "stream creation failed"));
+  if (cudaEventCreateWithFlags(&M->cg_fork.fork, cudaEventDisableTiming) != cudaSuccess)
+    return bail(fail(BSP_ERR_CUDA, "event creation failed"));
   *out = M;
   return BSP_OK;
 }
@@ -612,7 +624,7 @@ int enqueue_fixed(bsp_mesh* M, int c, int t_max, cudaStream_t s, int* launches) 
       cg.z = g;
       if (t == 0 && in_place) cg.vsrc = M->d_parent;
       rc = buckets ? launch_cg_buckets<T>(mv, U, Y, cg, M->wave_bucket[l].data(),
-                                          M->wave_bucket_rows[l].data(), c, s)
+                                          M->wave_bucket_rows[l].data(), c, s, &M->cg_fork)
                    : launch_cg<T>(mv, U, Y, cg, cs, wmax, c, s);
       if (rc) return fail(rc, "CG launch failed (block too large for shared memory?)");
       ++*launches;
@@ -834,7 +846,7 @@ int enqueue_dyn_round(bsp_mesh* M, int l, int cm, const DynParams& p, cudaStream
   const bool buckets = use_buckets(M, nw, wmax);
   for (int t = 0; t < p.t_max * M->opts.z; ++t) {   // z solves per step, Onorm after each
     rc = buckets ? launch_cg_buckets<T>(mv, U, Y, ca, M->wave_bucket[l].data(),
-                                        M->wave_bucket_rows[l].data(), cm, s)
+                                        M->wave_bucket_rows[l].data(), cm, s, &M->cg_fork)
                  : launch_cg<T>(mv, U, Y, ca, cs, wmax, cm, s);
     if (rc) return fail(rc, "CG launch failed");
     ++*launches;

@@ -654,33 +654,54 @@ bool cg1_fits(int max_nb, int max_deg, int real_bytes, bool weighted) {
   return bytes <= 220 * 1024;
 }
 
-// Size bucket of a block for the batched CG: up to 512, 1,024, 2,048 and
-// 4,096 rows (the team CG's teams of 1, 2, 4, 8 warps), -1 when the block is
-// too large.
+// Size bucket of a block for the batched CG: up to 256, 512, 1,024, 2,048
+// and 4,096 rows (the team CG's team sizes), -1 when the block is too large.
 int cg_bucket(int nb) {
-  return nb <= 512 ? 0 : nb <= 1024 ? 1 : nb <= 2048 ? 2 : nb <= 4096 ? 3 : -1;
+  return nb <= 256 ? 0 : nb <= 512 ? 1 : nb <= 1024 ? 2 : nb <= 2048 ? 3 : nb <= 4096 ? 4 : -1;
 }
 
 // CG over a batch sorted by size bucket (bucket_off[q] .. bucket_off[q + 1] of
 // a.batch holds bucket q): one launch per non-empty bucket, each sized for
 // its own largest block; the team kernel where its shared memory fits, else
-// one column per CTA.
+// one column per CTA.  With `fork`, the buckets after the first run on side
+// streams concurrently with it (each launch ends on its slowest column; side
+// by side their tails overlap), joined back into s before the return.
 template <typename T>
 int launch_cg_buckets(const MeshView<T>& mv, const T* V, T* Y, const CgArgs& a,
-                      const int* bucket_off, const int* bucket_rows, int c_max, cudaStream_t s) {
+                      const int* bucket_off, const int* bucket_rows, int c_max, cudaStream_t s,
+                      const CgFork* fork) {
   if (!(a.max_deg > 0 && a.max_deg <= 16)) return BSP_ERR_INVALID_ARG;
   prof_begin(KC_CG, s);
   int rc = BSP_OK;
-  for (int q = 0; q < 4 && rc == BSP_OK; ++q) {
+  int used[kCgBuckets] = {};
+  bool forked = false;
+  for (int q = 0, side = 0; q < kCgBuckets && rc == BSP_OK; ++q) {
     const int n = bucket_off[q + 1] - bucket_off[q];
     if (n <= 0) continue;
+    cudaStream_t st = s;
+    if (fork && side > 0) {
+      if (!forked) {
+        if (cudaEventRecord(fork->fork, s) != cudaSuccess) return BSP_ERR_CUDA;
+        forked = true;
+      }
+      st = fork->aux[side - 1];
+      if (cudaStreamWaitEvent(st, fork->fork, 0) != cudaSuccess) return BSP_ERR_CUDA;
+      used[side - 1] = 1;
+    }
+    ++side;
     CgArgs sub = a;
     sub.batch = a.batch + bucket_off[q];
     sub.nbatch = n;
     rc = cgt_fits(bucket_rows[q], a.max_deg, sizeof(T), mv.wt != nullptr)
-             ? launch_cgt<T>(mv, V, Y, sub, bucket_rows[q], c_max, s)
-             : launch_cg1_rows<T>(mv, V, Y, sub, bucket_rows[q], c_max, s);
+             ? launch_cgt<T>(mv, V, Y, sub, bucket_rows[q], c_max, st)
+             : launch_cg1_rows<T>(mv, V, Y, sub, bucket_rows[q], c_max, st);
   }
+  for (int k = 0; k < kCgBuckets - 1; ++k)
+    if (used[k]) {
+      if (cudaEventRecord(fork->join[k], fork->aux[k]) != cudaSuccess ||
+          cudaStreamWaitEvent(s, fork->join[k], 0) != cudaSuccess)
+        return BSP_ERR_CUDA;
+    }
   prof_end(KC_CG, s);
   return rc;
 }
@@ -746,9 +767,11 @@ template int launch_cg<float>(const MeshView<float>&, const float*, float*, cons
 template int launch_cg<double>(const MeshView<double>&, const double*, double*, const CgArgs&,
                                int, int, int, cudaStream_t);
 template int launch_cg_buckets<float>(const MeshView<float>&, const float*, float*,
-                                      const CgArgs&, const int*, const int*, int, cudaStream_t);
+                                      const CgArgs&, const int*, const int*, int, cudaStream_t,
+                                      const CgFork*);
 template int launch_cg_buckets<double>(const MeshView<double>&, const double*, double*,
-                                       const CgArgs&, const int*, const int*, int, cudaStream_t);
+                                       const CgArgs&, const int*, const int*, int, cudaStream_t,
+                                       const CgFork*);
 template void launch_spmm<float>(int64_t, const MeshView<float>&, const int32_t*, float,
                                  const float*, float*, int, cudaStream_t);
 template void launch_spmm<double>(int64_t, const MeshView<double>&, const int32_t*, double,

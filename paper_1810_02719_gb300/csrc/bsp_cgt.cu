@@ -14,10 +14,14 @@
 // independently: a column that converges frees nothing but also waits for
 // nothing, and a team of one warp synchronises with __syncwarp only.
 //
-// Buckets by block size: TW = 1 up to 512 rows (R = 8 up to 256), 2 up to
-// 1,024, 4 up to 2,048, 8 up to 4,096.  The stopping rule and the initial
-// guess (x0 = b (b, b) / (b, A b)) are those of the one-column-per-CTA
-// kernel in bsp_cg.cu.
+// Two forms.  Unweighted meshes of degree <= 8 up to 2,048 rows keep each
+// row's neighbour indices (packed two per register) and diagonal in registers
+// too, 8 rows per lane: teams of 1, 2, 4, 8 warps up to 256, 512, 1,024,
+// 2,048 rows.  The neighbour reads are then the only shared-memory loads of
+// the product.  Otherwise the pattern stays in shared memory, 16 rows per
+// lane (teams of 1, 2, 4, 8 warps up to 512, 1,024, 2,048, 4,096 rows).  The
+// stopping rule and the initial guess (x0 = b (b, b) / (b, A b)) are those of
+// the one-column-per-CTA kernel in bsp_cg.cu.
 #include "bsp_internal.cuh"
 
 namespace bsp {
@@ -38,21 +42,24 @@ BSP_DEV T warp_sum_t(T v) {
 }
 
 // Shared memory of one CTA: diagonal [CAP] T, weights [ELLW][CAP] T
-// (weighted meshes), team vectors [NT][CAP + 1] T, neighbours [ELLW][CAP] u16.
-template <typename T, int TW, int R, int ELLW>
+// (weighted meshes), team vectors [NT][CAP + 1] T, neighbours [ELLW][CAP] u16;
+// with the pattern in registers (REG) only the team vectors.
+template <typename T, int TW, int R, int ELLW, bool REG>
 constexpr size_t cgt_smem(bool weighted) {
   constexpr size_t CAP = 32 * TW * R, NT = kWarpsCta / TW;
+  if (REG) return NT * (CAP + 1) * sizeof(T);
   return CAP * sizeof(T) + (weighted ? ELLW * CAP * sizeof(T) : 0) + NT * (CAP + 1) * sizeof(T) +
          ELLW * CAP * sizeof(uint16_t);
 }
 
 // Two CTAs per SM in FP32 (x, r, p, s, w of 16 rows in 128 registers); one
 // in FP64, whose registers would otherwise spill.
-template <typename T, int TW, int R, int ELLW>
+template <typename T, int TW, int R, int ELLW, bool REG>
 __global__ void __launch_bounds__(kThreadsCta, sizeof(T) == 4 ? 2 : 1)
     k_cgt(MeshView<T> mv, const T* __restrict__ V, T* __restrict__ Y, CgArgs a) {
   constexpr int CAP = 32 * TW * R;
   constexpr int NT = kWarpsCta / TW;
+  static_assert(!REG || ELLW % 2 == 0, "indices are packed in pairs");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T tred[2][kWarpsCta][2];
   const int b = a.batch[blockIdx.y];
@@ -63,12 +70,12 @@ __global__ void __launch_bounds__(kThreadsCta, sizeof(T) == 4 ? 2 : 1)
   const int r0 = mv.bptr[b], nb = mv.bptr[b + 1] - r0;
   const bool weighted = mv.wt != nullptr;
   T* sdd = reinterpret_cast<T*>(smem_raw);
-  T* swt = sdd + CAP;
-  T* svec = swt + (weighted ? ELLW * CAP : 0);
+  T* swt = sdd + (REG ? 0 : CAP);
+  T* svec = swt + (weighted && !REG ? ELLW * CAP : 0);
   uint16_t* snb = reinterpret_cast<uint16_t*>(svec + NT * (CAP + 1));
   const T delta = (T)a.delta;
   const int dmax = a.max_deg < ELLW ? a.max_deg : ELLW;   // uniform: entries past it skipped
-  for (int i = threadIdx.x; i < CAP; i += kThreadsCta) {
+  for (int i = threadIdx.x; i < CAP && !REG; i += kThreadsCta) {
     T d0 = 0;
     int dg = 0, e0 = 0;
     if (i < nb) {
@@ -94,6 +101,29 @@ __global__ void __launch_bounds__(kThreadsCta, sizeof(T) == 4 ? 2 : 1)
   const T rtol2 = (T)(a.rtol * a.rtol);
 
   auto row = [&](int m) { return lane + 32 * (wt + TW * m); };
+  // REG: the team's rows' diagonal + delta and neighbour indices (two per word)
+  constexpr int RP = REG ? R : 1, EP = REG ? ELLW / 2 : 1;
+  T rdd[RP];
+  uint32_t rnb[RP][EP];
+  if constexpr (REG) {
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      const int i = row(m);
+      int dg = 0, e0 = 0;
+      rdd[m] = T(0);
+      if (i < nb) {
+        e0 = mv.rowptr[r0 + i];
+        dg = mv.rowptr[r0 + i + 1] - e0;
+        rdd[m] = mv.diag[r0 + i] + delta;
+      }
+#pragma unroll
+      for (int e = 0; e < ELLW / 2; ++e) {
+        const uint32_t lo = 2 * e < dg ? (uint32_t)mv.col[e0 + 2 * e] : (uint32_t)CAP;
+        const uint32_t hi = 2 * e + 1 < dg ? (uint32_t)mv.col[e0 + 2 * e + 1] : (uint32_t)CAP;
+        rnb[m][e] = lo | (hi << 16);
+      }
+    }
+  }
   auto sync_vec = [&]() {
     if constexpr (TW == 1) __syncwarp();
     else team_barrier(1 + team, 32 * TW);
@@ -123,6 +153,20 @@ __global__ void __launch_bounds__(kThreadsCta, sizeof(T) == 4 ? 2 : 1)
   };
   // out_m = (D + delta) v_m - sum_e C v_nbr, v read from vec
   auto apply = [&](const T (&v)[R], T (&out)[R]) {
+    if constexpr (REG) {
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        T acc = rdd[m] * v[m];
+#pragma unroll
+        for (int e = 0; e < ELLW / 2; ++e) {
+          const uint32_t w = rnb[m][e];
+          acc -= vec[w & 0xffffu];
+          acc -= vec[w >> 16];
+        }
+        out[m] = acc;
+      }
+      return;
+    }
 #pragma unroll
     for (int m = 0; m < R; ++m) {
       const int i = row(m);
@@ -254,35 +298,42 @@ __global__ void __launch_bounds__(kThreadsCta, sizeof(T) == 4 ? 2 : 1)
   }
 }
 
-template <typename T, int TW, int R, int ELLW>
+template <typename T, int TW, int R, int ELLW, bool REG>
 int launch_t(const MeshView<T>& mv, const T* V, T* Y, const CgArgs& a, int c_max,
              cudaStream_t s) {
   constexpr int NT = kWarpsCta / TW;
-  const size_t smem = cgt_smem<T, TW, R, ELLW>(mv.wt != nullptr);
+  const size_t smem = cgt_smem<T, TW, R, ELLW, REG>(mv.wt != nullptr);
   if (smem > 220 * 1024) return BSP_ERR_INVALID_ARG;
   dim3 grid((c_max + NT - 1) / NT, a.nbatch);
-  k_cgt<T, TW, R, ELLW><<<grid, kThreadsCta, smem, s>>>(mv, V, Y, a);
+  k_cgt<T, TW, R, ELLW, REG><<<grid, kThreadsCta, smem, s>>>(mv, V, Y, a);
   return cudaGetLastError() == cudaSuccess ? BSP_OK : BSP_ERR_CUDA;
 }
 
 template <typename T, int ELLW>
 int launch_rows(const MeshView<T>& mv, const T* V, T* Y, const CgArgs& a, int max_nb, int c_max,
                 cudaStream_t s) {
-  if (max_nb <= 256) return launch_t<T, 1, 8, ELLW>(mv, V, Y, a, c_max, s);
-  if (max_nb <= 512) return launch_t<T, 1, 16, ELLW>(mv, V, Y, a, c_max, s);
-  if (max_nb <= 1024) return launch_t<T, 2, 16, ELLW>(mv, V, Y, a, c_max, s);
-  if (max_nb <= 2048) return launch_t<T, 4, 16, ELLW>(mv, V, Y, a, c_max, s);
-  if (max_nb <= 4096) return launch_t<T, 8, 16, ELLW>(mv, V, Y, a, c_max, s);
+  if (max_nb <= 512) return launch_t<T, 1, 16, ELLW, false>(mv, V, Y, a, c_max, s);
+  if (max_nb <= 1024) return launch_t<T, 2, 16, ELLW, false>(mv, V, Y, a, c_max, s);
+  if (max_nb <= 2048) return launch_t<T, 4, 16, ELLW, false>(mv, V, Y, a, c_max, s);
+  if (max_nb <= 4096) return launch_t<T, 8, 16, ELLW, false>(mv, V, Y, a, c_max, s);
   return BSP_ERR_INVALID_ARG;
 }
 
 template <typename T, int ELLW>
+int launch_rows_reg(const MeshView<T>& mv, const T* V, T* Y, const CgArgs& a, int max_nb,
+                    int c_max, cudaStream_t s) {
+  if (max_nb <= 256) return launch_t<T, 1, 8, ELLW, true>(mv, V, Y, a, c_max, s);
+  if (max_nb <= 512) return launch_t<T, 2, 8, ELLW, true>(mv, V, Y, a, c_max, s);
+  if (max_nb <= 1024) return launch_t<T, 4, 8, ELLW, true>(mv, V, Y, a, c_max, s);
+  return launch_t<T, 8, 8, ELLW, true>(mv, V, Y, a, c_max, s);
+}
+
+template <typename T, int ELLW>
 void configure_t() {
-  set_max_dynamic_smem(k_cgt<T, 1, 8, ELLW>);
-  set_max_dynamic_smem(k_cgt<T, 1, 16, ELLW>);
-  set_max_dynamic_smem(k_cgt<T, 2, 16, ELLW>);
-  set_max_dynamic_smem(k_cgt<T, 4, 16, ELLW>);
-  set_max_dynamic_smem(k_cgt<T, 8, 16, ELLW>);
+  set_max_dynamic_smem(k_cgt<T, 1, 16, ELLW, false>);
+  set_max_dynamic_smem(k_cgt<T, 2, 16, ELLW, false>);
+  set_max_dynamic_smem(k_cgt<T, 4, 16, ELLW, false>);
+  set_max_dynamic_smem(k_cgt<T, 8, 16, ELLW, false>);
 }
 
 }  // namespace
@@ -294,11 +345,17 @@ void configure_cgt_kernels() {
   configure_t<double, 16>();
 }
 
+// The register form applies (unweighted, degree <= 8, up to 2,048 rows).
+bool cgt_reg(int max_nb, int max_deg, bool weighted) {
+  return !weighted && max_deg > 0 && max_deg <= 8 && max_nb <= 2048;
+}
+
 // Whether the team kernel holds blocks of up to max_nb rows of degree <= max_deg.
 bool cgt_fits(int max_nb, int max_deg, int real_bytes, bool weighted) {
   if (max_deg <= 0 || max_deg > 16 || max_nb > 4096) return false;
+  if (cgt_reg(max_nb, max_deg, weighted)) return true;   // 8 KB per team vector at most
   const size_t tw = max_nb <= 512 ? 1 : max_nb <= 1024 ? 2 : max_nb <= 2048 ? 4 : 8;
-  const size_t r = max_nb <= 256 ? 8 : 16, cap = 32 * tw * r, nt = kWarpsCta / tw;
+  const size_t r = 16, cap = 32 * tw * r, nt = kWarpsCta / tw;
   const size_t ellw = max_deg <= 8 ? 8 : 16;
   const size_t bytes = cap * real_bytes + (weighted ? ellw * cap * real_bytes : 0) +
                        nt * (cap + 1) * real_bytes + ellw * cap * 2;
@@ -309,6 +366,9 @@ template <typename T>
 int launch_cgt(const MeshView<T>& mv, const T* V, T* Y, const CgArgs& a, int max_nb, int c_max,
                cudaStream_t s) {
   if (!(a.max_deg > 0 && a.max_deg <= 16)) return BSP_ERR_INVALID_ARG;
+  if (cgt_reg(max_nb, a.max_deg, mv.wt != nullptr))
+    return a.max_deg <= 6 ? launch_rows_reg<T, 6>(mv, V, Y, a, max_nb, c_max, s)
+                          : launch_rows_reg<T, 8>(mv, V, Y, a, max_nb, c_max, s);
   return a.max_deg <= 8 ? launch_rows<T, 8>(mv, V, Y, a, max_nb, c_max, s)
                         : launch_rows<T, 16>(mv, V, Y, a, max_nb, c_max, s);
 }

@@ -156,7 +156,14 @@ int launch_cg(const MeshView<T>& mv, const T* V, T* Y, const CgArgs& a, int cs, 
 // Batched one-column-per-CTA CG (bsp_cg.cu): the batch sorted by size bucket
 // (rows per thread 1, 4, 8, 16), bucket_off[0..4] (host) delimiting the
 // buckets and bucket_rows[q] the largest block of bucket q.
+constexpr int kCgBuckets = 5;  // size buckets: up to 256, 512, 1,024, 2,048, 4,096 rows
 int cg_bucket(int nb);   // -1 when the block is too large (> 4,096 rows)
+// Streams and events on which the buckets of one batched CG launch run side
+// by side (fork from the launching stream, join back into it).
+struct CgFork {
+  cudaStream_t aux[kCgBuckets - 1] = {};
+  cudaEvent_t fork = nullptr, join[kCgBuckets - 1] = {};
+};
 // Team CG (bsp_cgt.cu): one column per team of 1-8 warps, the pattern in
 // shared memory once per CTA; blocks up to 4,096 rows, degrees up to 16.
 bool cgt_fits(int max_nb, int max_deg, int real_bytes, bool weighted);
@@ -167,7 +174,8 @@ void configure_cgt_kernels();
 bool cg1_fits(int max_nb, int max_deg, int real_bytes, bool weighted);
 template <typename T>
 int launch_cg_buckets(const MeshView<T>& mv, const T* V, T* Y, const CgArgs& a,
-                      const int* bucket_off, const int* bucket_rows, int c_max, cudaStream_t s);
+                      const int* bucket_off, const int* bucket_rows, int c_max, cudaStream_t s,
+                      const CgFork* fork = nullptr);
 template <typename T>
 int cg_smem_bytes(int cs, int max_nb);
 void configure_cg_kernels();
@@ -392,8 +400,9 @@ struct bsp_mesh {
   std::vector<std::vector<int32_t>> waves;
   std::vector<int32_t> h_wave_list;      // all waves concatenated
   std::vector<int32_t> h_wave_off;       // [levels+1]
-  std::vector<std::array<int, 5>> wave_bucket;  // CG size-bucket offsets per wave
-  std::vector<std::array<int, 4>> wave_bucket_rows;  // largest block per bucket
+  std::vector<std::array<int, bsp::kCgBuckets + 1>> wave_bucket;  // CG size-bucket offsets per wave
+  std::vector<std::array<int, bsp::kCgBuckets>> wave_bucket_rows;  // largest block per bucket
+  bsp::CgFork cg_fork;   // side streams of the batched CG (created before the first capture)
   int64_t root_rows = 0;
   // device arrays
   int32_t *d_bptr = nullptr, *d_verts = nullptr, *d_rowptr = nullptr, *d_eoff = nullptr,
