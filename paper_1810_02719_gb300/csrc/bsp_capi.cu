@@ -211,6 +211,9 @@ void release(bsp_mesh* m) {
     if (m->cg_fork.join[q]) cudaEventDestroy(m->cg_fork.join[q]);
   }
   if (m->cg_fork.fork) cudaEventDestroy(m->cg_fork.fork);
+  if (m->post_stream) cudaStreamDestroy(m->post_stream);
+  for (cudaEvent_t e : m->post_ev)
+    if (e) cudaEventDestroy(e);
 }
 
 int stream_error_status(bsp_mesh* m, cudaStream_t s) {
@@ -406,6 +409,11 @@ int create_common(const double* xyz, int64_t n, const int32_t* tri, int64_t m, i
   M->stats.intra_edges = M->intra_edges;
   M->stats.max_block = M->max_nb;
   M->stats.levels = levels;
+  // side stream and events of the deferred work of the engine's ranges
+  if (cudaStreamCreateWithFlags(&M->post_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&M->post_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&M->post_ev[1], cudaEventDisableTiming) != cudaSuccess)
+    return bail(fail(BSP_ERR_CUDA, "stream creation failed"));
   // side streams of the batched CG (bucket launches run side by side)
   for (int q = 0; q < kCgBuckets - 1; ++q)
     if (cudaStreamCreateWithFlags(&M->cg_fork.aux[q], cudaStreamNonBlocking) != cudaSuccess ||
@@ -517,17 +525,20 @@ int ensure_rr_groups(bsp_mesh* M, int c) {
   return BSP_OK;
 }
 
-// The whole fixed-c schedule in one launch of the persistent cluster engine
-// (FP32).  BSP_ERR_INVALID_ARG: the engine's cluster shape cannot be resident
-// here (the caller falls back to the per-wave launches).
-int enqueue_engine(bsp_mesh* M, int c, int t_max, cudaStream_t s, int* launches) {
+// The fixed-c schedule for the blocks at positions [pos0, pos1) of the wave
+// order in one launch of the persistent cluster engine (FP32).  The ready
+// flags are cleared with the first range.  BSP_ERR_INVALID_ARG: the engine's
+// cluster shape cannot be resident here (the caller falls back to the
+// per-wave launches).
+int enqueue_engine(bsp_mesh* M, int c, int t_max, cudaStream_t s, int* launches, int pos0,
+                   int pos1) {
   int maxwave = 0;
   for (auto& w : M->waves) maxwave = std::max(maxwave, (int)w.size());
-  if (maxwave > 1 || M->opts.withhold_block >= 0)
+  if (pos0 == 0 && (maxwave > 1 || M->opts.withhold_block >= 0))
     CU(cudaMemsetAsync(M->d_ready, 0, sizeof(int) * (M->k + 2), s));
   OiClusterArgs oa;
-  oa.order = M->d_waves;
-  oa.nblocks = M->k;
+  oa.order = M->d_waves + pos0;
+  oa.nblocks = pos1 - pos0;
   oa.k = M->k;
   oa.parent = M->d_parent;
   oa.root_off = M->d_root_off;
@@ -550,6 +561,67 @@ int enqueue_engine(bsp_mesh* M, int c, int t_max, cudaStream_t s, int* launches)
   return rc;
 }
 
+// Engine launches over a chain (every block's parent is the block before it
+// in the wave order, or none) are split into consecutive ranges so that the
+// deferred work of a range (the second CholeskyQR pass and Rayleigh-Ritz) runs
+// on a side stream while the engine works through the next range: the engine
+// holds one cluster of SMs, the deferred kernels use the others.  A block's
+// basis is read by its child only, which (at a range boundary) loads it from
+// U at the start of the next launch; so the deferred work of range i stops
+// one block short of it and that block goes with range i + 1.  Ranges of 128
+// blocks, the last 128 in 64, 32, 16, 16 (a short tail after the engine).
+// Returns the range ends, or {k} when the schedule does not split.
+std::vector<int> engine_ranges(const bsp_mesh* M) {
+  const int k = M->k;
+  std::vector<int> ends;
+  bool chain = M->engine_ncl == 1 && k >= 256;
+  for (int q = 1; q < k && chain; ++q) {
+    const int b = M->h_wave_list[q], p = M->h_parent[b];
+    chain = p < 0 || p == M->h_wave_list[q - 1];
+  }
+  if (!chain || M->opts.withhold_block >= 0 || !M->post_stream) return {k};
+  const int tail[] = {64, 32, 16, 16};
+  int front = k;
+  for (int t : tail) front -= t;
+  for (int pos = 128; pos < front; pos += 128) ends.push_back(pos);
+  int pos = front;
+  for (int t : tail) {
+    ends.push_back(pos);
+    pos += t;
+  }
+  ends.push_back(k);
+  return ends;
+}
+
+// Deferred work for the blocks at positions [q0, q1) of the wave order: the
+// second CholeskyQR pass (engine schedule) and Rayleigh-Ritz, per block
+// group of ensure_rr_groups() intersected with the range.
+template <typename T, typename TA>
+int enqueue_deferred(bsp_mesh* M, int c, bool engine, int q0, int q1, cudaStream_t s,
+                     int* launches) {
+  int rc;
+  for (size_t g = 0; g + 1 < M->rr_group.size(); ++g) {
+    const int g0 = std::max(M->rr_group[g], q0), g1 = std::min(M->rr_group[g + 1], q1);
+    if (g0 >= g1) continue;
+    int wmax = 0;
+    for (int q = g0; q < g1; ++q) {
+      const int b = M->h_wave_list[q];
+      wmax = std::max(wmax, M->h_bptr[b + 1] - M->h_bptr[b]);
+    }
+    DenseArgs da{M->d_waves + g0, g1 - g0, M->d_bptr, M->d_cb, M->c_cap, c, wmax, M->d_status};
+    if (engine &&
+        (rc = launch_cholqr2<T, TA>(da, (T*)M->d_U, (T*)M->d_U, (TA*)M->d_Gp_rr, (T*)M->d_Rsm_rr,
+                                    s, launches, 1)))
+      return fail(rc, "launch failed (second CholeskyQR pass)");
+    if (!M->opts.rayleigh_ritz) continue;
+    da.sweeps = &M->d_cgstats->jacobi_sweeps;
+    rc = launch_rayleigh_ritz<T, TA>(da, view<T>(M), (T*)M->d_U, (TA*)M->d_Gp_rr, (T*)M->d_Rsm_rr,
+                                     (T*)M->d_theta_rr, s, launches);
+    if (rc) return fail(rc, "launch failed (Rayleigh-Ritz)");
+  }
+  return BSP_OK;
+}
+
 // Enqueue the fixed-c schedule on stream s; returns a status, counts launches.
 template <typename T, typename TA>
 int enqueue_fixed(bsp_mesh* M, int c, int t_max, cudaStream_t s, int* launches) {
@@ -562,7 +634,27 @@ int enqueue_fixed(bsp_mesh* M, int c, int t_max, cudaStream_t s, int* launches) 
   if constexpr (sizeof(T) == 4 && sizeof(TA) == 4) {
     if (M->opts.schedule == BSP_SCHED_AUTO && M->engine_c == c && M->engine_ncl > 0 &&
         oi_cluster_fits(c, t_max, M->max_nb, M->max_deg, M->min_nb)) {
-      if ((rc = enqueue_engine(M, c, t_max, s, launches)) != BSP_OK)
+      const std::vector<int> ends = engine_ranges(M);
+      if (ends.size() > 1) {
+        // engine ranges on s; each range's deferred work (one block short) on
+        // the side stream, serialised there (shared workspace), joined at the end
+        int pos = 0, done = 0;
+        for (size_t i = 0; i < ends.size(); ++i) {
+          if ((rc = enqueue_engine(M, c, t_max, s, launches, pos, ends[i])) != BSP_OK)
+            return fail(rc, "launch failed (cluster engine)");
+          pos = ends[i];
+          const int upto = i + 1 < ends.size() ? pos - 1 : pos;
+          CU(cudaEventRecord(M->post_ev[0], s));
+          CU(cudaStreamWaitEvent(M->post_stream, M->post_ev[0], 0));
+          if ((rc = enqueue_deferred<T, TA>(M, c, true, done, upto, M->post_stream, launches)))
+            return rc;
+          done = upto;
+        }
+        CU(cudaEventRecord(M->post_ev[1], M->post_stream));
+        CU(cudaStreamWaitEvent(s, M->post_ev[1], 0));
+        return BSP_OK;
+      }
+      if ((rc = enqueue_engine(M, c, t_max, s, launches, 0, M->k)) != BSP_OK)
         return fail(rc, "launch failed (cluster engine)");
       engine = true;
     }
@@ -640,21 +732,8 @@ int enqueue_fixed(bsp_mesh* M, int c, int t_max, cudaStream_t s, int* launches) 
   // the spans the chain depends on, and no later wave reads its rotation: it
   // also runs once after the last wave.  Both use the groups of
   // ensure_rr_groups().
-  if (engine || M->opts.rayleigh_ritz) {
-    for (size_t g = 0; g + 1 < M->rr_group.size(); ++g) {
-      const int g0 = M->rr_group[g], nbg = M->rr_group[g + 1] - g0;
-      DenseArgs da{M->d_waves + g0, nbg, M->d_bptr, M->d_cb, M->c_cap, c, M->rr_wmax[g],
-                   M->d_status};
-      if (engine &&
-          (rc = launch_cholqr2<T, TA>(da, U, U, (TA*)M->d_Gp_rr, (T*)M->d_Rsm_rr, s, launches, 1)))
-        return fail(rc, "launch failed (second CholeskyQR pass)");
-      if (!M->opts.rayleigh_ritz) continue;
-      da.sweeps = &M->d_cgstats->jacobi_sweeps;
-      rc = launch_rayleigh_ritz<T, TA>(da, view<T>(M), U, (TA*)M->d_Gp_rr, (T*)M->d_Rsm_rr,
-                                       (T*)M->d_theta_rr, s, launches);
-      if (rc) return fail(rc, "launch failed (Rayleigh-Ritz)");
-    }
-  }
+  if (engine || M->opts.rayleigh_ritz)
+    return enqueue_deferred<T, TA>(M, c, engine, 0, M->k, s, launches);
   return BSP_OK;
 }
 
@@ -737,7 +816,8 @@ int track_fixed(bsp_mesh* M, int c, int t_max, const void* V0, cudaStream_t s) {
         return rc;
       }
       if (ce2 != cudaSuccess) return fail(BSP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce2));
-      cudaError_t ie = cudaGraphInstantiate(&M->graph_exec, g, 0);
+      // node priorities as launched (the engine above its side-stream work)
+      cudaError_t ie = cudaGraphInstantiate(&M->graph_exec, g, cudaGraphInstantiateFlagUseNodePriority);
       cudaGraphDestroy(g);
       if (ie != cudaSuccess) return fail(BSP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
       M->graph_c = c;

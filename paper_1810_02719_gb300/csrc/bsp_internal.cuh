@@ -403,6 +403,8 @@ struct bsp_mesh {
   std::vector<std::array<int, bsp::kCgBuckets + 1>> wave_bucket;  // CG size-bucket offsets per wave
   std::vector<std::array<int, bsp::kCgBuckets>> wave_bucket_rows;  // largest block per bucket
   bsp::CgFork cg_fork;   // side streams of the batched CG (created before the first capture)
+  cudaStream_t post_stream = nullptr;   // deferred work of the engine's ranges
+  cudaEvent_t post_ev[2] = {nullptr, nullptr};
   int64_t root_rows = 0;
   // device arrays
   int32_t *d_bptr = nullptr, *d_verts = nullptr, *d_rowptr = nullptr, *d_eoff = nullptr,

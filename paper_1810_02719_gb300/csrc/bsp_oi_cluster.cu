@@ -889,11 +889,23 @@ int launch_t(const MeshView<float>& mv, const OiClusterArgs& a, int P, int ncl, 
   if (sm > 220 * 1024) return BSP_ERR_INVALID_ARG;
   auto kern = k_oi_cluster<MAXR, ELLW, W>;
   cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = P;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  // highest scheduling priority: work running beside the engine (the deferred
+  // kernels of the previous range) yields SMs to the engine's next cluster
+  static const int top_priority = [] {
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    return greatest;
+  }();
+  attr[1].id = cudaLaunchAttributePriority;
+  attr[1].val.priority = top_priority;
   cfg.blockDim = dim3(kNT, 1, 1);
   cfg.dynamicSmemBytes = sm;
   cfg.stream = s;
@@ -912,6 +924,7 @@ int launch_t(const MeshView<float>& mv, const OiClusterArgs& a, int P, int ncl, 
     return BSP_OK;
   }
   cfg.gridDim = dim3(P * ncl, 1, 1);
+  cfg.numAttrs = 2;
   prof_begin(KC_OI, s);
   const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, mv, a);
   prof_end(KC_OI, s);

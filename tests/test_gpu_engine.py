@@ -100,6 +100,38 @@ def test_engine_forest_several_clusters_row_transfer(z, c):
         bsp.bsp_mesh_destroy(h)
 
 
+def test_engine_ranges_with_deferred_work_on_a_side_stream():
+    """A chain of 256 blocks (256^2 torus, 16 x 16 tiles) takes the engine in
+    consecutive ranges, each range's second CholeskyQR pass and Rayleigh-Ritz
+    running beside the next range: same bases as the per-wave schedule and the
+    oracle, bit-identical between the captured graph, its replay and the eager
+    launches."""
+    xyz, faces, ptr, verts, parent, om = torus_chain(256, 16, seed=5)
+    assert len(ptr) - 1 == 256
+    c, t_max = 16, 2
+    starts = synth.gaussian_starts(ptr, parent, c, seed=6)
+    U_ref = O.oi_track(om, c, t_max, starts, delta=1e-2)
+    runs = {}
+    for name, kw in [("graph", dict(schedule=bsp.BSP_SCHED_AUTO)),
+                     ("eager", dict(schedule=bsp.BSP_SCHED_AUTO, use_graph=0)),
+                     ("waves", dict(schedule=bsp.BSP_SCHED_WAVES))]:
+        h = bsp.bsp_mesh_create(xyz, faces, ptr, verts, parent,
+                                bsp.make_opts(precision=bsp.BSP_PREC_F32, **kw))
+        try:
+            bsp.bsp_oi_track(h, c, t_max, starts.astype(np.float32))
+            runs[name] = bases(h, om)
+            if name == "graph":
+                bsp.bsp_oi_track(h, c, t_max, starts.astype(np.float32))
+                assert all(np.array_equal(a, b) for a, b in zip(runs[name], bases(h, om)))
+            assert bsp.bsp_get_stats(h)["not_converged"] == 0
+        finally:
+            bsp.bsp_mesh_destroy(h)
+    assert all(np.array_equal(a, b) for a, b in zip(runs["graph"], runs["eager"]))
+    for name in ("graph", "waves"):
+        s, p = worst(runs[name], U_ref, om, xyz)
+        assert s <= SINE_F32 and p <= PROJ_F32, (name, s, p)
+
+
 def test_engine_graph_replay_is_deterministic_and_projects():
     xyz, faces, ptr, verts, parent, om = torus_chain(64, 32, seed=1)
     h = bsp.bsp_mesh_create(xyz, faces, ptr, verts, parent,
