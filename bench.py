@@ -131,12 +131,14 @@ def source_sha(rel):
         return None
 
 
-def captured_traffic(kernel):
-    """DRAM bytes (read + write) per full-size launch of `kernel` from the ncu
-    capture recorded in profiles/dram_traffic.txt, or None when there is no
-    record or the kernel's source file has changed since the capture (the
-    record stores the file's hash).  Line format:
-    kernel source_file sha256_12 bytes_per_launch scale note..."""
+def captured_traffic(kernel, blocks_per_launch=None):
+    """DRAM bytes (read + write) per launch of `kernel` from the ncu capture
+    recorded in profiles/dram_traffic.txt, or None when there is no record or
+    the kernel's source file has changed since the capture (the record stores
+    the file's hash).  Line format:
+    kernel source_file sha256_12 bytes scale note...
+    scale is a number (bytes per full-size launch = bytes x scale) or
+    "per_block" (bytes per block, times blocks_per_launch)."""
     try:
         with open(os.path.join(ROOT, "profiles", "dram_traffic.txt")) as f:
             lines = [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
@@ -146,6 +148,8 @@ def captured_traffic(kernel):
         if len(f) >= 5 and f[0] == kernel:
             if source_sha(f[1]) != f[2]:
                 return None
+            if f[4] == "per_block":
+                return None if blocks_per_launch is None else float(f[3]) * blocks_per_launch
             return float(f[3]) * float(f[4])
     return None
 
@@ -307,8 +311,9 @@ def run_ours(args, rank, world, device):
         # the chain runs on one cluster: c/4 of the 152 SMs
         roof["sms_used"] = (c + 3) // 4
         roof["cg_flops"], roof["onorm_flops"] = cg_flops, onorm_flops
-    roof["traffic"] = captured_traffic({"oi": "k_oi_cluster", "chol": "k_cholqr2_cluster"}.get(
-        dom, dom))
+    roof["traffic"] = captured_traffic(
+        {"oi": "k_oi_cluster", "chol": "k_cholqr2_cluster"}.get(dom, dom),
+        blocks_per_launch=k / kernels[dom]["launches"])
 
     # standalone operator product (L + delta I) P over all blocks, c columns (HBM-bound)
     P = torch.randn(n, args.c, device=device)
@@ -399,6 +404,7 @@ def run_ours(args, rank, world, device):
     bsp.bsp_mesh_destroy(h)
     return {
         "value": value, "ms_per_step": 1e3 * total / args.steps, "launches": launches // args.steps,
+        "step_ms_min_max": [round(1e3 * min(times), 3), round(1e3 * max(times), 3)],
         "clocks": clk_summary,
         "e2e": {"value": e2e_value, "unit": "Mvertices/s",
                 "h2d_bytes_per_step": int(V0h.nbytes + Xh.nbytes),
@@ -1306,6 +1312,7 @@ def main():
             extras = run_extras(args, device)
     line = {"metric": METRIC, "value": res["value"], "unit": "Mvertices/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
+            "step_ms_min_max": res["step_ms_min_max"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "f32" else "f32+f64(gram-accumulation,cholesky)",
             "data": "synthetic", "config": config_dict(args), "clocks": res["clocks"],

@@ -19,6 +19,7 @@ namespace {
 constexpr int kT = 256;
 constexpr int kMaxChk = 128 / 8 + 1;   // prefix checkpoints for c_step >= 8
 constexpr int kMaxC = 128;
+constexpr int kRowsInFlight = 4;       // rows whose loads a warp issues together
 
 template <typename T>
 __global__ void k_init_starts(const int32_t* batch, const int32_t* bptr, const int32_t* parent,
@@ -81,7 +82,6 @@ __global__ void __launch_bounds__(kT) k_dyn_decide(const int32_t* batch, const i
                                                    TA* rho_out, int32_t* live) {
   __shared__ TA Ered[kT / 32][3 * 32];
   __shared__ T Es[kMaxC][3];
-  __shared__ TA red[kT / 32];
   __shared__ TA res[kMaxChk];
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   T* Xs = reinterpret_cast<T*>(dyn_smem);   // the block's coordinates, local order [nb x 3]
@@ -102,16 +102,28 @@ __global__ void __launch_bounds__(kT) k_dyn_decide(const int32_t* batch, const i
     TA e0 = 0, e1 = 0, e2 = 0;
     T f0 = 0, f1 = 0, f2 = 0;
     int cnt = 0;
-    for (int i = w; i < nb; i += kT / 32) {
-      const T u = j < c ? U[(size_t)(r0 + i) * ld + j] : T(0);
-      const T* x = Xs + i * 3;
-      f0 += u * x[0];
-      f1 += u * x[1];
-      f2 += u * x[2];
-      if (++cnt == 32) {  // FP32 partial sums over 32 rows, accumulated in TA
-        e0 += f0; e1 += f1; e2 += f2;
-        f0 = f1 = f2 = 0;
-        cnt = 0;
+    // rows w, w + 8, ... in order; four rows' loads in flight per iteration
+    for (int i0 = w; i0 < nb; i0 += kRowsInFlight * (kT / 32)) {
+      T u[kRowsInFlight];
+#pragma unroll
+      for (int m = 0; m < kRowsInFlight; ++m) {
+        const int i = i0 + m * (kT / 32);
+        u[m] = (i < nb && j < c) ? U[(size_t)(r0 + i) * ld + j] : T(0);
+      }
+#pragma unroll
+      for (int m = 0; m < kRowsInFlight; ++m) {
+        const int i = i0 + m * (kT / 32);
+        if (i < nb) {
+          const T* x = Xs + i * 3;
+          f0 += u[m] * x[0];
+          f1 += u[m] * x[1];
+          f2 += u[m] * x[2];
+          if (++cnt == 32) {  // FP32 partial sums over 32 rows, accumulated in TA
+            e0 += f0; e1 += f1; e2 += f2;
+            f0 = f1 = f2 = 0;
+            cnt = 0;
+          }
+        }
       }
     }
     e0 += f0; e1 += f1; e2 += f2;
@@ -158,10 +170,27 @@ __global__ void __launch_bounds__(kT) k_dyn_decide(const int32_t* batch, const i
     }
     gcol[(size_t)(r0 + i)] = (x0 - h0) + (x1 - h1) + (x2 - h2);
   }
-  const TA xnorm2 = block_reduce<T, TA>((TA)xx, red);
-  for (int q = 0; q < nchk; ++q) {
-    TA v = block_reduce<T, TA>((TA)accs[q][threadIdx.x], red);
-    if (threadIdx.x == 0) res[q] = v;
+  // ||X||^2 and every checkpoint residual, reduced together (per warp by the
+  // same butterfly as block_reduce, then over the warps in warp order); each
+  // checkpoint's ratio by its own thread
+  __shared__ TA wred[kT / 32][kMaxChk + 1];
+  __shared__ TA ratio[kMaxChk];
+  {
+    const TA v = warp_sum((TA)xx);
+    if (lane == 0) wred[w][kMaxChk] = v;
+    for (int q = 0; q < nchk; ++q) {
+      const TA u = warp_sum((TA)accs[q][threadIdx.x]);
+      if (lane == 0) wred[w][q] = u;
+    }
+  }
+  __syncthreads();
+  TA xnorm2 = 0;
+  for (int ww = 0; ww < kT / 32; ++ww) xnorm2 += wred[ww][kMaxChk];
+  if (threadIdx.x < nchk) {
+    TA sq = 0;
+    for (int ww = 0; ww < kT / 32; ++ww) sq += wred[ww][threadIdx.x];
+    res[threadIdx.x] = sq;
+    ratio[threadIdx.x] = xnorm2 > 0 ? sqrt(sq / xnorm2) : TA(0);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -173,11 +202,11 @@ __global__ void __launch_bounds__(kT) k_dyn_decide(const int32_t* batch, const i
         cj = fc < c ? fc : c;
         act = 0;
         const int q = cj / c_step - 1;
-        rho = (q >= 0 && xnorm2 > 0) ? sqrt(res[q] / xnorm2) : TA(0);
+        rho = q >= 0 ? ratio[q] : TA(0);
       }
     } else {
       for (int q = 0; q < nchk; ++q) {
-        TA r = xnorm2 > 0 ? sqrt(res[q] / xnorm2) : TA(0);
+        const TA r = ratio[q];
         if (r <= (TA)tol) {
           act = 0;
           cj = (q + 1) * c_step;
@@ -238,12 +267,20 @@ __global__ void __launch_bounds__(kT) k_dyn_grow(const int32_t* batch, const int
     T a[8];
 #pragma unroll
     for (int g = 0; g < 8; ++g) a[g] = 0;
-    for (int i = w; i < nb; i += kT / 32) {
-      const T* row = U + (size_t)(r0 + i) * ld;
-      const T u = j < c ? row[j] : T(0);
+    for (int i0 = w; i0 < nb; i0 += kRowsInFlight * (kT / 32)) {
+      T u[kRowsInFlight], gv[kRowsInFlight][8];
 #pragma unroll
-      for (int g = 0; g < 8; ++g)
-        if (g < c_step) a[g] += u * row[c + g];
+      for (int m = 0; m < kRowsInFlight; ++m) {
+        const int i = i0 + m * (kT / 32);
+        const T* row = U + (size_t)(r0 + (i < nb ? i : 0)) * ld;
+        u[m] = (i < nb && j < c) ? row[j] : T(0);
+#pragma unroll
+        for (int g = 0; g < 8; ++g) gv[m][g] = (i < nb && g < c_step) ? row[c + g] : T(0);
+      }
+#pragma unroll
+      for (int m = 0; m < kRowsInFlight; ++m)
+#pragma unroll
+        for (int g = 0; g < 8; ++g) a[g] += u[m] * gv[m][g];
     }
 #pragma unroll
     for (int g = 0; g < 8; ++g) part[w][lane * 8 + g] = a[g];
