@@ -148,6 +148,7 @@ void configure_once() {
   std::call_once(flag, [] {
     configure_cg_kernels();
     configure_cgt_kernels();
+    configure_tcqr_kernels();
     configure_dense_kernels();
     configure_adjoint_kernels();
     configure_tc_kernels();
@@ -609,10 +610,19 @@ int enqueue_deferred(bsp_mesh* M, int c, bool engine, int q0, int q1, cudaStream
       wmax = std::max(wmax, M->h_bptr[b + 1] - M->h_bptr[b]);
     }
     DenseArgs da{M->d_waves + g0, g1 - g0, M->d_bptr, M->d_cb, M->c_cap, c, wmax, M->d_status};
-    if (engine &&
-        (rc = launch_cholqr2<T, TA>(da, (T*)M->d_U, (T*)M->d_U, (TA*)M->d_Gp_rr, (T*)M->d_Rsm_rr,
-                                    s, launches, 1)))
-      return fail(rc, "launch failed (second CholeskyQR pass)");
+    if (engine) {
+      // the second pass on the tensor cores where it fits (FP32, c <= 64)
+      rc = BSP_ERR_INVALID_ARG;
+      if constexpr (sizeof(T) == 4 && sizeof(TA) == 4) {
+        if (tcqr_fits(c, 4))
+          rc = launch_cholqr_pass_tc<float>(da, (float*)M->d_U, (float*)M->d_U,
+                                            (float*)M->d_Gp_rr, (float*)M->d_Rsm_rr, s, launches);
+      }
+      if (rc == BSP_ERR_INVALID_ARG)
+        rc = launch_cholqr2<T, TA>(da, (T*)M->d_U, (T*)M->d_U, (TA*)M->d_Gp_rr, (T*)M->d_Rsm_rr,
+                                   s, launches, 1);
+      if (rc) return fail(rc, "launch failed (second CholeskyQR pass)");
+    }
     if (!M->opts.rayleigh_ritz) continue;
     da.sweeps = &M->d_cgstats->jacobi_sweeps;
     rc = launch_rayleigh_ritz<T, TA>(da, view<T>(M), (T*)M->d_U, (TA*)M->d_Gp_rr, (T*)M->d_Rsm_rr,
@@ -869,10 +879,12 @@ int ensure_dyn_state(bsp_mesh* M) {
 // over width classes for the start, then a WHILE node over rounds whose body
 // is a SWITCH over width classes (launches sized for the largest live width,
 // a multiple of c_step = kDynClass), the conditions set by those kernels.  Without it
-// (or while profiling) the host replays the same launches, reading the class
-// and the "another round" flag back after each control kernel.
+// (or while profiling, or when the forest has too many levels for one graph)
+// the host replays the same launches, reading the class and the "another
+// round" flag back after each control kernel.
 constexpr int kDynClass = 8;
 constexpr int kDynMaxRounds = 64;
+constexpr size_t kDynMaxBodies = 256;   // waves x width classes captured in one graph
 
 struct DynParams {
   int c_min, c_max, c_step, t_max;
@@ -1146,7 +1158,11 @@ int track_dynamic(bsp_mesh* M, const void* X, double tol, int c_min, int c_max, 
   CU(cudaMemsetAsync(M->d_dynctl, 0, sizeof(DynCtl), s));
   DynParams p{c_min, c_max, c_step, t_max, tol, seed, forced ? M->d_forced : nullptr};
   int launches = 0;
-  if (M->opts.use_graph && !M->profiling) {
+  // the graph holds one start and one round body per wave and width class: a
+  // forest of a few deep levels captures once and replays cheaply, a long
+  // chain of single-block waves would not (host-driven replay instead)
+  const bool graph_fits = M->waves.size() * (size_t)ncls <= kDynMaxBodies;
+  if (M->opts.use_graph && !M->profiling && graph_fits) {
     const std::vector<double> key = {(double)sizeof(T), (double)sizeof(TA), (double)c_min,
                                      (double)c_max, (double)c_step, (double)t_max, tol,
                                      (double)(seed >> 32), (double)(seed & 0xffffffffu),

@@ -537,6 +537,29 @@ int launch_cholqr2(const DenseArgs& a, const T* Y, T* Q, TA* Gp, T* Rsm, cudaStr
   return cudaGetLastError() == cudaSuccess ? BSP_OK : BSP_ERR_CUDA;
 }
 
+// Chunk Grams -> G (fixed order), then M = D R^-1 per block: the middle of one
+// CholeskyQR pass whose chunk products run elsewhere (bsp_tcqr.cu).
+template <typename T, typename TA>
+int launch_reduce_chol(const DenseArgs& a, int CH, int maxch, const TA* Gp, TA* G, T* Rsm,
+                       cudaStream_t s) {
+  const int cpad = pad4(a.cmax);
+  dim3 gr((cpad * cpad + kDT - 1) / kDT, a.nbatch);
+  prof_begin(KC_REDUCE, s);
+  k_reduce<TA><<<gr, kDT, 0, s>>>(a, CH, maxch, true, Gp, G);
+  prof_end(KC_REDUCE, s);
+  const int cpw = chol_cp(cpad);
+  const size_t sm = (size_t)(chol_a_elems<T, TA>(cpad, cpw) + 2 * cpad) * sizeof(TA) +
+                    (size_t)cpw * cpw * sizeof(T);
+  prof_begin(KC_CHOL, s);
+  k_chol<T, TA><<<a.nbatch, kDT, sm, s>>>(a, G, Rsm);
+  prof_end(KC_CHOL, s);
+  return cudaGetLastError() == cudaSuccess ? BSP_OK : BSP_ERR_CUDA;
+}
+template int launch_reduce_chol<float, float>(const DenseArgs&, int, int, const float*, float*,
+                                              float*, cudaStream_t);
+template int launch_reduce_chol<float, double>(const DenseArgs&, int, int, const double*, double*,
+                                               float*, cudaStream_t);
+
 template <typename T, typename TA>
 int launch_rayleigh_ritz(const DenseArgs& a, const MeshView<T>& mv, T* V, TA* Gp, T* Rsm,
                          T* theta, cudaStream_t s, int* launches) {

@@ -205,6 +205,16 @@ template <typename T, typename TA>
 int launch_cholqr2_fused(const DenseArgs& a, const T* Y, T* Q, TA* Gp, int maxch, cudaStream_t s,
                          int passes);
 void configure_fused_kernels();
+template <typename T, typename TA>
+int launch_reduce_chol(const DenseArgs& a, int CH, int maxch, const TA* Gp, TA* G, T* Rsm,
+                       cudaStream_t s);
+// One CholeskyQR pass with both contractions on the tensor cores (bsp_tcqr.cu;
+// FP32 operands, c <= 64); BSP_ERR_INVALID_ARG when the shape does not fit.
+bool tcqr_fits(int cmax, int real_bytes);
+template <typename TA>
+int launch_cholqr_pass_tc(const DenseArgs& a, const float* Y, float* Q, TA* Gp, float* Rsm,
+                          cudaStream_t s, int* launches);
+void configure_tcqr_kernels();
 void set_last_error(const char* msg);  // message for bsp_last_error() on this thread
 extern bool g_disable_fused;  // force the multi-kernel Onorm (A/B checks)
 

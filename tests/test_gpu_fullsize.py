@@ -23,6 +23,7 @@ from paper_1810_02719_gb300 import bsp  # noqa: E402
 from paper_1810_02719_gb300.filter import block_low_pass  # noqa: E402
 
 SINE_F32, PROJ_F32 = 1e-4, 1e-5
+PROJ_ROOT_F32 = 5e-5   # random-start root after t steps (derivation at its use)
 # FP32 orthonormality after CholeskyQR2 and the Rayleigh-Ritz rotation: the
 # loss grows like n u (u = 2^-24, n up to ~3,000 rows); observed ~1e-5
 ORTH_F32 = 1e-4
@@ -87,7 +88,13 @@ def test_chain_1m_torus_c64():
         finally:
             O.apply_S = orig
         rows0 = om.blocks[0].verts
-        tol0 = max(PROJ_F32, 10 * O.projector_rel_error(U0p, U_ref[0], xyz[rows0]))
+        # The root's span holds the constant null vector, which R = (L + delta I)^-1
+        # scales by 1 / delta: an FP32 CG solve knows the residual only to
+        # u ||A|| ||x||, so the basis along that direction is good to about
+        # u ||A|| / (lambda_1 + delta) ~ 3.6e-5 (||A|| <= 12, lambda_1 = 0): the
+        # root's projector gate is 5e-5, as for c = 1 in the engine tests.
+        # Warm-started blocks start at their Ritz vectors and keep PROJ_F32.
+        tol0 = max(PROJ_ROOT_F32, 10 * O.projector_rel_error(U0p, U_ref[0], xyz[rows0]))
         for b in range(k):
             U = bsp.bsp_get_basis(h, b, 1024).astype(np.float64)
             assert _orthonormality(U) <= ORTH_F32, b
