@@ -177,6 +177,36 @@ def make_opts(**kw) -> bsp_opts:
     return o
 
 
+# per handle: the mesh's real type and block sizes, so that the readers below
+# size their host buffers from the mesh itself (the library writes n_b rows of
+# the mesh's precision; a smaller or narrower buffer would be overrun)
+_MESHES = {}
+
+
+def _remember(h, opts, block_ptr):
+    prec = opts.precision if opts is not None else bsp_opts_default().precision
+    _MESHES[h] = (np.float64 if prec == BSP_PREC_F64 else np.float32,
+                  np.diff(np.asarray(block_ptr, dtype=np.int64)))
+
+
+def _mesh_real(mesh, real, what):
+    info = _MESHES.get(mesh)
+    if info is None:
+        if real is None:
+            raise ValueError(f"{what}: unknown mesh handle; pass real=")
+        return real
+    if real is not None and np.dtype(real) != np.dtype(info[0]):
+        raise ValueError(f"{what}: the mesh holds {np.dtype(info[0])}, not {np.dtype(real)}")
+    return info[0]
+
+
+def _check_rows(mesh, b, n_b, what):
+    info = _MESHES.get(mesh)
+    if info is not None and not (0 <= b < info[1].size and int(info[1][b]) == int(n_b)):
+        raise ValueError(f"{what}: block {b} has {int(info[1][b]) if 0 <= b < info[1].size else '?'} "
+                         f"rows, not {n_b}")
+
+
 def bsp_mesh_create(xyz, faces, block_ptr, block_verts, parent, opts=None, n=None):
     """Create a mesh from faces; returns an opaque handle (int)."""
     xyz = _f64(xyz)
@@ -188,6 +218,7 @@ def bsp_mesh_create(xyz, faces, block_ptr, block_verts, parent, opts=None, n=Non
     _check(_lib.bsp_mesh_create(_ptr(xyz), n, _ptr(faces), int(faces.shape[0]), _ptr(block_ptr),
                                 _ptr(block_verts), int(block_ptr.shape[0]) - 1, _ptr(parent),
                                 C.byref(opts) if opts is not None else None, C.byref(h)))
+    _remember(h.value, opts, block_ptr)
     return h.value
 
 
@@ -202,10 +233,12 @@ def bsp_mesh_create_edges(xyz, edges, block_ptr, block_verts, parent, opts=None,
                                       _ptr(block_ptr), _ptr(block_verts),
                                       int(block_ptr.shape[0]) - 1, _ptr(parent),
                                       C.byref(opts) if opts is not None else None, C.byref(h)))
+    _remember(h.value, opts, block_ptr)
     return h.value
 
 
 def bsp_mesh_destroy(mesh):
+    _MESHES.pop(mesh, None)
     _check(_lib.bsp_mesh_destroy(mesh))
 
 
@@ -223,7 +256,11 @@ def bsp_get_edges(mesh) -> np.ndarray:
     return out
 
 
-def bsp_get_block_csr(mesh, b, n_b, real=np.float32):
+def bsp_get_block_csr(mesh, b, n_b, real=None):
+    """Block b's CSR (row pointers, local columns, off-diagonal weights,
+    diagonal) in the mesh's precision (real: that dtype or None)."""
+    real = _mesh_real(mesh, real, "bsp_get_block_csr")
+    _check_rows(mesh, b, n_b, "bsp_get_block_csr")
     nnz = C.c_int64()
     _check(_lib.bsp_get_block_csr(mesh, b, None, None, None, None, C.byref(nnz)))
     rp = np.empty(n_b + 1, np.int32)
@@ -267,7 +304,10 @@ def bsp_get_block_c(mesh, k) -> np.ndarray:
     return out
 
 
-def bsp_get_basis(mesh, b, n_b, real=np.float32) -> np.ndarray:
+def bsp_get_basis(mesh, b, n_b, real=None) -> np.ndarray:
+    """Block b's basis [n_b x c_b] in the mesh's precision (real: that dtype or None)."""
+    real = _mesh_real(mesh, real, "bsp_get_basis")
+    _check_rows(mesh, b, n_b, "bsp_get_basis")
     c = C.c_int32()
     _check(_lib.bsp_get_basis(mesh, b, None, C.byref(c)))
     U = np.empty((n_b, c.value), real)

@@ -55,7 +55,8 @@ def _oracle_dynamic_with_sensitivity(mesh, X, starts, **kw):
 
 
 def test_chain_1m_torus_c64():
-    """1024^2 torus, 1,024 chained 32x32 blocks, c = 64, 2 OI steps, RR, FP32, CUDA graph."""
+    """1024^2 torus, 1,024 chained 32x32 blocks, c = 64, 2 OI steps, RR, FP32, CUDA graph:
+    every block against the oracle's FP64 chain."""
     N, T, c, t = 1024, 32, 64, 2
     xyz, faces = synth.torus(N, seed=0)
     ptr, verts = synth.tile_partition(N, T)
@@ -95,16 +96,21 @@ def test_chain_1m_torus_c64():
         # root's projector gate is 5e-5, as for c = 1 in the engine tests.
         # Warm-started blocks start at their Ritz vectors and keep PROJ_F32.
         tol0 = max(PROJ_ROOT_F32, 10 * O.projector_rel_error(U0p, U_ref[0], xyz[rows0]))
-        for b in range(k):
+        worst = [0.0, 0.0]
+        for b in range(k):   # every block of the chain against the oracle's FP64 chain
             U = bsp.bsp_get_basis(h, b, 1024).astype(np.float64)
             assert _orthonormality(U) <= ORTH_F32, b
-            if b in (0, 1, 2, 255, 511, 767, 1022, 1023):
-                rows = om.blocks[b].verts
-                tol = tol0 if b == 0 else PROJ_F32
-                assert O.max_sine(U, U_ref[b]) <= max(SINE_F32, 10 * tol), b
-                assert O.projector_rel_error(U, U_ref[b], xyz[rows]) <= tol, b
-                ref = U_ref[b] @ (U_ref[b].T @ xyz[rows])
-                assert np.linalg.norm(Xon[rows] - ref) / np.linalg.norm(ref) <= tol, b
+            rows = om.blocks[b].verts
+            tol = tol0 if b == 0 else PROJ_F32
+            sn = O.max_sine(U, U_ref[b])
+            pe = O.projector_rel_error(U, U_ref[b], xyz[rows])
+            assert sn <= max(SINE_F32, 10 * tol), (b, sn)
+            assert pe <= tol, (b, pe)
+            ref = U_ref[b] @ (U_ref[b].T @ xyz[rows])
+            assert np.linalg.norm(Xon[rows] - ref) / np.linalg.norm(ref) <= tol, b
+            if b > 0:
+                worst = [max(worst[0], sn), max(worst[1], pe)]
+        print("warm blocks: worst sine %.3g, worst projector error %.3g" % tuple(worst))
     finally:
         bsp.bsp_mesh_destroy(h)
 
@@ -204,7 +210,8 @@ def test_frames_512_torus_200_frames_tensor_cores():
             ref = U_ref[b] @ (U_ref[b].T @ X64[blk.verts])
             num += np.sum((Xon[blk.verts] - ref) ** 2)
             den += np.sum(ref ** 2)
-        assert np.sqrt(num / den) <= 2e-2
+        # three BF16 roundings (X, U, E: 2^-9 relative each): 3 x 2^-9 = 5.9e-3
+        assert np.sqrt(num / den) <= 6e-3, np.sqrt(num / den)
     finally:
         bsp.bsp_mesh_destroy(h)
 

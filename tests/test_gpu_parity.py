@@ -22,6 +22,7 @@ if not torch.cuda.is_available():
 from paper_1810_02719_gb300 import bsp  # noqa: E402
 
 SINE_F32, PROJ_F32 = 1e-4, 1e-5
+BF16_E2E = 6e-3   # three BF16 roundings of 2^-9 relative: first-order bound 3 x 2^-9
 SINE_F64, PROJ_F64 = 1e-8, 1e-10
 
 
@@ -535,12 +536,13 @@ def _check_tensor_core_paths(N, F, ptr, verts, parent, c, seed):
             assert np.abs(Eb - Eref).max() <= 1e-5 * np.abs(Eref).max()
             Xref = Uq @ _bf16_round(Eb)
             assert np.abs(Xon[blk.verts] - Xref).max() <= 1e-5 * np.abs(Xref).max()
-        # end to end against the FP64 oracle's filter output: BF16 operand rounding
-        # (2^-9 relative each for X, U and E) bounds the error at about 1e-2
+        # end to end against the FP64 oracle's filter output: three BF16 roundings
+        # (X, U and E, each at most 2^-9 relative) bound the error to first order
+        # by 3 x 2^-9 = 5.9e-3 (observed ~1.9e-3); the FP32 basis adds ~1e-5
         U_ref = O.oi_track(om, c, 2, starts.astype(np.float64), delta=1e-2)
         Xr = O.reconstruct(om, U_ref, O.project(om, U_ref, X), cols)
         err = np.linalg.norm(Xon - Xr) / np.linalg.norm(Xr)
-        assert err <= 2e-2, err
+        assert err <= BF16_E2E, err
     finally:
         bsp.bsp_mesh_destroy(h)
 
