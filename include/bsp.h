@@ -92,6 +92,12 @@ typedef struct bsp_opts {
                               BSP_ERR_TIMEOUT.  Default 2000. */
   int32_t withhold_block;  /* test hook: block b >= 0 waits for a parent flag that is never
                               set (the wait runs out: BSP_ERR_TIMEOUT).  Default -1 (none). */
+  int32_t cg_rows_per_lane; /* tile shape of the batched CG (one column per team of warps):
+                              8 = 8 rows per lane, each row's neighbour indices in registers
+                              (unweighted meshes of degree <= 8, blocks <= 2,048 rows; teams
+                              twice as wide), 16 = 16 rows per lane, the pattern in shared
+                              memory.  0 = automatic (8 where it applies).  bsp_autotune
+                              sets it. */
 } bsp_opts;
 
 /* Execution of the fixed-c schedule (bsp_oi_track, FP32 precision).
@@ -383,12 +389,17 @@ int bsp_get_kernel_times(const bsp_mesh* mesh, double* ms_out, int32_t* launches
  * Autotuner for the tile shape of the solves (no counterpart in the paper):
  * times fixed-c tracking of this mesh (bsp_oi_track with c, t_max and the
  * given root starts, reps timed runs after one warm-up, median) for each
- * candidate CG layout -- one column per CTA in size buckets (0) and column
- * slabs of 2, 4 and 8 columns per CTA -- and keeps the fastest in the mesh's
- * options for later tracking calls (fixed and dynamic c).
+ * candidate CG layout -- the batched team CG in size buckets (0), timed with
+ * 8 and with 16 rows per lane (cg_rows_per_lane; 16 only where the 8-row
+ * form does not apply), and column slabs of 2, 4 and 8 columns per CTA --
+ * and keeps the fastest (cols_per_cta and cg_rows_per_lane) in the mesh's
+ * options for later tracking calls (fixed and dynamic c).  With the FP32
+ * schedule on the persistent engine the layouts are not used (a chain's
+ * timings then differ only by noise).
  *   times_ms  host double [4] or NULL: median ms per candidate, in the order
- *             0, 2, 4, 8 (a candidate whose shared memory does not fit the
- *             mesh's largest block reports -1).
+ *             0, 2, 4, 8 (for 0 the faster of its rows-per-lane forms; a
+ *             candidate whose shared memory does not fit the mesh's largest
+ *             block reports -1).
  *   chosen    host int32 or NULL: the kept columns-per-CTA value.
  * The tracked bases afterwards are those of the last run.  Errors: as
  * bsp_oi_track.

@@ -38,7 +38,8 @@ class bsp_opts(C.Structure):
                 ("cg_rtol", C.c_double), ("cg_max_steps", C.c_int32),
                 ("rayleigh_ritz", C.c_int32), ("cols_per_cta", C.c_int32),
                 ("use_graph", C.c_int32), ("schedule", C.c_int32),
-                ("wait_limit_ms", C.c_int32), ("withhold_block", C.c_int32)]
+                ("wait_limit_ms", C.c_int32), ("withhold_block", C.c_int32),
+                ("cg_rows_per_lane", C.c_int32)]
 
 
 class bsp_stats(C.Structure):

@@ -708,6 +708,7 @@ int enqueue_fixed(bsp_mesh* M, int c, int t_max, cudaStream_t s, int* launches) 
     // nears 1/u).
     CgArgs ca{batch, nbw, M->d_cb, M->c_cap, 1, M->opts.delta, M->opts.cg_rtol,
               M->opts.cg_max_steps, M->d_status, M->d_cgstats, M->max_deg};
+    ca.rows_per_lane = M->opts.cg_rows_per_lane;
     const int cs = pick_cs(M, nbw, c, sizeof(T));
     const bool buckets = use_buckets(M, nbw, wmax);
     // Onorm placement.  Only the span matters between steps (span(S Q) =
@@ -810,7 +811,7 @@ int track_fixed(bsp_mesh* M, int c, int t_max, const void* V0, cudaStream_t s) {
   if ((rc = stage_onorm_lists(M)) != BSP_OK) return rc;
   if (M->opts.use_graph && !M->profiling) {
     if (!M->graph_exec || M->graph_c != c || M->graph_t != t_max ||
-        M->graph_cs != M->opts.cols_per_cta) {
+        M->graph_cs != M->opts.cols_per_cta || M->graph_rpl != M->opts.cg_rows_per_lane) {
       if (M->graph_exec) {
         cudaGraphExecDestroy(M->graph_exec);
         M->graph_exec = nullptr;
@@ -833,6 +834,7 @@ int track_fixed(bsp_mesh* M, int c, int t_max, const void* V0, cudaStream_t s) {
       M->graph_c = c;
       M->graph_t = t_max;
       M->graph_cs = M->opts.cols_per_cta;
+      M->graph_rpl = M->opts.cg_rows_per_lane;
       M->graph_launches = launches;
     }
     CU(cudaGraphLaunch(M->graph_exec, s));
@@ -933,6 +935,7 @@ int enqueue_dyn_round(bsp_mesh* M, int l, int cm, const DynParams& p, cudaStream
   da.live = M->d_live;
   CgArgs ca{wave, nw, M->d_cb, M->c_cap, 1, M->opts.delta, M->opts.cg_rtol, M->opts.cg_max_steps,
             M->d_status, M->d_cgstats, M->max_deg};
+  ca.rows_per_lane = M->opts.cg_rows_per_lane;
   ca.live = M->d_live;
   const int cs = pick_cs(M, nw, cm, sizeof(T));
   const bool buckets = use_buckets(M, nw, wmax);
@@ -1168,7 +1171,8 @@ int track_dynamic(bsp_mesh* M, const void* X, double tol, int c_min, int c_max, 
                                      (double)(seed >> 32), (double)(seed & 0xffffffffu),
                                      forced ? 1.0 : 0.0, (double)M->opts.z, M->opts.delta,
                                      M->opts.cg_rtol, (double)M->opts.cg_max_steps,
-                                     (double)M->opts.cols_per_cta, (double)M->c_cap};
+                                     (double)M->opts.cols_per_cta,
+                                     (double)M->opts.cg_rows_per_lane, (double)M->c_cap};
     if (M->dyn_exec && (realloc || key != M->dyn_key)) {
       cudaGraphExecDestroy(M->dyn_exec);
       M->dyn_exec = nullptr;
@@ -1290,6 +1294,7 @@ int track_doi(bsp_mesh* M, const void* X, int c0, double eps_l, double eps_h, in
       DenseArgs da{d_list, nbw, M->d_bptr, M->d_cb, c_cap, cm, wmax, M->d_status};
       CgArgs ca{d_list, nbw, M->d_cb, c_cap, 1, M->opts.delta, M->opts.cg_rtol,
                 M->opts.cg_max_steps, M->d_status, M->d_cgstats, M->max_deg};
+      ca.rows_per_lane = M->opts.cg_rows_per_lane;
       const int cs = pick_cs(M, nbw, cm, sizeof(T));
       // U = Onorm(R^z U): z solves, an Onorm after each (same span as R^z U)
       for (int q = 0; q < M->opts.z; ++q) {
@@ -1392,6 +1397,7 @@ int filter_forward(bsp_mesh* M, int c, int t_max, const void* V0, cudaStream_t s
     }
     CgArgs ca{batch, nbw, M->d_cb, c, M->opts.z, M->opts.delta, M->opts.cg_rtol,
               M->opts.cg_max_steps, M->d_status, M->d_cgstats, M->max_deg};
+    ca.rows_per_lane = M->opts.cg_rows_per_lane;
     const int cs = pick_cs(M, nbw, c, sizeof(T));
     for (int t = 1; t <= t_max; ++t) {
       if ((rc = launch_cg<T>(mv, ckV + (t - 1) * nc, ckY + (t - 1) * nc, ca, cs, wmax, c, s)))
@@ -1547,6 +1553,7 @@ void bsp_opts_default(bsp_opts* o) {
   o->schedule = BSP_SCHED_AUTO;
   o->wait_limit_ms = 2000;
   o->withhold_block = -1;
+  o->cg_rows_per_lane = 0;
 }
 
 const char* bsp_last_error(void) { return g_err.c_str(); }
@@ -1676,16 +1683,26 @@ int bsp_autotune(bsp_mesh* M, int32_t c, int32_t t_max, const void* V0, int32_t 
   if (!M) return fail(BSP_ERR_INVALID_ARG, "mesh is NULL");
   if (reps < 1) return fail(BSP_ERR_INVALID_ARG, "reps must be >= 1");
   cudaStream_t s = (cudaStream_t)stream;
-  const int cand[4] = {0, 2, 4, 8};
-  const int keep = M->opts.cols_per_cta;
+  // (columns per CTA, team CG rows per lane): the team CG in both tile shapes
+  // (the 8-row form only where it applies), then the column slabs
+  struct Cand { int cs, rpl, slot; };
+  std::vector<Cand> cands;
+  if (cgt_reg(std::min(M->max_nb, 2048), M->max_deg, M->d_wt != nullptr))
+    cands.push_back({0, 8, 0});   // buckets up to 2,048 rows take the register form
+  cands.push_back({0, 16, 0});
+  for (int q = 1; q < 4; ++q) cands.push_back({1 << q, 0, q});
+  const int keep_cs = M->opts.cols_per_cta, keep_rpl = M->opts.cg_rows_per_lane;
   double best = -1.0;
-  int best_cs = keep;
+  Cand best_c{keep_cs, keep_rpl, -1};
+  if (times_ms)
+    for (int q = 0; q < 4; ++q) times_ms[q] = -1.0;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
   int rc = BSP_OK;
-  for (int q = 0; q < 4; ++q) {
-    M->opts.cols_per_cta = cand[q];
+  for (const Cand& cd : cands) {
+    M->opts.cols_per_cta = cd.cs;
+    M->opts.cg_rows_per_lane = cd.rpl;
     double ms_med = -1.0;
     rc = bsp_oi_track(M, c, t_max, V0, stream);   // warm-up (captures the schedule)
     if (rc == BSP_OK) {
@@ -1704,20 +1721,22 @@ int bsp_autotune(bsp_mesh* M, int32_t c, int32_t t_max, const void* V0, int32_t 
         ms_med = ts[ts.size() / 2];
       }
     }
-    if (rc == BSP_ERR_INVALID_ARG && cand[q] != 0) {
+    if (rc == BSP_ERR_INVALID_ARG && cd.cs != 0) {
       rc = BSP_OK;   // this slab does not fit the mesh's blocks: not a candidate
       cudaGetLastError();
     }
     if (rc != BSP_OK) break;
-    if (times_ms) times_ms[q] = ms_med;
+    if (times_ms && ms_med >= 0 && (times_ms[cd.slot] < 0 || ms_med < times_ms[cd.slot]))
+      times_ms[cd.slot] = ms_med;
     if (ms_med >= 0 && (best < 0 || ms_med < best)) {
       best = ms_med;
-      best_cs = cand[q];
+      best_c = cd;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  M->opts.cols_per_cta = rc == BSP_OK ? best_cs : keep;
+  M->opts.cols_per_cta = rc == BSP_OK ? best_c.cs : keep_cs;
+  M->opts.cg_rows_per_lane = rc == BSP_OK ? best_c.rpl : keep_rpl;
   if (chosen) *chosen = M->opts.cols_per_cta;
   if (rc != BSP_OK) return rc;
   g_err.clear();

@@ -366,7 +366,7 @@ template <typename T>
 int launch_cgt(const MeshView<T>& mv, const T* V, T* Y, const CgArgs& a, int max_nb, int c_max,
                cudaStream_t s) {
   if (!(a.max_deg > 0 && a.max_deg <= 16)) return BSP_ERR_INVALID_ARG;
-  if (cgt_reg(max_nb, a.max_deg, mv.wt != nullptr))
+  if (a.rows_per_lane != 16 && cgt_reg(max_nb, a.max_deg, mv.wt != nullptr))
     return a.max_deg <= 6 ? launch_rows_reg<T, 6>(mv, V, Y, a, max_nb, c_max, s)
                           : launch_rows_reg<T, 8>(mv, V, Y, a, max_nb, c_max, s);
   return a.max_deg <= 8 ? launch_rows<T, 8>(mv, V, Y, a, max_nb, c_max, s)

@@ -148,6 +148,8 @@ struct CgArgs {
   // [k] per-block flags: a CTA whose block has live[b] == 0 returns at once
   // (the device-driven dynamic-c rounds); nullptr: every block of the batch
   const int32_t* live = nullptr;
+  // team CG tile shape: 8 or 16 rows per lane (0: 8 where the register form applies)
+  int rows_per_lane = 0;
 };
 extern bool g_disable_cg1;  // force the shared-memory CG kernel (A/B checks)
 template <typename T>
@@ -167,6 +169,7 @@ struct CgFork {
 // Team CG (bsp_cgt.cu): one column per team of 1-8 warps, the pattern in
 // shared memory once per CTA; blocks up to 4,096 rows, degrees up to 16.
 bool cgt_fits(int max_nb, int max_deg, int real_bytes, bool weighted);
+bool cgt_reg(int max_nb, int max_deg, bool weighted);   // the 8-rows-per-lane register form applies
 template <typename T>
 int launch_cgt(const MeshView<T>& mv, const T* V, T* Y, const CgArgs& a, int max_nb, int c_max,
                cudaStream_t s);
@@ -462,7 +465,7 @@ struct bsp_mesh {
   size_t cap_Gp_rr = 0, cap_Rsm_rr = 0, cap_theta_rr = 0;
   // graph cache for the fixed-c schedule
   cudaGraphExec_t graph_exec = nullptr;
-  int graph_c = -1, graph_t = -1, graph_launches = 0, graph_cs = -1;
+  int graph_c = -1, graph_t = -1, graph_launches = 0, graph_cs = -1, graph_rpl = -1;
   cudaStream_t graph_stream = nullptr;
   // dynamic-c schedule: device state and its graph (conditional nodes), keyed
   // by the call's parameters

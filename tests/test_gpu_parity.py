@@ -275,14 +275,16 @@ def _wide_wave_mesh(prec, **kw):
     return h, om, xyz, faces, ptr, verts, parent
 
 
+@pytest.mark.parametrize("rows_per_lane", [0, 16])
 @pytest.mark.parametrize("prec,z,real", [(bsp.BSP_PREC_MIXED, 2, np.float32),
                                          (bsp.BSP_PREC_F32, 1, np.float32),
                                          (bsp.BSP_PREC_F64, 1, np.float64)])
-def test_batched_cg_wide_wave(prec, z, real):
-    """Batched blocks of one wave (one-column-per-CTA CG per size bucket, the
-    pattern in registers up to 1,024 rows and in shared memory above): same
-    bases as the oracle."""
-    kw = dict(z=z)
+def test_batched_cg_wide_wave(prec, z, real, rows_per_lane):
+    """Batched blocks of one wave (the team CG per size bucket, teams of 1-4
+    warps): same bases as the oracle in both tile shapes, 8 rows per lane with
+    the neighbour indices in registers (automatic) and 16 rows per lane with
+    the pattern in shared memory."""
+    kw = dict(z=z, cg_rows_per_lane=rows_per_lane)
     if real == np.float64:
         kw["cg_rtol"] = 1e-13
     h, om, xyz, faces, ptr, verts, parent = _wide_wave_mesh(prec, **kw)
