@@ -476,9 +476,12 @@ BSP_DEV int col8(int j) { return 2 * j + (j >> 2); }
 BSP_DEV void factor8(const float* A, int K, float* w, int* fail) {
   float R[8][8], W[8][8];
 #pragma unroll
-  for (int q = 0; q < 8; ++q)
-#pragma unroll
-    for (int r = q; r < 8; ++r) R[q][r] = A[(K + q) * kLDA + K + r];
+  for (int q = 0; q < 8; ++q) {   // whole rows as float4 (only r >= q is used)
+    const float4 a0 = *reinterpret_cast<const float4*>(A + (K + q) * kLDA + K);
+    const float4 a1 = *reinterpret_cast<const float4*>(A + (K + q) * kLDA + K + 4);
+    R[q][0] = a0.x; R[q][1] = a0.y; R[q][2] = a0.z; R[q][3] = a0.w;
+    R[q][4] = a1.x; R[q][5] = a1.y; R[q][6] = a1.z; R[q][7] = a1.w;
+  }
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     float sq = R[q][q];
@@ -591,17 +594,21 @@ BSP_DEV void chol_inverse(const Dense& d, int cpad) {
       } else {
         PT[col8(j)] = lo;
         PT[col8(j) + 1] = hi;
+        // a column of the next diagonal block updates its own diagonal entry
+        // (the rest of that block is warp 0's below)
+        if (j >= K + 8 && j < K + 16) A[j * kLDA + j] -= dot4(lo, lo) + dot4(hi, hi);
       }
     }
     __syncthreads();
     if (kb + 1 == nt) break;
     const int K8 = K + 8;
     if (warp == 0) {
-      // next diagonal block: its 36 upper entries, then one lane factorises it
-      for (int e = lane; e < 36; e += 32) {
-        int q = 0, rem = e;
-        while (rem >= 8 - q) { rem -= 8 - q; ++q; }
-        const int r = q + rem;
+      // next diagonal block: its 28 strictly upper entries, one per lane
+      // (row q holds 7 - q of them), then one lane factorises it
+      if (lane < 28) {
+        const int e = lane;
+        const int q = (e >= 7) + (e >= 13) + (e >= 18) + (e >= 22) + (e >= 25) + (e >= 27);
+        const int r = q + 1 + e - (7 * q - (q * (q - 1)) / 2);
         A[(K8 + q) * kLDA + K8 + r] -= dot8(PT + col8(K8 + q), PT + col8(K8 + r));
       }
       __syncwarp();
