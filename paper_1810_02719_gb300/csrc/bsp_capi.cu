@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstdint>
 #include <cstring>
+#include <functional>
 #include <mutex>
 #include <new>
 #include <string>
@@ -204,6 +205,7 @@ void release(bsp_mesh* m) {
     if (p) cudaFree(p);
   if (m->graph_exec) cudaGraphExecDestroy(m->graph_exec);
   if (m->dyn_exec) cudaGraphExecDestroy(m->dyn_exec);
+  if (m->doi_exec) cudaGraphExecDestroy(m->doi_exec);
   if (m->graph_stream) cudaStreamDestroy(m->graph_stream);
   for (cudaStream_t q : m->dyn_stream)
     if (q) cudaStreamDestroy(q);
@@ -480,6 +482,10 @@ int ensure_workspace(bsp_mesh* M, int c_cap, int maxbatch) {
   if ((M->c_cap != c_cap || g_realloc) && M->dyn_exec) {
     cudaGraphExecDestroy(M->dyn_exec);
     M->dyn_exec = nullptr;
+  }
+  if ((M->c_cap != c_cap || g_realloc) && M->doi_exec) {
+    cudaGraphExecDestroy(M->doi_exec);
+    M->doi_exec = nullptr;
   }
   M->c_cap = c_cap;
   return BSP_OK;
@@ -991,14 +997,36 @@ int add_conditional(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphCondi
   return BSP_OK;
 }
 
-// The graph of the whole dynamic-c schedule (see above).  counts[l][0..ncls)
-// and [ncls..2 ncls): launches of the start and round bodies of wave l.
-template <typename T, typename TA>
-int build_dyn_graph(bsp_mesh* M, const DynParams& p, std::vector<unsigned>* counts,
-                    cudaGraphExec_t* exec) {
-  const int ncls = dyn_classes(p.c_max);
+// A device-driven wave schedule: per wave, an init kernel (widths, live
+// flags, the start's width class), the start at its width class, rounds while
+// a block is live, and optionally a final body for the blocks still live
+// after the last round.  Bodies are enqueued per width class q (launches
+// sized for widths <= the class width) by the callbacks; the control kernels
+// choose the class and whether another round runs.
+struct WaveSchedule {
+  int ncls = 0;         // width classes
+  int max_rounds = 0;   // bound of the round loop
+  bool has_final = false;
+  // init(l, counts of wave l, handle, set_handle, stream): launches the wave's init kernel
+  std::function<int(int, const unsigned*, int, cudaGraphConditionalHandle, cudaStream_t)> init;
+  // start / round / final (l, q, stream, launches)
+  std::function<int(int, int, cudaStream_t, int*)> start, round, final_;
+};
+
+// Launch-count table of a schedule: per wave, [start | round | final] x ncls.
+size_t wave_counts_size(const bsp_mesh* M, const WaveSchedule& w) {
+  return (M->waves.size() + 1) * 3 * (size_t)w.ncls;
+}
+
+// The whole schedule as one CUDA graph: per wave a SWITCH over width classes
+// for the start, a WHILE over rounds whose body is a SWITCH over width classes
+// (the class and the loop condition set on the device), and for a final body
+// one more class kernel and SWITCH.  counts: launches of every body.
+int build_wave_graph(bsp_mesh* M, const WaveSchedule& w, std::vector<unsigned>* counts,
+                     cudaGraphExec_t* exec) {
+  const int ncls = w.ncls;
   const int levels = (int)M->waves.size();
-  counts->assign((size_t)levels * 2 * ncls, 0u);
+  counts->assign(wave_counts_size(M, w), 0u);
   cudaStream_t s0 = M->graph_stream, s1 = M->dyn_stream[0], s2 = M->dyn_stream[1];
   const cudaStreamCaptureMode mode = cudaStreamCaptureModeRelaxed;
   cudaGraph_t g;
@@ -1016,61 +1044,62 @@ int build_dyn_graph(bsp_mesh* M, const DynParams& p, std::vector<unsigned>* coun
     cudaGetLastError();
     return rc;
   };
+  // capture the bodies of a SWITCH node, one per class, on stream cs
+  auto capture_bodies = [&](std::vector<cudaGraph_t>& bodies, cudaStream_t cs,
+                            const std::function<int(int, int, cudaStream_t, int*)>& fn, int l,
+                            unsigned* cnt) -> int {
+    for (int q = 0; q < ncls; ++q) {
+      int n = 0, rc;
+      if (cudaStreamBeginCaptureToGraph(cs, bodies[q], nullptr, nullptr, 0, mode) != cudaSuccess)
+        return fail(BSP_ERR_CUDA, "graph capture failed to start");
+      if ((rc = fn(l, q, cs, &n))) return rc;
+      cudaGraph_t t;
+      if (cudaStreamEndCapture(cs, &t) != cudaSuccess) return fail(BSP_ERR_CUDA, "graph capture");
+      cnt[q] = (unsigned)n;
+    }
+    return BSP_OK;
+  };
   if (cudaStreamBeginCaptureToGraph(s0, g, nullptr, nullptr, 0, mode) != cudaSuccess)
     return abort_capture(fail(BSP_ERR_CUDA, "graph capture failed to start"));
   int rc = BSP_OK;
   for (int l = 0; l < levels; ++l) {
     const int32_t* wave = M->d_waves + M->h_wave_off[l];
     const int nw = (int)M->waves[l].size();
-    unsigned* cnt = M->d_dyn_launches + (size_t)l * 2 * ncls;
-    unsigned* hcnt = counts->data() + (size_t)l * 2 * ncls;
-    cudaGraphConditionalHandle h_start, h_while, h_round;
+    const unsigned* dcnt = M->d_dyn_launches + (size_t)l * 3 * ncls;
+    unsigned* hcnt = counts->data() + (size_t)l * 3 * ncls;
+    cudaGraphConditionalHandle h_start, h_while, h_round, h_final;
     if (cudaGraphConditionalHandleCreate(&h_start, g, 0, 0) != cudaSuccess ||
-        cudaGraphConditionalHandleCreate(&h_while, g, 1, cudaGraphCondAssignDefault) != cudaSuccess)
+        cudaGraphConditionalHandleCreate(&h_while, g, 1, cudaGraphCondAssignDefault) != cudaSuccess ||
+        (w.has_final && cudaGraphConditionalHandleCreate(&h_final, g, 0, 0) != cudaSuccess))
       return abort_capture(fail(BSP_ERR_CUDA, "conditional handle"));
-    if ((rc = launch_dyn_wave_init(wave, nw, M->d_bptr, M->d_parent, M->d_cb, M->d_cpar, M->d_live,
-                                   M->d_round, p.c_min, p.c_max, p.c_step, kDynClass, ncls, cnt,
-                                   M->d_dynctl, 1, h_start, s0)))
-      return abort_capture(fail(rc, "launch failed"));
-    std::vector<cudaGraph_t> sb, wb, rb;
-    if ((rc = add_conditional(s0, h_start, cudaGraphCondTypeSwitch, ncls, &sb)))
+    if ((rc = w.init(l, dcnt, 1, h_start, s0))) return abort_capture(fail(rc, "launch failed"));
+    std::vector<cudaGraph_t> sb, wb, rb, fb;
+    if ((rc = add_conditional(s0, h_start, cudaGraphCondTypeSwitch, ncls, &sb)) ||
+        (rc = capture_bodies(sb, s1, w.start, l, hcnt)))
       return abort_capture(rc);
-    for (int q = 0; q < ncls; ++q) {
-      int n = 0;
-      if (cudaStreamBeginCaptureToGraph(s1, sb[q], nullptr, nullptr, 0, mode) != cudaSuccess)
-        return abort_capture(fail(BSP_ERR_CUDA, "graph capture failed to start"));
-      if ((rc = enqueue_dyn_start<T, TA>(M, l, dyn_class_width(q, p.c_max), p, s1, &n)))
-        return abort_capture(rc);
-      cudaGraph_t t;
-      if (cudaStreamEndCapture(s1, &t) != cudaSuccess)
-        return abort_capture(fail(BSP_ERR_CUDA, "graph capture"));
-      hcnt[q] = (unsigned)n;
-    }
     if ((rc = add_conditional(s0, h_while, cudaGraphCondTypeWhile, 1, &wb))) return abort_capture(rc);
     if (cudaGraphConditionalHandleCreate(&h_round, wb[0], 0, 0) != cudaSuccess ||
         cudaStreamBeginCaptureToGraph(s1, wb[0], nullptr, nullptr, 0, mode) != cudaSuccess)
       return abort_capture(fail(BSP_ERR_CUDA, "graph capture failed to start"));
-    if ((rc = launch_dyn_class(wave, nw, M->d_cb, M->d_live, kDynClass, ncls, cnt + ncls,
-                               M->d_dynctl, 1, h_round, s1)))
+    if ((rc = launch_dyn_class(wave, nw, M->d_cb, M->d_live, kDynClass, ncls, dcnt + ncls,
+                               M->d_dynctl, 1, h_round, s1, 2)))
       return abort_capture(fail(rc, "launch failed"));
-    if ((rc = add_conditional(s1, h_round, cudaGraphCondTypeSwitch, ncls, &rb)))
+    if ((rc = add_conditional(s1, h_round, cudaGraphCondTypeSwitch, ncls, &rb)) ||
+        (rc = capture_bodies(rb, s2, w.round, l, hcnt + ncls)))
       return abort_capture(rc);
-    for (int q = 0; q < ncls; ++q) {
-      int n = 0;
-      if (cudaStreamBeginCaptureToGraph(s2, rb[q], nullptr, nullptr, 0, mode) != cudaSuccess)
-        return abort_capture(fail(BSP_ERR_CUDA, "graph capture failed to start"));
-      if ((rc = enqueue_dyn_round<T, TA>(M, l, dyn_class_width(q, p.c_max), p, s2, &n)))
-        return abort_capture(rc);
-      cudaGraph_t t;
-      if (cudaStreamEndCapture(s2, &t) != cudaSuccess)
-        return abort_capture(fail(BSP_ERR_CUDA, "graph capture"));
-      hcnt[ncls + q] = (unsigned)n;
-    }
-    if ((rc = launch_dyn_next(wave, nw, M->d_live, kDynMaxRounds, M->d_dynctl, 1, h_while, s1)))
+    if ((rc = launch_dyn_next(wave, nw, M->d_live, w.max_rounds, M->d_dynctl, 1, h_while, s1)))
       return abort_capture(fail(rc, "launch failed"));
     cudaGraph_t t;
     if (cudaStreamEndCapture(s1, &t) != cudaSuccess)
       return abort_capture(fail(BSP_ERR_CUDA, "graph capture"));
+    if (w.has_final) {
+      if ((rc = launch_dyn_class(wave, nw, M->d_cb, M->d_live, kDynClass, ncls, dcnt + 2 * ncls,
+                                 M->d_dynctl, 1, h_final, s0, 1)))
+        return abort_capture(fail(rc, "launch failed"));
+      if ((rc = add_conditional(s0, h_final, cudaGraphCondTypeSwitch, ncls, &fb)) ||
+          (rc = capture_bodies(fb, s1, w.final_, l, hcnt + 2 * ncls)))
+        return abort_capture(rc);
+    }
   }
   cudaGraph_t t;
   if (cudaStreamEndCapture(s0, &t) != cudaSuccess)
@@ -1083,11 +1112,12 @@ int build_dyn_graph(bsp_mesh* M, const DynParams& p, std::vector<unsigned>* coun
 }
 
 // The same schedule launched from the host: control values read back after
-// each control kernel (one synchronisation per kernel; profiling mode).
-template <typename T, typename TA>
-int run_dyn_eager(bsp_mesh* M, const DynParams& p, cudaStream_t s, int* launches) {
-  const int ncls = dyn_classes(p.c_max);
-  const unsigned* zeros = M->d_dyn_launches + (size_t)M->waves.size() * 2 * ncls;
+// each control kernel (one synchronisation per kernel; profiling mode, or a
+// forest with too many levels for one graph).  The device's launch counter
+// counts only the control kernels here; *launches gets the bodies'.
+int run_wave_eager(bsp_mesh* M, const WaveSchedule& w, cudaStream_t s, int* launches) {
+  const int ncls = w.ncls;
+  const unsigned* zeros = M->d_dyn_launches + (size_t)M->waves.size() * 3 * ncls;
   DynCtl ctl;
   auto read_ctl = [&]() -> int {
     CU(cudaMemcpyAsync(&ctl, M->d_dynctl, sizeof(DynCtl), cudaMemcpyDeviceToHost, s));
@@ -1098,31 +1128,61 @@ int run_dyn_eager(bsp_mesh* M, const DynParams& p, cudaStream_t s, int* launches
   for (int l = 0; l < (int)M->waves.size(); ++l) {
     const int32_t* wave = M->d_waves + M->h_wave_off[l];
     const int nw = (int)M->waves[l].size();
-    if ((rc = launch_dyn_wave_init(wave, nw, M->d_bptr, M->d_parent, M->d_cb, M->d_cpar, M->d_live,
-                                   M->d_round, p.c_min, p.c_max, p.c_step, kDynClass, ncls, zeros,
-                                   M->d_dynctl, 0, 0, s)))
-      return fail(rc, "launch failed");
+    if ((rc = w.init(l, zeros, 0, 0, s))) return fail(rc, "launch failed");
     if ((rc = read_ctl())) return rc;
-    if (ctl.cls_start < ncls &&
-        (rc = enqueue_dyn_start<T, TA>(M, l, dyn_class_width(ctl.cls_start, p.c_max), p, s,
-                                       launches)))
-      return rc;
+    if (ctl.cls_start < ncls && (rc = w.start(l, ctl.cls_start, s, launches))) return rc;
     for (;;) {
       if ((rc = launch_dyn_class(wave, nw, M->d_cb, M->d_live, kDynClass, ncls, zeros,
-                                 M->d_dynctl, 0, 0, s)))
+                                 M->d_dynctl, 0, 0, s, 2)))
         return fail(rc, "launch failed");
       if ((rc = read_ctl())) return rc;
-      if (ctl.cls_round < ncls &&
-          (rc = enqueue_dyn_round<T, TA>(M, l, dyn_class_width(ctl.cls_round, p.c_max), p, s,
-                                         launches)))
-        return rc;
-      if ((rc = launch_dyn_next(wave, nw, M->d_live, kDynMaxRounds, M->d_dynctl, 0, 0, s)))
+      if (ctl.cls_round < ncls && (rc = w.round(l, ctl.cls_round, s, launches))) return rc;
+      if ((rc = launch_dyn_next(wave, nw, M->d_live, w.max_rounds, M->d_dynctl, 0, 0, s)))
         return fail(rc, "launch failed");
       if ((rc = read_ctl())) return rc;
       if (!ctl.more) break;
     }
+    if (w.has_final) {
+      if ((rc = launch_dyn_class(wave, nw, M->d_cb, M->d_live, kDynClass, ncls, zeros,
+                                 M->d_dynctl, 0, 0, s, 1)))
+        return fail(rc, "launch failed");
+      if ((rc = read_ctl())) return rc;
+      if (ctl.cls_round < ncls && (rc = w.final_(l, ctl.cls_round, s, launches))) return rc;
+    }
   }
   return BSP_OK;
+}
+
+// The schedule of one call: the cached graph (rebuilt when the key, a buffer
+// or the bodies' layout changed) or the host-driven replay.
+int run_wave_schedule(bsp_mesh* M, const WaveSchedule& w, const std::vector<double>& key,
+                      bool realloc, cudaGraphExec_t* exec, std::vector<double>* cached_key,
+                      cudaStream_t s, int* launches) {
+  const size_t ncounts = wave_counts_size(M, w);
+  const bool graph_fits = M->waves.size() * (size_t)w.ncls <= kDynMaxBodies;
+  if (M->opts.use_graph && !M->profiling && graph_fits) {
+    if (*exec && (realloc || key != *cached_key)) {
+      cudaGraphExecDestroy(*exec);
+      *exec = nullptr;
+    }
+    if (!*exec) {
+      if (!M->graph_stream) CU(cudaStreamCreateWithFlags(&M->graph_stream, cudaStreamNonBlocking));
+      for (auto& q : M->dyn_stream)
+        if (!q) CU(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
+      CU(cudaStreamSynchronize(s));
+      std::vector<unsigned> counts;
+      int rc;
+      if ((rc = build_wave_graph(M, w, &counts, exec)) != BSP_OK) return rc;
+      counts.resize(ncounts, 0u);   // the host-driven replay's zero counts at the end
+      CU(cudaMemcpy(M->d_dyn_launches, counts.data(), ncounts * sizeof(unsigned),
+                    cudaMemcpyHostToDevice));
+      *cached_key = key;
+    }
+    CU(cudaGraphLaunch(*exec, s));
+    return BSP_OK;
+  }
+  CU(cudaMemsetAsync(M->d_dyn_launches + (ncounts - 3 * w.ncls), 0, 3 * w.ncls * sizeof(unsigned), s));
+  return run_wave_eager(M, w, s, launches);
 }
 
 template <typename T, typename TA>
@@ -1144,12 +1204,27 @@ int track_dynamic(bsp_mesh* M, const void* X, double tol, int c_min, int c_max, 
   if ((rc = ensure(&M->d_starts, &M->cap_starts, (size_t)M->root_rows * c_min * sizeof(T))) != BSP_OK)
     return rc;
   if ((rc = ensure(&M->d_X, &M->cap_X, (size_t)M->n * 3 * sizeof(T))) != BSP_OK) return rc;
-  const int ncls = dyn_classes(c_max);
-  const size_t ncounts = (M->waves.size() + 1) * 2 * (size_t)ncls;
+  DynParams p{c_min, c_max, c_step, t_max, tol, seed, nullptr};
+  WaveSchedule w;
+  w.ncls = dyn_classes(c_max);
+  w.max_rounds = kDynMaxRounds;
+  w.init = [&](int l, const unsigned* cnt, int set, cudaGraphConditionalHandle h,
+                cudaStream_t q) -> int {
+    return launch_dyn_wave_init(M->d_waves + M->h_wave_off[l], (int)M->waves[l].size(), M->d_bptr,
+                                M->d_parent, M->d_cb, M->d_cpar, M->d_live, M->d_round, c_min,
+                                c_max, c_step, kDynClass, w.ncls, cnt, M->d_dynctl, set, h, q);
+  };
+  w.start = [&](int l, int q, cudaStream_t st, int* n) -> int {
+    return enqueue_dyn_start<T, TA>(M, l, dyn_class_width(q, c_max), p, st, n);
+  };
+  w.round = [&](int l, int q, cudaStream_t st, int* n) -> int {
+    return enqueue_dyn_round<T, TA>(M, l, dyn_class_width(q, c_max), p, st, n);
+  };
   if ((rc = ensure((void**)&M->d_dyn_launches, &M->cap_dyn_launches,
-                   ncounts * sizeof(unsigned))) != BSP_OK)
+                   wave_counts_size(M, w) * sizeof(unsigned))) != BSP_OK)
     return rc;
   if ((rc = ensure_dyn_state(M)) != BSP_OK) return rc;
+  p.forced = forced ? M->d_forced : nullptr;   // allocated by ensure_dyn_state on first use
   realloc = realloc || g_realloc;
   if ((rc = to_device(M->d_starts, V0, (size_t)M->root_rows * c_min * sizeof(T), s)) != BSP_OK)
     return rc;
@@ -1159,41 +1234,19 @@ int track_dynamic(bsp_mesh* M, const void* X, double tol, int c_min, int c_max, 
   CU(cudaMemsetAsync(M->d_status, 0, sizeof(int), s));
   CU(cudaMemsetAsync(M->d_cgstats, 0, sizeof(CgStats), s));
   CU(cudaMemsetAsync(M->d_dynctl, 0, sizeof(DynCtl), s));
-  DynParams p{c_min, c_max, c_step, t_max, tol, seed, forced ? M->d_forced : nullptr};
   int launches = 0;
   // the graph holds one start and one round body per wave and width class: a
   // forest of a few deep levels captures once and replays cheaply, a long
   // chain of single-block waves would not (host-driven replay instead)
-  const bool graph_fits = M->waves.size() * (size_t)ncls <= kDynMaxBodies;
-  if (M->opts.use_graph && !M->profiling && graph_fits) {
-    const std::vector<double> key = {(double)sizeof(T), (double)sizeof(TA), (double)c_min,
-                                     (double)c_max, (double)c_step, (double)t_max, tol,
-                                     (double)(seed >> 32), (double)(seed & 0xffffffffu),
-                                     forced ? 1.0 : 0.0, (double)M->opts.z, M->opts.delta,
-                                     M->opts.cg_rtol, (double)M->opts.cg_max_steps,
-                                     (double)M->opts.cols_per_cta,
-                                     (double)M->opts.cg_rows_per_lane, (double)M->c_cap};
-    if (M->dyn_exec && (realloc || key != M->dyn_key)) {
-      cudaGraphExecDestroy(M->dyn_exec);
-      M->dyn_exec = nullptr;
-    }
-    if (!M->dyn_exec) {
-      if (!M->graph_stream) CU(cudaStreamCreateWithFlags(&M->graph_stream, cudaStreamNonBlocking));
-      for (auto& q : M->dyn_stream)
-        if (!q) CU(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
-      CU(cudaStreamSynchronize(s));
-      std::vector<unsigned> counts;
-      if ((rc = build_dyn_graph<T, TA>(M, p, &counts, &M->dyn_exec)) != BSP_OK) return rc;
-      counts.resize(ncounts, 0u);   // the eager path's zero counts at the end
-      CU(cudaMemcpy(M->d_dyn_launches, counts.data(), ncounts * sizeof(unsigned),
-                    cudaMemcpyHostToDevice));
-      M->dyn_key = key;
-    }
-    CU(cudaGraphLaunch(M->dyn_exec, s));
-  } else {
-    CU(cudaMemsetAsync(M->d_dyn_launches + (ncounts - 2 * ncls), 0, 2 * ncls * sizeof(unsigned), s));
-    if ((rc = run_dyn_eager<T, TA>(M, p, s, &launches)) != BSP_OK) return rc;
-  }
+  const std::vector<double> key = {(double)sizeof(T), (double)sizeof(TA), (double)c_min,
+                                   (double)c_max, (double)c_step, (double)t_max, tol,
+                                   (double)(seed >> 32), (double)(seed & 0xffffffffu),
+                                   forced ? 1.0 : 0.0, (double)M->opts.z, M->opts.delta,
+                                   M->opts.cg_rtol, (double)M->opts.cg_max_steps,
+                                   (double)M->opts.cols_per_cta,
+                                   (double)M->opts.cg_rows_per_lane, (double)M->c_cap};
+  if ((rc = run_wave_schedule(M, w, key, realloc, &M->dyn_exec, &M->dyn_key, s, &launches)))
+    return rc;
   // the chosen widths and the launch count: one read-back at the end
   std::vector<int32_t>& hc = M->h_c;
   hc.assign(M->k, 0);
@@ -1227,8 +1280,12 @@ int track_dynamic(bsp_mesh* M, const void* X, double tol, int c_min, int c_max, 
 // iterations run, and a basis still carrying an appended column at the cap
 // is orthonormalised once more.  A root starts from its rows of V0 (c0
 // columns), a child from its parent's final basis and width.  The blocks of a
-// DAG level run as one batch; the host reads the stop flags after every
-// iteration and keeps the blocks still running.
+// DAG level run as one batch, device-driven like the step-8 dynamic c: a
+// live flag per block (cleared by the decision when the block stops), the
+// iteration number read on the device, the round loop and the width class
+// of each iteration decided by the control kernels; the whole call is one
+// CUDA graph (WHILE over iterations, SWITCH over width classes, a final
+// SWITCH for the blocks still running at the cap).
 template <typename T, typename TA>
 int track_doi(bsp_mesh* M, const void* X, int c0, double eps_l, double eps_h, int c_min,
               int c_max, int t_cap, const void* V0, int32_t* c_out, int32_t* iters_out,
@@ -1244,92 +1301,101 @@ int track_doi(bsp_mesh* M, const void* X, int c0, double eps_l, double eps_h, in
   for (auto& w : M->waves) maxbatch = std::max(maxbatch, (int)w.size());
   int rc;
   if ((rc = ensure_workspace<T, TA>(M, c_max, maxbatch)) != BSP_OK) return rc;
+  bool realloc = g_realloc;
   if ((rc = ensure(&M->d_starts, &M->cap_starts, (size_t)M->root_rows * c0 * sizeof(T))) != BSP_OK)
     return rc;
-  if ((rc = to_device(M->d_starts, V0, (size_t)M->root_rows * c0 * sizeof(T), s)) != BSP_OK)
-    return rc;
   if ((rc = ensure(&M->d_X, &M->cap_X, (size_t)M->n * 3 * sizeof(T))) != BSP_OK) return rc;
-  if ((rc = to_device(M->d_X, X, (size_t)M->n * 3 * sizeof(T), s)) != BSP_OK) return rc;
-  if ((rc = ensure_dyn_state(M)) != BSP_OK) return rc;
-  CU(cudaMemsetAsync(M->d_action, 0, sizeof(int32_t) * M->k, s));   // stop iteration per block
-  CU(cudaMemsetAsync(M->d_status, 0, sizeof(int), s));
-  CU(cudaMemsetAsync(M->d_cgstats, 0, sizeof(CgStats), s));
   const MeshView<T> mv = view<T>(M);
   T* U = (T*)M->d_U;
   T* Y = (T*)M->d_Y;
-  const int c_cap = M->c_cap;
+  WaveSchedule w;
+  w.ncls = dyn_classes(c_max);
+  w.max_rounds = t_cap;
+  w.has_final = true;
+  auto wave_rows_of = [&](int l) { return wave_rows(M, l); };
+  // wave start: root c0, child min(parent width, c_max, n_b) (c_step 1)
+  w.init = [&](int l, const unsigned* cnt, int set, cudaGraphConditionalHandle h,
+                cudaStream_t q) -> int {
+    return launch_dyn_wave_init(M->d_waves + M->h_wave_off[l], (int)M->waves[l].size(), M->d_bptr,
+                                M->d_parent, M->d_cb, M->d_cpar, M->d_live, M->d_round, c0, c_max,
+                                1, kDynClass, w.ncls, cnt, M->d_dynctl, set, h, q);
+  };
+  w.start = [&](int l, int q, cudaStream_t st, int* n) -> int {
+    const int32_t* wave = M->d_waves + M->h_wave_off[l];
+    launch_init_starts<T>(wave, (int)M->waves[l].size(), M->d_bptr, M->d_parent, M->d_root_off,
+                          M->d_cb, M->d_cpar, (const T*)M->d_starts, c0, U, M->c_cap,
+                          wave_rows_of(l), dyn_class_width(q, c_max), st);
+    ++*n;
+    return BSP_OK;
+  };
+  // one iteration: U = Onorm(R^z U) (z solves, an Onorm after each), then the
+  // decision (grow by e/||e||, drop the last column, or stop)
+  w.round = [&](int l, int q, cudaStream_t st, int* n) -> int {
+    const int32_t* wave = M->d_waves + M->h_wave_off[l];
+    const int nw = (int)M->waves[l].size(), wmax = wave_rows_of(l);
+    const int cm = dyn_class_width(q, c_max);
+    int rc2;
+    DenseArgs da{wave, nw, M->d_bptr, M->d_cb, M->c_cap, cm, wmax, M->d_status};
+    da.live = M->d_live;
+    CgArgs ca{wave, nw, M->d_cb, M->c_cap, 1, M->opts.delta, M->opts.cg_rtol,
+              M->opts.cg_max_steps, M->d_status, M->d_cgstats, M->max_deg};
+    ca.rows_per_lane = M->opts.cg_rows_per_lane;
+    ca.live = M->d_live;
+    const int cs = pick_cs(M, nw, cm, sizeof(T));
+    for (int zz = 0; zz < M->opts.z; ++zz) {
+      if ((rc2 = launch_cg<T>(mv, U, Y, ca, cs, wmax, cm, st)))
+        return fail(rc2, "CG launch failed (block too large for shared memory?)");
+      ++*n;
+      if ((rc2 = launch_cholqr2<T, TA>(da, Y, U, (TA*)M->d_Gp, (T*)M->d_Rsm, st, n)))
+        return fail(rc2, "launch failed (Onorm)");
+    }
+    if ((rc2 = launch_doi_decide<T>(wave, nw, M->d_bptr, M->d_verts, (const T*)M->d_X, U,
+                                    M->c_cap, M->d_cb, M->d_action, 0, eps_l, eps_h, c_min, c_max,
+                                    (T*)M->d_gcol, (double*)M->d_rho, st, M->d_live, M->d_dynctl)))
+      return fail(rc2, "launch failed (decision)");
+    ++*n;
+    return BSP_OK;
+  };
+  // blocks still running at the iteration cap: one more Onorm
+  w.final_ = [&](int l, int q, cudaStream_t st, int* n) -> int {
+    const int32_t* wave = M->d_waves + M->h_wave_off[l];
+    DenseArgs da{wave, (int)M->waves[l].size(), M->d_bptr, M->d_cb, M->c_cap,
+                 dyn_class_width(q, c_max), wave_rows_of(l), M->d_status};
+    da.live = M->d_live;
+    const int rc2 = launch_cholqr2<T, TA>(da, U, U, (TA*)M->d_Gp, (T*)M->d_Rsm, st, n);
+    return rc2 ? fail(rc2, "launch failed (Onorm)") : BSP_OK;
+  };
+  if ((rc = ensure((void**)&M->d_dyn_launches, &M->cap_dyn_launches,
+                   wave_counts_size(M, w) * sizeof(unsigned))) != BSP_OK)
+    return rc;
+  if ((rc = ensure_dyn_state(M)) != BSP_OK) return rc;
+  realloc = realloc || g_realloc;
+  if ((rc = to_device(M->d_starts, V0, (size_t)M->root_rows * c0 * sizeof(T), s)) != BSP_OK)
+    return rc;
+  if ((rc = to_device(M->d_X, X, (size_t)M->n * 3 * sizeof(T), s)) != BSP_OK) return rc;
+  CU(cudaMemsetAsync(M->d_action, 0, sizeof(int32_t) * M->k, s));   // stop iteration per block
+  CU(cudaMemsetAsync(M->d_status, 0, sizeof(int), s));
+  CU(cudaMemsetAsync(M->d_cgstats, 0, sizeof(CgStats), s));
+  CU(cudaMemsetAsync(M->d_dynctl, 0, sizeof(DynCtl), s));
+  int launches = 0;
+  const std::vector<double> key = {(double)sizeof(T), (double)sizeof(TA), (double)c0, eps_l, eps_h,
+                                   (double)c_min, (double)c_max, (double)t_cap, (double)M->opts.z,
+                                   M->opts.delta, M->opts.cg_rtol, (double)M->opts.cg_max_steps,
+                                   (double)M->opts.cols_per_cta,
+                                   (double)M->opts.cg_rows_per_lane, (double)M->c_cap};
+  if ((rc = run_wave_schedule(M, w, key, realloc, &M->doi_exec, &M->doi_key, s, &launches)))
+    return rc;
+  // widths, stop iterations and the launch count: one read-back at the end
   std::vector<int32_t>& hc = M->h_c;
   hc.assign(M->k, 0);
-  std::vector<int32_t> cpar(M->k, 0), done(M->k, 0), its(M->k, 0);
-  int32_t* d_list = M->d_waves + 2 * M->k;   // scratch list area (last third)
-  int launches = 0;
-  for (size_t l = 0; l < M->waves.size(); ++l) {
-    std::vector<int32_t> active = M->waves[l];
-    for (int b : active) {
-      const int p = M->h_parent[b];
-      const int nb = M->h_bptr[b + 1] - M->h_bptr[b];
-      hc[b] = p < 0 ? c0 : std::min(hc[p], std::min(c_max, nb));
-      cpar[b] = p < 0 ? 0 : hc[p];
-    }
-    CU(cudaMemcpyAsync(M->d_cb, hc.data(), sizeof(int32_t) * M->k, cudaMemcpyHostToDevice, s));
-    CU(cudaMemcpyAsync(M->d_cpar, cpar.data(), sizeof(int32_t) * M->k, cudaMemcpyHostToDevice, s));
-    auto stats = [&](int* wmax, int* cm) {
-      *wmax = 0;
-      *cm = 0;
-      for (int b : active) {
-        *wmax = std::max(*wmax, M->h_bptr[b + 1] - M->h_bptr[b]);
-        *cm = std::max(*cm, hc[b]);
-      }
-    };
-    int wmax, cm;
-    stats(&wmax, &cm);
-    CU(cudaMemcpyAsync(d_list, active.data(), sizeof(int32_t) * active.size(),
-                       cudaMemcpyHostToDevice, s));
-    launch_init_starts<T>(d_list, (int)active.size(), M->d_bptr, M->d_parent, M->d_root_off,
-                          M->d_cb, M->d_cpar, (const T*)M->d_starts, c0, U, c_cap, wmax, cm, s);
-    ++launches;
-    for (int t = 1; t <= t_cap && !active.empty(); ++t) {
-      stats(&wmax, &cm);
-      const int nbw = (int)active.size();
-      DenseArgs da{d_list, nbw, M->d_bptr, M->d_cb, c_cap, cm, wmax, M->d_status};
-      CgArgs ca{d_list, nbw, M->d_cb, c_cap, 1, M->opts.delta, M->opts.cg_rtol,
-                M->opts.cg_max_steps, M->d_status, M->d_cgstats, M->max_deg};
-      ca.rows_per_lane = M->opts.cg_rows_per_lane;
-      const int cs = pick_cs(M, nbw, cm, sizeof(T));
-      // U = Onorm(R^z U): z solves, an Onorm after each (same span as R^z U)
-      for (int q = 0; q < M->opts.z; ++q) {
-        if ((rc = launch_cg<T>(mv, U, Y, ca, cs, wmax, cm, s)))
-          return fail(rc, "CG launch failed (block too large for shared memory?)");
-        ++launches;
-        if ((rc = launch_cholqr2<T, TA>(da, Y, U, (TA*)M->d_Gp, (T*)M->d_Rsm, s, &launches)))
-          return fail(rc, "launch failed (Onorm)");
-      }
-      if ((rc = launch_doi_decide<T>(d_list, nbw, M->d_bptr, M->d_verts, (const T*)M->d_X, U,
-                                     c_cap, M->d_cb, M->d_action, t, eps_l, eps_h, c_min, c_max,
-                                     (T*)M->d_gcol, (double*)M->d_rho, s)))
-        return fail(rc, "launch failed (decision)");
-      ++launches;
-      CU(cudaMemcpyAsync(done.data(), M->d_action, sizeof(int32_t) * M->k, cudaMemcpyDeviceToHost, s));
-      CU(cudaMemcpyAsync(hc.data(), M->d_cb, sizeof(int32_t) * M->k, cudaMemcpyDeviceToHost, s));
-      CU(cudaStreamSynchronize(s));
-      std::vector<int32_t> next;
-      for (int b : active) {
-        if (done[b]) its[b] = done[b];
-        else next.push_back(b);
-      }
-      active.swap(next);
-      if (!active.empty())
-        CU(cudaMemcpyAsync(d_list, active.data(), sizeof(int32_t) * active.size(),
-                           cudaMemcpyHostToDevice, s));
-    }
-    if (!active.empty()) {   // blocks at the iteration cap: one more Onorm
-      stats(&wmax, &cm);
-      DenseArgs da{d_list, (int)active.size(), M->d_bptr, M->d_cb, c_cap, cm, wmax, M->d_status};
-      if ((rc = launch_cholqr2<T, TA>(da, U, U, (TA*)M->d_Gp, (T*)M->d_Rsm, s, &launches)))
-        return fail(rc, "launch failed (Onorm)");
-      for (int b : active) its[b] = t_cap;
-    }
-  }
+  std::vector<int32_t> its(M->k, 0);
+  DynCtl ctl;
+  CU(cudaMemcpyAsync(hc.data(), M->d_cb, sizeof(int32_t) * M->k, cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(its.data(), M->d_action, sizeof(int32_t) * M->k, cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(&ctl, M->d_dynctl, sizeof(DynCtl), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  for (auto& t : its)
+    if (t == 0) t = t_cap;   // still running at the cap
   std::vector<int32_t> ce(M->k + 1, 0);
   for (int b = 0; b < M->k; ++b) ce[b + 1] = ce[b] + hc[b];
   CU(cudaMemcpyAsync(M->d_ceoff, ce.data(), sizeof(int32_t) * (M->k + 1), cudaMemcpyHostToDevice, s));
@@ -1337,7 +1403,7 @@ int track_doi(bsp_mesh* M, const void* X, int c0, double eps_l, double eps_h, in
     return rc;
   if (iters_out && (rc = to_host_or_device(iters_out, its.data(), sizeof(int32_t) * M->k, s)) != BSP_OK)
     return rc;
-  M->stats.gpu_launches = launches;
+  M->stats.gpu_launches = (int)(ctl.launches + (unsigned long long)launches);
   M->tracked = true;
   M->ubf_valid = false;
   return stream_error_status(M, s);

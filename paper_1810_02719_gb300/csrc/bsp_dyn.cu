@@ -365,8 +365,8 @@ __global__ void __launch_bounds__(kCT) k_dyn_wave_init(
 
 __global__ void __launch_bounds__(kCT) k_dyn_class(const int32_t* wave, int nw, const int32_t* cb,
                                                    const int32_t* live, int cls_width, int ncls,
-                                                   const unsigned* round_launches, DynCtl* ctl,
-                                                   int set_handle,
+                                                   const unsigned* round_launches, unsigned base,
+                                                   DynCtl* ctl, int set_handle,
                                                    cudaGraphConditionalHandle h_round) {
   __shared__ int red[kCT / 32];
   int mx = 0;
@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(kCT) k_dyn_class(const int32_t* wave, int nw, 
   if (threadIdx.x == 0) {
     const int q = width_class(mx, cls_width, ncls);
     ctl->cls_round = q;
-    ctl->launches += 2 + (q < ncls ? round_launches[q] : 0u);
+    ctl->launches += base + (q < ncls ? round_launches[q] : 0u);
     if (set_handle) cudaGraphSetConditional(h_round, (unsigned)q);
   }
 }
@@ -412,13 +412,18 @@ template <typename T>
 __global__ void __launch_bounds__(kT) k_doi_decide(const int32_t* batch, const int32_t* bptr,
                                                    const int32_t* verts, const T* __restrict__ X,
                                                    T* U, int ld, int32_t* cb, int32_t* done,
-                                                   int t, double eps_l, double eps_h, int c_min,
-                                                   int c_max, T* gcol, double* enorm) {
+                                                   int t_arg, double eps_l, double eps_h, int c_min,
+                                                   int c_max, T* gcol, double* enorm,
+                                                   int32_t* live, const DynCtl* ctl) {
   __shared__ double Ered[kT / 32][3 * 32];
   __shared__ T Es[kMaxC][3];
   __shared__ double red[kT / 32];
   __shared__ int s_act;
   const int b = batch[blockIdx.x];
+  if (live && !live[b]) return;
+  // the iteration number: the argument, or (device-driven rounds) the rounds
+  // already run in this wave plus one
+  const int t = ctl ? ctl->rounds + 1 : t_arg;
   const int c = cb[b];
   const int r0 = bptr[b], nb = bptr[b + 1] - r0;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -478,6 +483,7 @@ __global__ void __launch_bounds__(kT) k_doi_decide(const int32_t* batch, const i
     if (act == 1) cb[b] = c + 1;
     else if (act == 2) cb[b] = c - 1;
     else done[b] = t;
+    if (live && act == 0) live[b] = 0;
     enorm[b] = ne;
     s_act = act;
   }
@@ -550,8 +556,9 @@ int launch_dyn_wave_init(const int32_t* wave, int nw, const int32_t* bptr, const
 
 int launch_dyn_class(const int32_t* wave, int nw, const int32_t* cb, const int32_t* live,
                      int cls_width, int ncls, const unsigned* round_launches, DynCtl* ctl,
-                     int set_handle, cudaGraphConditionalHandle h_round, cudaStream_t s) {
-  k_dyn_class<<<1, kCT, 0, s>>>(wave, nw, cb, live, cls_width, ncls, round_launches, ctl,
+                     int set_handle, cudaGraphConditionalHandle h_round, cudaStream_t s,
+                     unsigned base) {
+  k_dyn_class<<<1, kCT, 0, s>>>(wave, nw, cb, live, cls_width, ncls, round_launches, base, ctl,
                                 set_handle, h_round);
   return cudaGetLastError() == cudaSuccess ? BSP_OK : BSP_ERR_CUDA;
 }
@@ -565,20 +572,23 @@ int launch_dyn_next(const int32_t* wave, int nw, const int32_t* live, int max_ro
 template <typename T>
 int launch_doi_decide(const int32_t* batch, int nbatch, const int32_t* bptr, const int32_t* verts,
                       const T* X, T* U, int ld, int32_t* cb, int32_t* done, int t, double eps_l,
-                      double eps_h, int c_min, int c_max, T* gcol, double* enorm, cudaStream_t s) {
+                      double eps_h, int c_min, int c_max, T* gcol, double* enorm, cudaStream_t s,
+                      int32_t* live, const DynCtl* ctl) {
   if (c_max > kMaxC) return BSP_ERR_INVALID_ARG;
   prof_begin(KC_DYN, s);
   k_doi_decide<T><<<nbatch, kT, 0, s>>>(batch, bptr, verts, X, U, ld, cb, done, t, eps_l, eps_h,
-                                        c_min, c_max, gcol, enorm);
+                                        c_min, c_max, gcol, enorm, live, ctl);
   prof_end(KC_DYN, s);
   return cudaGetLastError() == cudaSuccess ? BSP_OK : BSP_ERR_CUDA;
 }
 template int launch_doi_decide<float>(const int32_t*, int, const int32_t*, const int32_t*,
                                       const float*, float*, int, int32_t*, int32_t*, int, double,
-                                      double, int, int, float*, double*, cudaStream_t);
+                                      double, int, int, float*, double*, cudaStream_t, int32_t*,
+                                      const DynCtl*);
 template int launch_doi_decide<double>(const int32_t*, int, const int32_t*, const int32_t*,
                                        const double*, double*, int, int32_t*, int32_t*, int,
-                                       double, double, int, int, double*, double*, cudaStream_t);
+                                       double, double, int, int, double*, double*, cudaStream_t,
+                                       int32_t*, const DynCtl*);
 
 template void launch_init_starts<float>(const int32_t*, int, const int32_t*, const int32_t*,
                                         const int32_t*, const int32_t*, const int32_t*,

@@ -352,11 +352,12 @@ int launch_dyn_wave_init(const int32_t* wave, int nw, const int32_t* bptr, const
                          const unsigned* start_launches, DynCtl* ctl, int set_handle,
                          cudaGraphConditionalHandle h_start, cudaStream_t s);
 // Round class: the largest width among live blocks -> ctl->cls_round and the
-// SWITCH handle; ctl->launches += round_launches[class] + 2 (this kernel and
-// the round's end).
+// SWITCH handle; ctl->launches += round_launches[class] + base (base: this
+// kernel and the round's end, 2; a final class with no end kernel, 1).
 int launch_dyn_class(const int32_t* wave, int nw, const int32_t* cb, const int32_t* live,
                      int cls_width, int ncls, const unsigned* round_launches, DynCtl* ctl,
-                     int set_handle, cudaGraphConditionalHandle h_round, cudaStream_t s);
+                     int set_handle, cudaGraphConditionalHandle h_round, cudaStream_t s,
+                     unsigned base = 2);
 // Round end: ctl->more = any live block and fewer than max_rounds rounds run;
 // sets the WHILE handle.
 int launch_dyn_next(const int32_t* wave, int nw, const int32_t* live, int max_rounds, DynCtl* ctl,
@@ -375,10 +376,14 @@ int launch_ov_merge(int64_t n_orig, int cols, const int32_t* off, const int32_t*
 
 // The paper's dynamic OI (Sec. 5, Algorithm 2): per block of the batch, the
 // summed residual e and the grow / shrink / stop decision (bsp_dyn.cu).
+// live (optional): blocks with live[b] == 0 are skipped and a stopping block
+// clears its flag; ctl (optional): the iteration number is ctl->rounds + 1
+// instead of t (device-driven rounds).
 template <typename T>
 int launch_doi_decide(const int32_t* batch, int nbatch, const int32_t* bptr, const int32_t* verts,
                       const T* X, T* U, int ld, int32_t* cb, int32_t* done, int t, double eps_l,
-                      double eps_h, int c_min, int c_max, T* gcol, double* enorm, cudaStream_t s);
+                      double eps_h, int c_min, int c_max, T* gcol, double* enorm, cudaStream_t s,
+                      int32_t* live = nullptr, const struct DynCtl* ctl = nullptr);
 
 // Adjoint of the low-pass filter (bsp_adjoint.cu)
 struct AdjointArgs {
@@ -475,6 +480,8 @@ struct bsp_mesh {
   size_t cap_dyn_launches = 0;
   cudaGraphExec_t dyn_exec = nullptr;
   std::vector<double> dyn_key;
+  cudaGraphExec_t doi_exec = nullptr;   // the paper's dynamic OI, same machinery
+  std::vector<double> doi_key;
   cudaStream_t dyn_stream[2] = {nullptr, nullptr};
   bsp_stats stats{};
   // low-pass filter checkpoints (last bsp_filter_forward)

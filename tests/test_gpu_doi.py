@@ -90,3 +90,31 @@ def test_paper_doi_rejects_bad_arguments():
             assert ei.value.code == bsp.BSP_ERR_INVALID_ARG
     finally:
         bsp.bsp_mesh_destroy(h)
+
+
+@pytest.mark.parametrize("prec,real", [(bsp.BSP_PREC_MIXED, np.float32),
+                                       (bsp.BSP_PREC_F64, np.float64)])
+def test_paper_doi_graph_and_host_driven_agree(prec, real):
+    """The iterations are decided on the device; the captured graph (WHILE over
+    iterations, SWITCH over width classes) and the host-driven replay of the
+    same launches give the same widths, iterations and bases bit for bit, and
+    a second call replays the cached graph."""
+    xyz, faces, ptr, verts, parent, om, starts = case()
+    out = []
+    for use_graph, reps in ((1, 2), (0, 1)):
+        h = bsp.bsp_mesh_create(xyz, faces, ptr, verts, parent,
+                                bsp.make_opts(precision=prec, use_graph=use_graph,
+                                              cg_rtol=1e-12 if real == np.float64 else 1e-6))
+        try:
+            for _ in range(reps):
+                c, its = bsp.bsp_oi_track_paper_doi(h, xyz.astype(real), C0, EPS_L, EPS_H, CMIN,
+                                                    CMAX, TCAP, starts.astype(real))
+                U = [bsp.bsp_get_basis(h, b, blk.verts.size) for b, blk in enumerate(om.blocks)]
+                out.append((c.copy(), its.copy(), U, bsp.bsp_get_stats(h)["gpu_launches"]))
+        finally:
+            bsp.bsp_mesh_destroy(h)
+    (c1, i1, U1, n1), (c2, i2, U2, n2), (c3, i3, U3, n3) = out
+    for c, its, U, n in ((c2, i2, U2, n2), (c3, i3, U3, n3)):
+        assert np.array_equal(c, c1) and np.array_equal(its, i1)
+        assert all(np.array_equal(a, b) for a, b in zip(U, U1))
+        assert n == n1 > 0
