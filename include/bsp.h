@@ -85,7 +85,11 @@ typedef struct bsp_opts {
   int32_t cg_max_steps;    /* CG step cap per solve. Default 2000. */
   int32_t rayleigh_ritz;   /* 1: Rayleigh-Ritz after the OI steps of each block (ascending order). Default 1. */
   int32_t cols_per_cta;    /* CG column-slab width (1, 2, 4 or 8); 0 = automatic. */
-  int32_t use_graph;       /* 1: capture the fixed-c tracking schedule in a CUDA graph. Default 1. */
+  int32_t use_graph;       /* 1: run the tracking schedules (fixed c, dynamic c, the paper's
+                              dynamic OI) as CUDA graphs, captured on the first call and
+                              replayed while the parameters stay the same; the dynamic
+                              schedules decide their rounds on the device (conditional
+                              nodes).  0: the same launches from the host.  Default 1. */
   int32_t schedule;        /* bsp_schedule: how the fixed-c schedule runs.  Default BSP_SCHED_AUTO. */
   int32_t wait_limit_ms;   /* bound of a device-side wait for a block computed by another
                               cluster of the persistent engine; on expiry the call returns
@@ -198,7 +202,10 @@ int bsp_set_edge_weights(bsp_mesh* mesh, const void* w, int64_t E);
  *   t_max    >= 0 OI steps per block.
  *   V0_roots host or device real [sum over roots of n_b, c]: the roots' start
  *            matrices concatenated in block order; any full-rank matrices.
- * Results stay on the device (bsp_get_basis, bsp_project).
+ * Results stay on the device (bsp_get_basis, bsp_project).  On a chain the
+ * FP32 schedule runs the persistent engine over consecutive ranges of blocks
+ * with each range's second CholeskyQR pass and Rayleigh-Ritz beside the next
+ * range; the call returns once every block is done.
  * Errors: BSP_ERR_INVALID_ARG, BSP_ERR_NUMERICAL, BSP_ERR_NOT_CONVERGED, BSP_ERR_CUDA.
  */
 int bsp_oi_track(bsp_mesh* mesh, int32_t c, int32_t t_max, const void* V0_roots, void* stream);
@@ -225,6 +232,8 @@ int bsp_oi_track(bsp_mesh* mesh, int32_t c, int32_t t_max, const void* V0_roots,
  *   V0_roots  host or device real [sum over roots of n_b, c0].
  *   c_out     host or device int32 [k] or NULL: final widths c_b.
  *   iters_out host or device int32 [k] or NULL: iterations run per block.
+ * The iterations are decided on the device (no read-back between them); the
+ * widths and iteration counts are read back once at the end.
  * Errors: BSP_ERR_INVALID_ARG, BSP_ERR_NUMERICAL, BSP_ERR_NOT_CONVERGED, BSP_ERR_CUDA.
  */
 int bsp_oi_track_paper_doi(bsp_mesh* mesh, const void* X, int32_t c0, double eps_l, double eps_h,
@@ -244,7 +253,9 @@ int bsp_oi_track_paper_doi(bsp_mesh* mesh, const void* X, int32_t c0, double eps
  *   forced_c host or device int32 [k] or NULL: when forced_c[b] >= 0 it replaces
  *            the decision of block b (replay hook).
  *   c_out    host or device int32 [k] or NULL: chosen c_b.
- * Requires c_min, c_max multiples of c_step, c_max <= 128.
+ * Requires c_min, c_max multiples of c_step, c_max <= 128.  The rounds are
+ * decided on the device (no read-back between them); the widths are read
+ * back once at the end.
  */
 int bsp_oi_track_dynamic(bsp_mesh* mesh, const void* X, double rel_tol, int32_t c_min,
                          int32_t c_max, int32_t c_step, int32_t t_max, uint64_t seed,
