@@ -2081,9 +2081,9 @@ int bsp_spmm(bsp_mesh* M, const void* P, void* Y, int32_t c, void* stream) {
   if (!M->d_spmm_chunks) {
     // chunk table, once per mesh: rows on the host, neighbour ranges on the device
     std::vector<int32_t> ch = spmm_chunk_rows(M->h_bptr);
-    const int nch = (int)(ch.size() / 4);
+    const int nch = (int)(ch.size() / 8);
     void* d = nullptr;
-    if (cudaMalloc(&d, sizeof(int32_t) * (ch.empty() ? 4 : ch.size())) != cudaSuccess) {
+    if (cudaMalloc(&d, sizeof(int32_t) * (ch.empty() ? 8 : ch.size())) != cudaSuccess) {
       cudaGetLastError();
       return fail(BSP_ERR_OOM, "device allocation failed");
     }
@@ -2091,11 +2091,9 @@ int bsp_spmm(bsp_mesh* M, const void* P, void* Y, int32_t c, void* stream) {
     launch_spmm_ranges(view<float>(M), M->d_blk_row, (int32_t*)d, nch, 0);
     CU(cudaMemcpy(ch.data(), d, sizeof(int32_t) * ch.size(), cudaMemcpyDeviceToHost));
     int span = 0, mnnz = 0;
-    std::vector<int32_t> rp(M->n + 1);
-    CU(cudaMemcpy(rp.data(), M->d_rowptr, sizeof(int32_t) * (M->n + 1), cudaMemcpyDeviceToHost));
     for (int q = 0; q < nch; ++q) {
-      span = std::max(span, ch[4 * q + 3] - ch[4 * q + 2] + 1);
-      mnnz = std::max(mnnz, rp[ch[4 * q] + ch[4 * q + 1]] - rp[ch[4 * q]]);
+      span = std::max(span, ch[8 * q + 3] - ch[8 * q + 2] + 1);
+      mnnz = std::max(mnnz, ch[8 * q + 5]);
     }
     M->d_spmm_chunks = (int32_t*)d;
     M->spmm_nchunks = nch;
@@ -2105,16 +2103,14 @@ int bsp_spmm(bsp_mesh* M, const void* P, void* Y, int32_t c, void* stream) {
   ProfScope ps(M);
   int rc;
   if (M->real_bytes == 8) {
-    rc = launch_spmm_tiled<double>(view<double>(M), M->d_blk_row, M->d_spmm_chunks, M->spmm_nchunks,
-                                   M->spmm_max_span, M->spmm_max_nnz, M->opts.delta, (const double*)P, (double*)Y,
-                                   c, s);
+    rc = launch_spmm_tiled<double>(view<double>(M), M->d_spmm_chunks, M->spmm_nchunks, M->spmm_max_span,
+                                   M->spmm_max_nnz, M->opts.delta, (const double*)P, (double*)Y, c, s);
     if (rc == BSP_ERR_INVALID_ARG)
       launch_spmm<double>(M->n, view<double>(M), M->d_blk_row, M->opts.delta, (const double*)P,
                           (double*)Y, c, s);
   } else {
-    rc = launch_spmm_tiled<float>(view<float>(M), M->d_blk_row, M->d_spmm_chunks, M->spmm_nchunks,
-                                  M->spmm_max_span, M->spmm_max_nnz, (float)M->opts.delta, (const float*)P,
-                                  (float*)Y, c, s);
+    rc = launch_spmm_tiled<float>(view<float>(M), M->d_spmm_chunks, M->spmm_nchunks, M->spmm_max_span,
+                                  M->spmm_max_nnz, (float)M->opts.delta, (const float*)P, (float*)Y, c, s);
     if (rc == BSP_ERR_INVALID_ARG)
       launch_spmm<float>(M->n, view<float>(M), M->d_blk_row, (float)M->opts.delta, (const float*)P,
                          (float*)Y, c, s);

@@ -269,17 +269,17 @@ int launch_recon_tc(const ProjArgs& a, const void* Ub, const float* E, int64_t e
                     float* X, int* status, cudaStream_t s);
 void configure_tc_kernels();
 
-// Tiled operator product (bsp_spmm.cu): chunks of up to 128 rows inside a
-// block, each with the row range [lo, hi] that its neighbours reach.
+// Tiled operator product (bsp_spmm.cu): chunks of up to 64 rows inside a
+// block, each with the row range [lo, hi] that its neighbours reach (8 int32
+// per chunk in the table).
 void configure_spmm_kernels();
 void configure_dyn_kernels();
 std::vector<int32_t> spmm_chunk_rows(const std::vector<int32_t>& bptr);
 void launch_spmm_ranges(const MeshView<float>& mv_any, const int32_t* blk_row, int32_t* chunks,
                         int nchunks, cudaStream_t s);
 template <typename T>
-int launch_spmm_tiled(const MeshView<T>& mv, const int32_t* blk_row, const int32_t* chunks,
-                      int nchunks, int max_span, int max_nnz, T delta, const T* P, T* Y, int c,
-                      cudaStream_t s);
+int launch_spmm_tiled(const MeshView<T>& mv, const int32_t* chunks, int nchunks, int max_span,
+                      int max_nnz, T delta, const T* P, T* Y, int c, cudaStream_t s);
 
 // Coefficient quantiser and NMSVE (bsp_codec.cu).  ceoff: [k + 1] row offsets
 // of the blocks' coefficients; range: [k x cols x 2] (lo, hi).
@@ -457,7 +457,7 @@ struct bsp_mesh {
   int* d_ready = nullptr;              // cluster engine: ready flags + abort word
   size_t cap_ready = 0;
   int engine_c = -1, engine_ncl = 0;   // engine prepared for width c: clusters (0: not usable)
-  int32_t* d_spmm_chunks = nullptr;   // tiled operator product: 4 int32 per chunk
+  int32_t* d_spmm_chunks = nullptr;   // tiled operator product: 8 int32 per chunk
   int spmm_nchunks = 0, spmm_max_span = 0, spmm_max_nnz = 0;
   void* d_Ebf = nullptr;   // BF16 copy of the coefficients of a reconstruction call
   size_t cap_Ebf = 0;

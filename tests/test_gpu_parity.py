@@ -176,6 +176,53 @@ def test_spmm_uneven_blocks_and_weights(mode, c):
         bsp.bsp_mesh_destroy(h)
 
 
+@pytest.mark.parametrize("kind,prec,c,mode", [
+    ("tiles", bsp.BSP_PREC_MIXED, 64, bsp.BSP_W_COMBINATORIAL),
+    ("tiles", bsp.BSP_PREC_MIXED, 48, bsp.BSP_W_INV_SQ_DIST),
+    ("tiles", bsp.BSP_PREC_F64, 44, bsp.BSP_W_COMBINATORIAL),
+    ("tiles", bsp.BSP_PREC_F64, 128, bsp.BSP_W_COMBINATORIAL),
+    ("bfs", bsp.BSP_PREC_MIXED, 32, bsp.BSP_W_INV_SQ_DIST),
+])
+def test_spmm_chunk_table_many_blocks(kind, prec, c, mode):
+    """The operator product reads every chunk's first edge, edge count and
+    column shift from the chunk table: 1,024-1,064 chunks of the 256^2 torus
+    (regular tiles, or uneven BFS blocks with ragged last chunks and wide
+    halos), FP32 and FP64 up to c = 128 (the largest staged range); every row
+    of every block is compared with the dense operator."""
+    N = 256
+    real = np.float64 if prec == bsp.BSP_PREC_F64 else np.float32
+    tdt = torch.float64 if prec == bsp.BSP_PREC_F64 else torch.float32
+    xyz, faces = synth.torus(N, seed=4)
+    if kind == "tiles":
+        ptr, verts = synth.tile_partition(N, 32)
+    else:
+        ptr, verts = synth.bfs_partition(N, target_blocks=90, min_size=300, max_size=1500, seed=5)
+    k = len(ptr) - 1
+    parent = -np.ones(k, np.int32)
+    h = bsp.bsp_mesh_create(xyz, faces, ptr, verts, parent,
+                            bsp.make_opts(precision=prec, weight_mode=mode))
+    om = O.build_mesh(N * N, ptr, verts, parent, faces=faces, xyz=xyz,
+                      weight_mode={0: O.WEIGHT_COMBINATORIAL, 2: O.WEIGHT_INV_SQ_DIST}[mode])
+    try:
+        rng = np.random.default_rng(7)
+        P = rng.standard_normal((N * N, c))
+        Pd = torch.tensor(P, dtype=tdt, device="cuda")
+        Yd = torch.full_like(Pd, float("nan"))
+        bsp.bsp_spmm(h, Pd, Yd, c)
+        torch.cuda.synchronize()
+        Y = Yd.cpu().double().numpy()
+        assert np.isfinite(Y).all()
+        Pr = P.astype(real).astype(np.float64)
+        for b, blk in enumerate(om.blocks):
+            rows = slice(ptr[b], ptr[b + 1])
+            A = O.laplacian(blk) + 1e-2 * np.eye(blk.verts.size)
+            ref = A @ Pr[rows]
+            err = np.abs(Y[rows] - ref).max() / np.abs(ref).max()
+            assert err <= (1e-12 if real == np.float64 else 2e-6), (b, err)
+    finally:
+        bsp.bsp_mesh_destroy(h)
+
+
 # ---------------------------------------------------------------- fixed-c OI
 
 def test_fixed_c_fp64_grid_blocks():
