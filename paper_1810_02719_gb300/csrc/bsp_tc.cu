@@ -3,13 +3,14 @@
 // E[b] = U[b]^T X[b] and X~[b] = U[b] E[b] (Sec. 3 GFT / inverse GFT).
 //
 // BF16 operands (kind::f16), FP32 accumulation in tensor memory.  Operands are
-// staged by all threads from global memory into shared memory in the
-// K-major, non-swizzled core-matrix layout (8 rows x 16 bytes per core
-// matrix; neighbouring core matrices 128 bytes apart along K and 1024 bytes
-// apart along M/N), one elected thread issues the MMAs and commits them to an
-// mbarrier, and four warps read the accumulator back with tcgen05.ld.  Every
-// mbarrier wait is bounded: on expiry the kernel records an error, still
-// frees its tensor memory and returns.
+// staged from global memory into shared memory by 16-byte asynchronous
+// copies, in the canonical core-matrix layouts (non-swizzled: 8 rows x 16
+// bytes per core matrix; or, for the projection's gathered coordinate rows,
+// 128-byte swizzled atoms of 8 rows x 128 bytes), one elected thread issues
+// the MMAs and commits them to an mbarrier, and four warps read the
+// accumulator back with tcgen05.ld.  Every mbarrier wait is bounded: on
+// expiry the kernel records an error, skips its later waits, still frees its
+// tensor memory and returns.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -21,10 +22,11 @@ namespace {
 
 constexpr int kTT = 256;         // threads per CTA
 constexpr int kM = 128;          // MMA M (rows of D = TMEM lanes)
-constexpr int kKC = 32;          // projection K chunk per ring stage (2 MMAs of K = 16)
+constexpr int kKC = 64;          // projection K chunk per ring stage (4 MMAs of K = 16)
 constexpr long kSpin = 1L << 26; // bounded mbarrier wait (iterations)
-constexpr int kS = 6;            // projection ring depth
-constexpr int kD = 4;            // chunks in flight ahead of the MMAs (kS - 2)
+constexpr int kS = 3;            // projection ring depth
+constexpr int kD = 1;            // projection: chunks a copying thread runs ahead of its arrivals
+constexpr int kProd = kTT - 32;  // projection: copying threads (warps 1-7)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -37,15 +39,18 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
 }
 
+// The same with the 128-byte swizzle (layout type 2): for an MN-major operand,
+// atoms of 8 K-rows x 128 bytes (64 elements along MN, row k's 16-byte piece
+// j stored at piece j ^ (k & 7)), lbo = the stride between atoms along MN,
+// sbo = the stride between 8-row groups along K.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return smem_desc(saddr, lbo, sbo) | ((uint64_t)2 << 61);
+}
+
 // Instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major.
 __device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
-}
-
-// Element (r, k) of a K-major tile with K extent kc, in elements.
-__device__ __forceinline__ int kmaj(int r, int k, int kc) {
-  return ((r >> 3) * (kc >> 3) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7);
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc,
@@ -60,8 +65,11 @@ __device__ __forceinline__ void mma_commit(uint64_t* mbar) {
                ::"r"(smem_u32(mbar)));
 }
 
-// Bounded wait for the given phase of an mbarrier; returns false on expiry.
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t phase) {
+// Bounded wait for the given phase of an mbarrier; returns false on expiry,
+// and at once when `ok` is already false (a thread whose earlier wait expired
+// skips the rest instead of spinning again).
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t phase, bool ok = true) {
+  if (!ok) return false;
   uint32_t done = 0;
   for (long it = 0; it < kSpin && !done; ++it) {
     asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -69,6 +77,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t phase) {
                  : "=r"(done) : "r"(smem_u32(mbar)), "r"(phase));
   }
   return done != 0;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.release.cta.shared::cta.b64 st, [%0];\n\t}\n"
+               ::"r"(smem_u32(mbar)) : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t addr, float (&v)[16]) {
@@ -154,23 +167,30 @@ __global__ void k_coef_bf16(const float* __restrict__ E, __nv_bfloat16* __restri
 
 // E^T tile = X^T U for block b = blockIdx.y and frame-columns [m0, m0 + 128):
 // A[m][k] = X[verts[r0 + k]][m0 + m] and B[n][k] = Ub[r0 + k][n], both
-// MN-major, so every 16-byte piece of a gathered X row (8 frame-columns) and
-// of a basis row (8 basis columns) is one asynchronous copy, no register
-// staging.  K runs over the block's vertices in chunks of 32 through a
-// 6-stage ring with 4 chunks in flight (3 CTAs per SM); stage reuse waits on
-// the MMA commit of the chunk that last read it.  Eight consecutive threads fill one core matrix (8 rows x 16 B,
-// contiguous), so the shared-memory writes are conflict-free.
+// MN-major.  K runs over the block's vertices in chunks of 64 through a ring
+// of 3 stages.  Warps 1-7 copy: 16 consecutive threads take one gathered X
+// row's 256 bytes (coalesced), written into 128-byte swizzled atoms (atom
+// (k / 8, m / 64) at 1024 (2 (k / 8) + m / 64) bytes, conflict-free); the
+// basis rows go to the non-swizzled core-matrix layout.  Each copying thread
+// waits for the stage's release (the MMA commit of the chunk that last read
+// it), copies, and one chunk later waits for its own copies, fences them for
+// the tensor core's proxy and arrives on the stage's full barrier.  Lane 0 of
+// warp 0 waits on the full barriers and issues the MMAs.  No CTA barrier per
+// chunk.
 __global__ void __launch_bounds__(kTT) k_project_tc(ProjArgs a, const __nv_bfloat16* __restrict__ Ub,
                                                     const __nv_bfloat16* __restrict__ X,
                                                     float* __restrict__ E, int NP, int tcols,
                                                     int* status) {
-  constexpr int S = kS;
+  constexpr int S = kS, D = kD;
+  static_assert(D < S, "a copying thread runs fewer chunks ahead than the ring holds");
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const int stageA = kM * kKC, stageB = NP * kKC;                     // elements
-  __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(smem_raw);     // S x kM x kKC
+  // swizzled atoms need 1024-byte alignment: the launch adds 1024 bytes of slack
+  const uint32_t raw = smem_u32(smem_raw);
+  __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(smem_raw + (((raw + 1023u) & ~1023u) - raw));
   __nv_bfloat16* sB = sA + S * stageA;                                 // S x NP x kKC
   int32_t* sv = reinterpret_cast<int32_t*>(sB + S * stageB);           // the block's vertex ids
-  __shared__ __align__(8) uint64_t mbar[kS];
+  __shared__ __align__(8) uint64_t full[kS], empty[kS];
   __shared__ uint32_t tmem_base;
   const int tid = threadIdx.x, warp = tid >> 5;
   const int b = blockIdx.y;
@@ -182,69 +202,75 @@ __global__ void __launch_bounds__(kTT) k_project_tc(ProjArgs a, const __nv_bfloa
   // vertex ids once per CTA: the row gathers below then need no dependent
   // global load before each copy
   for (int t = tid; t < nb; t += kTT) sv[t] = a.verts[r0 + t];
-  if (tid < S) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[tid])));
+  if (tid < S) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[tid])), "r"(kProd));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[tid])));
+  }
   if (tid == 0) asm volatile("fence.mbarrier_init.release.cluster;");
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
-  const uint32_t idesc = idesc_bf16_major(kM, NP, 1, 1);
   const int nchunk = (nb + kKC - 1) / kKC;
   const int gB = NP / 8;
-  auto issue = [&](int ch) {
-    const int st = ch % S, k0 = ch * kKC;
-    __nv_bfloat16* tA = sA + st * stageA;
-    __nv_bfloat16* tB = sB + st * stageB;
-    // A: kKC rows x 16 pieces; item -> (k % 8 fastest, piece, k / 8)
-    for (int it = tid; it < kKC * (kM / 8); it += kTT) {
-      const int k = (it & 7) + 8 * (it >> 7), mg = (it >> 3) & 15;
-      const int row = k0 + k;
-      const bool ok = row < nb && m0 + 8 * mg < cols;
-      const __nv_bfloat16* src = ok ? X + (size_t)sv[row] * cols + m0 + 8 * mg : X;
-      cp16(tA + mnmaj(8 * mg, k, kM), src, ok ? 16 : 0);
-    }
-    // B: kKC rows x NP/8 pieces of the BF16 basis
-    for (int it = tid; it < kKC * gB; it += kTT) {
-      const int q = it >> 3, k = (it & 7) + 8 * (q / gB), ng = q % gB;
-      const int row = k0 + k;
-      const bool ok = row < nb;
-      const __nv_bfloat16* src = ok ? Ub + (size_t)(r0 + row) * NP + 8 * ng : Ub;
-      cp16(tB + mnmaj(8 * ng, k, NP), src, ok ? 16 : 0);
-    }
-  };
   bool ok = true;
-  for (int ch = 0; ch < kD; ++ch) {
-    if (ch < nchunk) issue(ch);
-    cp_commit();
-  }
-  for (int ch = 0; ch < nchunk; ++ch) {
-    const int nxt = ch + kD;
-    if (nxt < nchunk) {
-      // stage nxt % S was last read by the MMAs of chunk ch - 2, issued two
-      // iterations ago, so this wait rarely blocks
-      if (ch >= 2 && !mbar_wait(&mbar[(ch - 2) % S], ((ch - 2) / S) & 1)) ok = false;
-      issue(nxt);
-    }
-    cp_commit();
-    cp_wait<kD>();  // chunk ch's copies (this thread's) have landed
-    asm volatile("fence.proxy.async.shared::cta;");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      const int st = ch % S;
-      const uint32_t aBase = smem_u32(sA + st * stageA), bBase = smem_u32(sB + st * stageB);
-#pragma unroll
-      for (int q = 0; q < kKC / 16; ++q) {
-        const uint64_t da = smem_desc(aBase + q * 2 * (kM / 8) * 128, (kM / 8) * 128, 128);
-        const uint64_t db = smem_desc(bBase + q * 2 * gB * 128, gB * 128, 128);
-        mma_bf16(tmem, da, db, idesc, (ch > 0 || q > 0) ? 1u : 0u);
+  if (warp > 0) {
+    const int p = tid - 32;
+    for (int ch = 0; ch < nchunk + D; ++ch) {
+      if (ch < nchunk) {
+        const int st = ch % S, k0 = ch * kKC;
+        if (ch >= S && !mbar_wait(&empty[st], ((ch / S) - 1) & 1, ok)) ok = false;
+        __nv_bfloat16* tA = sA + st * stageA;
+        __nv_bfloat16* tB = sB + st * stageB;
+        for (int it = p; it < kKC * (kM / 8); it += kProd) {
+          const int k = it >> 4, mg = it & 15, row = k0 + k;
+          const bool okr = row < nb && m0 + 8 * mg < cols;
+          const __nv_bfloat16* src = okr ? X + (size_t)sv[row] * cols + m0 + 8 * mg : X;
+          const int ma = mg >> 3, jj = mg & 7;
+          cp16(tA + ((k >> 3) * 2 + ma) * 512 + (k & 7) * 64 + ((jj ^ (k & 7)) * 8), src,
+               okr ? 16 : 0);
+        }
+        // basis: item -> (k % 8 fastest, piece, k / 8)
+        for (int it = p; it < kKC * gB; it += kProd) {
+          const int q = it >> 3, k = (it & 7) + 8 * (q / gB), ng = q % gB;
+          const int row = k0 + k;
+          const bool okr = row < nb;
+          const __nv_bfloat16* src = okr ? Ub + (size_t)(r0 + row) * NP + 8 * ng : Ub;
+          cp16(tB + mnmaj(8 * ng, k, NP), src, okr ? 16 : 0);
+        }
       }
-      mma_commit(&mbar[st]);
+      cp_commit();
+      if (ch >= D) {
+        cp_wait<D>();   // this thread's copies of chunk ch - D have landed
+        asm volatile("fence.proxy.async.shared::cta;");
+        mbar_arrive(&full[(ch - D) % S]);
+      }
     }
+    cp_wait<0>();
+  } else {
+    // lanes 1-31 of warp 0 wait at the warp barrier (no spinning beside the
+    // issuing lane)
+    if (tid == 0) {
+      const uint32_t idesc = idesc_bf16_major(kM, NP, 1, 1);
+      for (int ch = 0; ch < nchunk; ++ch) {
+        const int st = ch % S;
+        if (!mbar_wait(&full[st], (ch / S) & 1, ok)) ok = false;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t aBase = smem_u32(sA + st * stageA), bBase = smem_u32(sB + st * stageB);
+#pragma unroll
+        for (int q = 0; q < kKC / 16; ++q) {
+          const uint64_t da = smem_desc_sw128(aBase + q * 4096, 1024, 2048);
+          const uint64_t db = smem_desc(bBase + q * 2 * gB * 128, gB * 128, 128);
+          mma_bf16(tmem, da, db, idesc, (ch > 0 || q > 0) ? 1u : 0u);
+        }
+        mma_commit(&empty[st]);
+      }
+    }
+    __syncwarp();
   }
-  cp_wait<0>();
-  // the last commit covers every MMA issued before it
-  if (nchunk > 0 && !mbar_wait(&mbar[(nchunk - 1) % S], ((nchunk - 1) / S) & 1)) ok = false;
+  // every thread: the last commit covers every MMA issued before it
+  if (nchunk > 0 && !mbar_wait(&empty[(nchunk - 1) % S], ((nchunk - 1) / S) & 1, ok)) ok = false;
+  __syncwarp();
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ok && nchunk > 0) {
     // warp w reads lanes 32 (w % 4) .. + 31; warps 0-3 and 4-7 split the columns
@@ -258,7 +284,7 @@ __global__ void __launch_bounds__(kTT) k_project_tc(ProjArgs a, const __nv_bfloa
         if (c0 + j < c && m0 + m < cols) E[(eb + c0 + j) * cols + m0 + m] = v[j];
     }
   }
-  if (!ok && tid == 0) atomicOr(status, ST_TIMEOUT);
+  if (!ok) atomicOr(status, ST_TIMEOUT);
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0) tmem_free(tmem, tcols);
@@ -415,7 +441,7 @@ int launch_project_tc(const ProjArgs& a, const void* Ub, const void* X, float* E
   const int NP = pad16(a.cmax);
   if (a.cols % 8 != 0 || NP > 256) return BSP_ERR_INVALID_ARG;
   const size_t smem = (size_t)kS * (kM + NP) * kKC * sizeof(__nv_bfloat16) +
-                      (size_t)a.max_nb * sizeof(int32_t);
+                      (size_t)a.max_nb * sizeof(int32_t) + 1024;   // + alignment slack
   if (smem > 220 * 1024) return BSP_ERR_INVALID_ARG;
   dim3 grid((a.cols + kM - 1) / kM, a.k);
   prof_begin(KC_PROJECT, s);
