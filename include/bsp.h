@@ -441,8 +441,8 @@ int bsp_autotune(bsp_mesh* mesh, int32_t c, int32_t t_max, const void* V0_roots,
  * The first call on each device looks up the scratch array's device address
  * and configures the kernel.  All calls share the one scratch array: calls
  * that overlap on the GPU (other host threads, other streams) race and must
- * be serialised by the caller.  Errors: BSP_ERR_INVALID_ARG, BSP_ERR_NUMERICAL (rank-deficient Y),
- * BSP_ERR_CUDA.
+ * be serialised by the caller.  Errors: BSP_ERR_INVALID_ARG,
+ * BSP_ERR_NUMERICAL (rank-deficient Y), BSP_ERR_CUDA.
  */
 int bsp_onorm_noalloc(const float* Y, float* Q, int32_t n, int32_t c, void* stream);
 
