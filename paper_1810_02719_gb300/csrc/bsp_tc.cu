@@ -390,16 +390,33 @@ __global__ void __launch_bounds__(kTT) k_recon_tc(ProjArgs a, const __nv_bfloat1
       asm volatile("tcgen05.fence::before_thread_sync;");
       __syncthreads();
       const int width = min(kNT, cols - n0);
-      for (int r = warp; r < kM; r += kTT / 32) {
-        if (m0 + r >= nb) break;
-        float* dst = X + (size_t)sv[r] * cols + n0;
-        const float* srow = out + r * kOS;
-        if (ok) {
-          if (vec && width == kNT) {
-            reinterpret_cast<float4*>(dst)[lane] = reinterpret_cast<const float4*>(srow)[lane];
-          } else {
-            for (int e = lane; e < width; e += 32) dst[e] = srow[e];
-          }
+      if (ok && vec) {
+        // the warp's 16 rows: every shared-memory load first, then the
+        // 16-byte stores (no load -> store dependency per row); width is a
+        // multiple of 4 here (cols % 4 == 0, n0 % 128 == 0)
+        constexpr int kRW = kM / (kTT / 32);   // rows per warp
+        const int nv = width >> 2;
+        float4 buf[kRW];
+        int vid[kRW];
+#pragma unroll
+        for (int i = 0; i < kRW; ++i) {
+          const int r = warp + (kTT / 32) * i;
+          const bool live = lane < nv && m0 + r < nb;
+          buf[i] = live ? reinterpret_cast<const float4*>(out + r * kOS)[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+          vid[i] = live ? sv[r] : 0;
+        }
+#pragma unroll
+        for (int i = 0; i < kRW; ++i) {
+          const int r = warp + (kTT / 32) * i;
+          if (lane < nv && m0 + r < nb)
+            reinterpret_cast<float4*>(X + (size_t)vid[i] * cols + n0)[lane] = buf[i];
+        }
+      } else if (ok) {
+        for (int r = warp; r < kM; r += kTT / 32) {
+          if (m0 + r >= nb) break;
+          float* dst = X + (size_t)sv[r] * cols + n0;
+          const float* srow = out + r * kOS;
+          for (int e = lane; e < width; e += 32) dst[e] = srow[e];
         }
       }
     }
