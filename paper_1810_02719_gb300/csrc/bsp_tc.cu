@@ -271,6 +271,7 @@ __global__ void __launch_bounds__(kTT) k_project_tc(ProjArgs a, const __nv_bfloa
   // every thread: the last commit covers every MMA issued before it
   if (nchunk > 0 && !mbar_wait(&empty[(nchunk - 1) % S], ((nchunk - 1) / S) & 1, ok)) ok = false;
   __syncwarp();
+  ok = __all_sync(0xffffffffu, ok);   // one outcome per warp: tcgen05.ld is warp-aligned
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ok && nchunk > 0) {
     // warp w reads lanes 32 (w % 4) .. + 31; warps 0-3 and 4-7 split the columns

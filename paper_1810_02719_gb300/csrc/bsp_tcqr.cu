@@ -183,7 +183,8 @@ __global__ void __launch_bounds__(kTQ) k_gram_tc(DenseArgs a, const float* __res
     }
     commit(&mbar);
   }
-  const bool ok = wait_bounded(&mbar, 0);
+  // one outcome per warp: the tensor-memory loads below are warp-aligned
+  const bool ok = __all_sync(0xffffffffu, wait_bounded(&mbar, 0));
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ok && warp < 2) {   // Gram rows < 64 live in lanes 0 .. 63
     const int i = tid;    // Gram row (lane)
@@ -273,7 +274,8 @@ __global__ void __launch_bounds__(kTQ) k_mul_tc(DenseArgs a, const float* Y, flo
     }
     commit(&mbar);
   }
-  const bool ok = wait_bounded(&mbar, 0);
+  // one outcome per warp: the tensor-memory loads below are warp-aligned
+  const bool ok = __all_sync(0xffffffffu, wait_bounded(&mbar, 0));
   asm volatile("tcgen05.fence::after_thread_sync;");
   __syncthreads();   // every thread past the wait: the operand buffers are free
   const int os = Np + 1;
