@@ -82,3 +82,38 @@ def test_mesh_options_are_checked_before_the_device(bsp):
         _invalid(bsp, bsp.bsp_mesh_create, xyz, faces, ptr, verts, parent, bsp.make_opts(**kw))
     _invalid(bsp, bsp.bsp_mesh_create, xyz, faces, ptr, verts, parent, bsp.make_opts(), n=0,
              match="positive")
+
+
+# every entry point that takes a mesh handle, checked straight through ctypes
+# (the Python wrappers are bypassed so that the library's own check is seen)
+MESH_CALLS = ["bsp_get_edges", "bsp_get_block_csr", "bsp_set_edge_weights", "bsp_oi_track",
+              "bsp_oi_track_dynamic", "bsp_get_block_c", "bsp_get_basis", "bsp_project",
+              "bsp_reconstruct", "bsp_reconstruct_bf16", "bsp_spmm", "bsp_set_profiling",
+              "bsp_get_kernel_times", "bsp_filter_forward", "bsp_filter_backward",
+              "bsp_autotune", "bsp_quantize", "bsp_dequantize", "bsp_bits_per_vertex",
+              "bsp_merge_overlapped", "bsp_oi_track_paper_doi", "bsp_get_stats"]
+
+
+def test_every_mesh_call_rejects_a_null_handle_before_the_device(bsp):
+    import ctypes as C
+    ints = (C.c_int32, C.c_int64, C.c_uint64)
+    for name in MESH_CALLS:
+        f = getattr(bsp._lib, name)
+        args = []
+        for t in f.argtypes:
+            if t in ints:
+                args.append(1)
+            elif t is C.c_double:
+                args.append(1.0)
+            else:
+                args.append(None)        # the handle and every buffer: NULL
+        rc = f(*args)
+        assert rc == bsp.BSP_ERR_INVALID_ARG, (name, rc)
+        assert bsp.bsp_last_error(), name
+    # destroying a NULL handle is a no-op
+    assert bsp._lib.bsp_mesh_destroy(None) == bsp.BSP_OK
+    # the list above covers every exported call that takes a mesh handle
+    no_mesh = {"bsp_opts_default", "bsp_mesh_create", "bsp_mesh_create_edges",
+               "bsp_mesh_destroy", "bsp_last_error", "bsp_onorm_noalloc", "bsp_nmsve",
+               "bsp_fine_denoise", "bsp_normal_angle_error"}
+    assert set(bsp.exported_symbols()) == set(MESH_CALLS) | no_mesh
