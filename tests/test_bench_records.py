@@ -56,3 +56,16 @@ def test_lookup_follows_the_source_hash(monkeypatch):
     for kernel in recs:
         assert bench.captured_traffic(kernel, blocks_per_launch=4) is None
     assert bench.captured_traffic("no_such_kernel") is None
+
+
+def test_operator_product_bytes_count_the_chunk_table():
+    # blocks of 65, 64 and 1 rows: chunks of up to 64 rows -> 2 + 1 + 1 = 4
+    ptr = [0, 65, 129, 130]
+    n, c, nnz = 130, 8, 500
+    want = n * c * 8 + nnz * 2 + (n + 1) * 4 + n * 4 + 4 * 32
+    assert bench.spmm_algorithmic_bytes(n, c, nnz, ptr) == want
+    # the 1024^2 torus in 32 x 32 tiles: 16 chunks per block
+    from paper_1810_02719_gb300 import synth
+    ptr, _ = synth.tile_partition(64, 32)
+    assert bench.spmm_algorithmic_bytes(64 * 64, 1, 0, ptr) == \
+        64 * 64 * 8 + (64 * 64 + 1) * 4 + 64 * 64 * 4 + 4 * 16 * 32
