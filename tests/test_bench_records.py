@@ -64,7 +64,7 @@ def test_operator_product_bytes_count_the_chunk_table():
     n, c, nnz = 130, 8, 500
     want = n * c * 8 + nnz * 2 + (n + 1) * 4 + n * 4 + 4 * 32
     assert bench.spmm_algorithmic_bytes(n, c, nnz, ptr) == want
-    # the 1024^2 torus in 32 x 32 tiles: 16 chunks per block
+    # a 64^2 grid in four 32 x 32 tiles: 16 chunks per block
     from paper_1810_02719_gb300 import synth
     ptr, _ = synth.tile_partition(64, 32)
     assert bench.spmm_algorithmic_bytes(64 * 64, 1, 0, ptr) == \
